@@ -1,0 +1,297 @@
+/*
+ * lightfuse.h - C ABI of the B300 (sm_103a) surfel ray tracer.
+ *
+ * Differentiable ray tracing of 2D Gaussian surfels (Eq. 1) with one-bounce
+ * physically based shading under an environment map (Eq. 10-11), for scenes
+ * assembled from a shared background plus rigidly movable objects (Eq. 2).
+ *
+ * Conventions shared by every call
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; they
+ *     must stay valid for as long as the context uses them (the scene arrays
+ *     until the next lf_bvh_build or lf_destroy, an environment map until it
+ *     is replaced).  Other pointers are host pointers, read during the call.
+ *   - All work is enqueued asynchronously on the context's CUDA stream; no
+ *     call synchronises except lf_sync, lf_bvh_build (it reads object
+ *     offsets and sizes) and the serving calls that say so.
+ *   - Render calls allocate nothing.  lf_bvh_build and lf_env_set allocate
+ *     library-owned device storage (BVH nodes, packed records, sampling
+ *     tables) when the scene or map grows.
+ *   - Errors are returned as lf_status; the library never aborts, traps or
+ *     exits.  Kernels report device-side conditions (traversal stack
+ *     overflow, round limit) through a device status word that lf_sync
+ *     returns.  lf_last_error gives a human-readable message.
+ *   - Floating point data are FP32.  Gradients are ACCUMULATED (+=) into the
+ *     caller's buffers; the caller zeroes them.
+ *   - Limits: at most LF_MAX_OBJECTS objects (background included), at most
+ *     2^24 surfels per object and 2^24 surfels in total (surfel ids and hit
+ *     counts are stored exactly in FP32 G-buffer channels).
+ */
+#ifndef LIGHTFUSE_H
+#define LIGHTFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LF_MAX_OBJECTS 64
+#define LF_MAX_ENVS 16     /* environment map slots                              */
+#define LF_KBUF 16        /* hits collected per traversal round (k-buffer)    */
+#define LF_STACK_DEPTH 64 /* per-thread traversal stack entries (shared mem)  */
+
+typedef enum {
+  LF_OK = 0,
+  LF_ERR_INVALID = 1,     /* bad argument; nothing was enqueued              */
+  LF_ERR_OOM = 2,         /* device allocation failed / over memory budget   */
+  LF_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+  LF_ERR_STACK = 4,       /* a traversal stack overflowed (device status)    */
+  LF_ERR_ROUND_LIMIT = 5, /* a ray needed more than max_rounds k-buffer rounds */
+  LF_ERR_TIMEOUT = 6,     /* a wait ran out of time                          */
+  LF_ERR_BUSY = 7,        /* no free slot (serving)                          */
+  LF_ERR_NOT_BUILT = 8    /* render before lf_bvh_build / lf_env_set         */
+} lf_status;
+
+/*
+ * Method constants.  The paper fixes only the 0.99 opacity cap (Sec. 3.2,
+ * Eq. 6); the others are readings of what it leaves open.
+ */
+typedef struct {
+  float T_min;       /* compositing stops after the hit whose T falls below  */
+  float alpha_min;   /* Eq. 6: hits with alpha~ below this are discarded     */
+  float alpha_max;   /* Eq. 6: alpha~ = min(alpha_max, o exp(-|xi|^2/2))     */
+  float support_r2;  /* Eq. 6: finite support u^2 + v^2 <= support_r2        */
+  float eps_w;       /* Eq. 7: z = sum w z / (sum w + eps_w)                 */
+  float t_min;       /* hits need t > t_min                                  */
+  float ray_offset;  /* secondary rays start at x + ray_offset * n           */
+  float p_spec;      /* Eq. 11: probability of the GGX lobe in the mixture   */
+  int max_rounds;    /* k-buffer rounds per ray before LF_ERR_ROUND_LIMIT    */
+  int brdf_mode;     /* 0 Lambert + GGX metallic-roughness, 1 Lambert a/pi   */
+  int sampling_mode; /* 0 MIS (NEE + BSDF), 1 BSDF only, 2 NEE only          */
+} lf_params;
+
+/* Scene: caller-owned FP32 device arrays, surfel i at index i.  Object k
+ * owns the contiguous surfels [object_offsets[k], object_offsets[k+1]);
+ * object 0 is the background.  Eq. 1: centre mu, tangent axes tu, tv (the
+ * surfel normal is tu x tv), in-plane scales (s_u, s_v), opacity o, base
+ * colour a, metallic m, roughness r. */
+typedef struct {
+  float* mu_dev;        /* N x 3 */
+  float* tu_dev;        /* N x 3 */
+  float* tv_dev;        /* N x 3 */
+  float* scale_dev;     /* N x 2 */
+  float* opacity_dev;   /* N     */
+  float* albedo_dev;    /* N x 3 */
+  float* metallic_dev;  /* N     */
+  float* roughness_dev; /* N     */
+  int n;
+  const int* object_offsets; /* host, n_objects + 1 entries, offsets[0] = 0, offsets[n_objects] = n */
+  int n_objects;
+} lf_scene;
+
+/* Pinhole camera: pixel (x, y) looks through its centre; fovy is vertical. */
+typedef struct {
+  float eye[3], target[3], up[3];
+  float fovy_deg;
+  int width, height;
+} lf_camera;
+
+/* G-buffer written by lf_trace_primary: LF_GBUF_CHANNELS planes of P = W*H
+ * floats, channel c of pixel p at gbuf[c * P + p] (p = y * width + x). */
+enum {
+  LF_CH_T = 0,       /* final transmittance T                         */
+  LF_CH_W = 1,       /* sum of weights (= 1 - T)                      */
+  LF_CH_DEPTH = 2,   /* composited ray distance                       */
+  LF_CH_X = 3,       /* composited position (3)                       */
+  LF_CH_N = 6,       /* composited, renormalised normal (3)           */
+  LF_CH_A = 9,       /* composited base colour (3)                    */
+  LF_CH_M = 12,      /* composited metallic                           */
+  LF_CH_R = 13,      /* composited roughness                          */
+  LF_CH_RHO = 14,    /* unlit radiance sum w a + T E(d) (3)           */
+  LF_CH_NLEN = 17,   /* length of the normal before renormalising     */
+  LF_CH_HITS = 18,   /* number of composited hits                     */
+  LF_CH_TSTOP = 19,  /* ray distance of the last composited hit       */
+  LF_CH_IDSTOP = 20, /* surfel id of the last composited hit (-1: none) */
+  LF_CH_DIR = 21,    /* primary ray direction (3)                     */
+  LF_GBUF_CHANNELS = 24,
+  LF_GBUF_DIFF = 17  /* channels 0..16 accept an upstream gradient    */
+};
+
+/* Per-surfel gradient layout: 17 floats per surfel. */
+enum { LF_G_MU = 0, LF_G_TU = 3, LF_G_TV = 6, LF_G_S = 9, LF_G_O = 11, LF_G_A = 12, LF_G_M = 15, LF_G_R = 16,
+       LF_G_STRIDE = 17 };
+
+typedef struct lf_ctx lf_ctx;
+
+/* Defaults: T_min 1e-4, alpha_min 1/255, alpha_max 0.99, support_r2 9,
+ * eps_w 1e-8, t_min 1e-4, ray_offset 1e-3, p_spec 0.5, max_rounds 64. */
+lf_status lf_params_default(lf_params* out);
+
+/* Create a context bound to the current CUDA device and `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Allocates the device status
+ * word.  *out is set only on LF_OK. */
+lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out);
+lf_status lf_destroy(lf_ctx* ctx);
+lf_status lf_set_stream(lf_ctx* ctx, void* stream);
+const char* lf_last_error(const lf_ctx* ctx);
+
+/* Wait for the context's stream, then read and clear the device status word. */
+lf_status lf_sync(lf_ctx* ctx);
+
+/*
+ * Build the two-level acceleration structure (Eq. 2 assembly: one BLAS per
+ * object, background included, under a flat TLAS of object boxes).  Per
+ * object: surfel AABBs at the support radius, 30-bit Morton codes of their
+ * centres in the object's bounds, an LSD radix sort, Karras hierarchy
+ * (duplicate codes ordered by index), bottom-up box fit.  Packs the surfel
+ * records the traversal reads.  Keeps the scene pointers.  Synchronises.
+ */
+lf_status lf_bvh_build(lf_ctx* ctx, const lf_scene* scene);
+
+/*
+ * Rigid object rearrangement (Eq. 2: T = (R, t) acts on centres and
+ * orientations only).  Applies mu <- R mu + t, tu <- R tu, tv <- R tv IN
+ * PLACE to object `object_id`'s surfels in the caller's arrays, repacks
+ * them, refits that object's BLAS (topology kept) and updates the TLAS.
+ * R is row-major 3x3 (host), t is 3 floats (host).
+ */
+lf_status lf_bvh_refit(lf_ctx* ctx, int object_id, const float R[9], const float t[3]);
+
+/* After the caller changed any surfel attribute of object `object_id`
+ * (-1: all objects) in place: repack its records and refit its BLAS. */
+lf_status lf_scene_sync(lf_ctx* ctx, int object_id);
+
+/* Material edit (Sec. 3.4.2): overwrite object `object_id`'s base colour
+ * (rgb != NULL), metallic (>= 0) and/or roughness (>= 0) in the caller's
+ * arrays and repack. */
+lf_status lf_material_set(lf_ctx* ctx, int object_id, const float* rgb, float metallic, float roughness);
+
+/*
+ * Register environment map `env_id` (0 <= env_id < LF_MAX_ENVS): H x W x 3 FP32
+ * texels, row 0 looking up (+y), column 0 at phi = 0 of the y-up
+ * equirectangular mapping theta = acos(w_y), phi = atan2(w_x, -w_z) + pi.
+ * Builds the importance-sampling tables (texel weight = (Rec.709 luminance
+ * + 1e-6) * sin(theta at the row centre), FP64 sums, FP32 tables).  The
+ * texels are read in place at render time.
+ */
+lf_status lf_env_set(lf_ctx* ctx, int env_id, const float* rgb_dev, int H, int W);
+
+/*
+ * Primary rays (Eq. 6-7): per pixel, rounds of "collect the LF_KBUF nearest
+ * accepted hits with key (t, id) beyond the last round's key", composited
+ * front to back until T < T_min.  Writes the G-buffer (see LF_CH_*); the
+ * radiance channel uses environment `env_id` for T E(d).
+ * gbuf_dev: LF_GBUF_CHANNELS * width * height floats.
+ */
+lf_status lf_trace_primary(lf_ctx* ctx, const lf_camera* cam, int env_id, float* gbuf_dev);
+
+/*
+ * One-bounce shading (Eq. 11, Sec. 4.2 path budget): per pixel and sample,
+ * Philox4x32-10 uniforms keyed by `seed` with counter (pixel, sample, group,
+ * 0); one environment NEE sample with a shadow ray, one BSDF continuation
+ * from the cosine/GGX mixture traced to a secondary record, two environment
+ * NEE samples with shadow rays there; power-heuristic MIS.
+ * rgb_dev[p*3 + c] = T E(d) + (1 - T) / spp * sum_s (NEE + BSDF terms).
+ * ray_count_dev (nullable): a device uint64 the kernel ADDS the number of
+ * rays it traced to.
+ */
+lf_status lf_shade_bounce(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
+                          uint64_t seed, float* rgb_dev, unsigned long long* ray_count_dev);
+
+/* Scratch bytes lf_trace_backward needs for a width x height image. */
+size_t lf_backward_scratch_bytes(int width, int height);
+
+/*
+ * Adjoint of lf_trace_primary + lf_shade_bounce under path replay (Sec. 3.3):
+ * the shading pass replays the same Philox samples and keeps directions,
+ * pdfs, MIS weights, visibilities and secondary records fixed; gradients flow
+ * through the primary record and every environment lookup.  The primary pass
+ * re-traverses each ray back to front from the stored final transmittance
+ * and stop key (no per-ray hit lists), recovering T_j = T_{j+1} / (1 -
+ * alpha_j), and scatters Eq. 6-7 adjoints to the surfels.
+ *   gbuf_dev:     the G-buffer of the forward pass (unchanged scene).
+ *   dL_drgb_dev:  P x 3 (nullable: no shading term).
+ *   dL_dgbuf_dev: LF_GBUF_CHANNELS planes (nullable); channels
+ *                 0..LF_GBUF_DIFF-1 are used.
+ *   d_surfel_dev: N x 17 (LF_G_* layout), accumulated.
+ *   d_env_dev:    H x W x 3 of `env_id`, accumulated (nullable).
+ *   scratch_dev:  at least lf_backward_scratch_bytes(width, height) bytes.
+ */
+lf_status lf_trace_backward(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
+                            uint64_t seed, const float* dL_drgb_dev, const float* dL_dgbuf_dev,
+                            float* d_surfel_dev, float* d_env_dev, void* scratch_dev, size_t scratch_bytes);
+
+/*
+ * Traversal counters for roofline accounting: when counters_dev (4 x uint64
+ * on the device) is non-NULL, every trace kernel adds [node visits, surfel
+ * tests, composited hits, rays] to it.  NULL turns counting off.
+ */
+lf_status lf_set_counters(lf_ctx* ctx, unsigned long long* counters_dev);
+
+/* Philox4x32-10 of n counters (device n x 4 words) with key (k0, k1). */
+lf_status lf_philox(lf_ctx* ctx, const uint32_t* ctr_dev, int n, uint32_t k0, uint32_t k1, uint32_t* out_dev);
+
+/* Copy the sampling tables of `env_id` (device FP32: H, H, H*W, H*W). */
+lf_status lf_env_tables(lf_ctx* ctx, int env_id, float* pmf_row_dev, float* cdf_row_dev, float* pmf_col_dev,
+                        float* cdf_col_dev);
+
+/* BVH inspection: number of internal nodes of object k, and a host copy of
+ * its nodes (16 floats each: child boxes and child codes, see the build). */
+lf_status lf_bvh_info(lf_ctx* ctx, int object_id, int* n_internal, int* root_code);
+lf_status lf_bvh_copy_nodes(lf_ctx* ctx, int object_id, float* host_out, size_t bytes);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * A request is one edit plus one camera.  Edits are applied to the served
+ * scene in submission order, each creating a new version of the edited
+ * object (copy on write), so a request renders exactly the scene state
+ * after its own edit, even while later requests are already editing.
+ * Admission: a request is admitted when a slot is free and its frame and
+ * object version fit under the memory budget; admitted requests are
+ * batched into shared kernel launches (work items from several requests in
+ * one launch) on a pool of streams, so their work overlaps on the device.
+ */
+typedef enum { LF_EDIT_NONE = 0, LF_EDIT_MOVE = 1, LF_EDIT_MATERIAL = 2, LF_EDIT_ENV = 3 } lf_edit_kind;
+
+typedef struct {
+  int kind;          /* lf_edit_kind */
+  int object_id;     /* MOVE / MATERIAL */
+  float R[9], t[3];  /* MOVE: x -> R x + t applied to the object's current pose */
+  float albedo[3];   /* MATERIAL: new base colour (if set_albedo) */
+  float metallic, roughness; /* MATERIAL: new values when >= 0 */
+  int set_albedo;
+  int env_id;        /* ENV: environment used from this request on */
+} lf_edit;
+
+typedef struct {
+  lf_edit edit;
+  lf_camera cam;
+  int spp;
+  uint64_t seed;
+} lf_request;
+
+typedef struct {
+  double t_submit, t_admit, t_start, t_done; /* seconds, steady clock */
+  unsigned long long rays;
+} lf_timing;
+
+typedef struct lf_serve lf_serve;
+
+/* Create a server over the context's built scene and environments.
+ * mem_budget_bytes bounds frame + version memory of in-flight requests. */
+lf_status lf_serve_create(lf_ctx* ctx, size_t mem_budget_bytes, int max_slots, int n_streams, lf_serve** out);
+/* Enqueue a request (host copy); returns its ticket.  Never blocks. */
+lf_status lf_serve_submit(lf_serve* srv, const lf_request* req, uint64_t* ticket);
+/* done = 1 when finished; then frame_host (width*height*3 floats, may be
+ * NULL) receives the image and timing (may be NULL) the timestamps. */
+lf_status lf_serve_poll(lf_serve* srv, uint64_t ticket, int* done, float* frame_host, size_t frame_floats,
+                        lf_timing* timing);
+/* Block until the ticket is done or timeout_ms passes (LF_ERR_TIMEOUT). */
+lf_status lf_serve_wait(lf_serve* srv, uint64_t ticket, int timeout_ms);
+lf_status lf_serve_destroy(lf_serve* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIGHTFUSE_H */

@@ -1,0 +1,337 @@
+// Adjoint of the renderer under path replay (Sec. 3.3).
+//
+// k_shade_backward replays every (pixel, sample) with the same Philox
+// uniforms, re-traces its shadow and continuation rays, keeps the sampled
+// directions, pdfs, MIS weights, visibilities and the secondary record
+// fixed, and differentiates Eq. 11 with respect to the primary record
+// (normal, base colour, metallic, roughness, final transmittance) and every
+// environment lookup.  k_trace_backward then re-traverses each primary ray
+// back to front from the stored final transmittance and stop key, recovers
+// T_j = T_{j+1} / (1 - alpha_j) and scatters the adjoint of Eq. 6-7 to the
+// surfel parameters.
+#include "lf_kernels.h"
+
+namespace lf {
+
+constexpr int TB = 128;
+constexpr int G = 8;
+constexpr int STACK_SMEM = TB * STACK * (int)sizeof(int);
+
+__device__ __forceinline__ void load_instances_b(Inst* dst, const Inst* src, int n) {
+  const float4* s = reinterpret_cast<const float4*>(src);
+  float4* d = reinterpret_cast<float4*>(dst);
+  for (int i = threadIdx.x; i < n * 4; i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
+// d_env += v at the four bilinear texels of direction w.
+__device__ __forceinline__ void env_scatter(const EnvDev& e, float* __restrict__ d_env, float3 w, float3 v) {
+  if (!d_env) return;
+  const Bilin b = env_bilinear(e, w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (b.w[k] == 0.0f) continue;
+    float* t = d_env + 3 * b.idx[k];
+    atomicAdd(t + 0, b.w[k] * v.x);
+    atomicAdd(t + 1, b.w[k] * v.y);
+    atomicAdd(t + 2, b.w[k] * v.z);
+  }
+}
+
+struct RecordGrad {
+  float3 n, a;
+  float m, r;
+};
+
+// Replays one (pixel, sample) and accumulates its forward value into `sum`
+// and the adjoint of gc . value into `rg` and d_env.
+__device__ __forceinline__ void shade_sample_adjoint(const TraceArgs& a, const Inst* insts, const float3 x,
+                                                     const float3 n, const float3 al, const float m, const float r,
+                                                     const float3 dir, uint32_t pixel, int s, uint32_t k0,
+                                                     uint32_t k1, int* stack, float3 gc, float* d_env,
+                                                     float3& sum, RecordGrad& rg) {
+  const DevParams& P = a.P;
+  Counters cnt;
+  unsigned comp = 0;
+  const float3 wo = -dir;
+  const float3 xs = x + n * P.ray_offset;
+  const float ps = P.brdf_mode == 1 ? 0.0f : P.p_spec;
+  float u[9];
+  sample_uniforms(pixel, (uint32_t)s, k0, k1, u);
+  if (P.sampling_mode != 1) {
+    float3 we;
+    float pe;
+    env_sample(a.env, u[0], u[1], we, pe);
+    const float ce = dot3(n, we);
+    if (ce > 0.0f && pe > 0.0f) {
+      const float Ve = trace_shadow(insts, a.n_inst, xs, we, P, stack, TB, a.status, cnt);
+      const float pb = pdf_bsdf(n, wo, we, r, ps);
+      const float wenv = P.sampling_mode == 2 ? 1.0f : pe * pe / (pe * pe + pb * pb);
+      const float kk = Ve * wenv / pe;
+      const float3 f = brdf_eval(n, wo, we, al, m, r, P.brdf_mode);
+      const float3 E = env_lookup(a.env, we);
+      add3(sum, mul3(f, E) * (ce * kk));
+      brdf_adjoint(n, wo, we, al, m, r, P.brdf_mode, mul3(gc, E) * (ce * kk), rg.n, rg.a, rg.m, rg.r);
+      add3(rg.n, we * (dot3(gc, mul3(f, E)) * kk));
+      env_scatter(a.env, d_env, we, mul3(gc, f) * (ce * kk));
+    }
+  }
+  const float3 wi = (u[2] < ps) ? sample_ggx(n, wo, r, u[3], u[4]) : sample_cos(n, u[3], u[4]);
+  const float ci = dot3(n, wi);
+  const float pb = pdf_bsdf(n, wo, wi, r, ps);
+  if (!(ci > 0.0f && pb > 0.0f)) return;
+  const float pei = env_pdf(a.env, wi);
+  const float wb = P.sampling_mode == 1 ? 1.0f : pb * pb / (pb * pb + pei * pei);
+  Surface s2;
+  trace_composite(insts, a.n_inst, xs, wi, P, stack, TB, a.status, cnt, s2, comp);
+  float3 inc = P.sampling_mode == 2 ? f3(0.f, 0.f, 0.f) : env_lookup(a.env, wi) * (wb * s2.T);
+  float3 wq[2], fk[2];
+  bool qok[2] = {false, false};
+  if (s2.hits > 0) {
+    const float3 n2 = s2.n, wo2 = -wi;
+    const float co2 = dot3(n2, wo2);
+    const float3 xs2 = s2.x + n2 * P.ray_offset;
+#pragma unroll
+    for (int qq = 0; qq < 2; ++qq) {
+      float pq;
+      env_sample(a.env, u[5 + 2 * qq], u[6 + 2 * qq], wq[qq], pq);
+      const float cq = dot3(n2, wq[qq]);
+      if (!(cq > 0.0f && co2 > 0.0f && pq > 0.0f)) continue;
+      const float Vq = trace_shadow(insts, a.n_inst, xs2, wq[qq], P, stack, TB, a.status, cnt);
+      fk[qq] = brdf_eval(n2, wo2, wq[qq], s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f * Vq / pq);
+      qok[qq] = true;
+      add3(inc, mul3(fk[qq], env_lookup(a.env, wq[qq])));
+    }
+  }
+  const float3 f = brdf_eval(n, wo, wi, al, m, r, P.brdf_mode);
+  const float3 beta = f * (ci / pb);
+  add3(sum, mul3(beta, inc));
+  const float3 gbeta = mul3(gc, inc);
+  brdf_adjoint(n, wo, wi, al, m, r, P.brdf_mode, gbeta * (ci / pb), rg.n, rg.a, rg.m, rg.r);
+  add3(rg.n, wi * (dot3(gbeta, f) / pb));
+  const float3 ginc = mul3(gc, beta);
+  if (P.sampling_mode != 2) env_scatter(a.env, d_env, wi, ginc * (wb * s2.T));
+#pragma unroll
+  for (int qq = 0; qq < 2; ++qq)
+    if (qok[qq]) env_scatter(a.env, d_env, wq[qq], mul3(ginc, fk[qq]));
+}
+
+__global__ void __launch_bounds__(TB) k_shade_backward(TraceArgs a, const float* __restrict__ gbuf, int n_pix,
+                                                       int spp, uint32_t k0, uint32_t k1,
+                                                       const float* __restrict__ dL_drgb, float* __restrict__ sg,
+                                                       float* __restrict__ d_env) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  extern __shared__ int s_stack[];
+  load_instances_b(s_inst, a.insts, a.n_inst);
+  const int p = blockIdx.x * (TB / G) + threadIdx.x / G, lane = threadIdx.x % G;
+  const bool valid = p < n_pix;
+  const size_t P = (size_t)n_pix;
+  float3 sum = f3(0.f, 0.f, 0.f);
+  RecordGrad rg;
+  rg.n = rg.a = f3(0.f, 0.f, 0.f);
+  rg.m = rg.r = 0.f;
+  float T = 1.0f;
+  float3 dir = f3(0.f, 0.f, 1.f), g = f3(0.f, 0.f, 0.f);
+  if (valid) {
+    const float* gb = gbuf + p;
+    T = __ldg(gb + LF_CH_T * P);
+    const int hits = (int)__ldg(gb + LF_CH_HITS * P);
+    dir = f3(__ldg(gb + LF_CH_DIR * P), __ldg(gb + (LF_CH_DIR + 1) * P), __ldg(gb + (LF_CH_DIR + 2) * P));
+    const float3 n = f3(__ldg(gb + LF_CH_N * P), __ldg(gb + (LF_CH_N + 1) * P), __ldg(gb + (LF_CH_N + 2) * P));
+    g = f3(__ldg(dL_drgb + 3 * p), __ldg(dL_drgb + 3 * p + 1), __ldg(dL_drgb + 3 * p + 2));
+    if (hits > 0 && dot3(n, -dir) > 0.0f) {
+      const float3 x = f3(__ldg(gb + LF_CH_X * P), __ldg(gb + (LF_CH_X + 1) * P), __ldg(gb + (LF_CH_X + 2) * P));
+      const float3 al = f3(__ldg(gb + LF_CH_A * P), __ldg(gb + (LF_CH_A + 1) * P), __ldg(gb + (LF_CH_A + 2) * P));
+      const float m = __ldg(gb + LF_CH_M * P), r = __ldg(gb + LF_CH_R * P);
+      const float3 gc = g * ((1.0f - T) / (float)spp);
+      for (int s = lane; s < spp; s += G)
+        shade_sample_adjoint(a, s_inst, x, n, al, m, r, dir, (uint32_t)p, s, k0, k1, s_stack + threadIdx.x, gc,
+                             d_env, sum, rg);
+    }
+  }
+  float v[11] = {sum.x, sum.y, sum.z, rg.n.x, rg.n.y, rg.n.z, rg.a.x, rg.a.y, rg.a.z, rg.m, rg.r};
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+  }
+  if (valid && lane == 0) {
+    const float3 Ed = env_lookup(a.env, dir);
+    const float inv_spp = 1.0f / (float)spp;
+    const float gT = g.x * (Ed.x - v[0] * inv_spp) + g.y * (Ed.y - v[1] * inv_spp) + g.z * (Ed.z - v[2] * inv_spp);
+    env_scatter(a.env, d_env, dir, g * T);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sg[k * P + p] = v[3 + k];
+    sg[8 * P + p] = gT;
+  }
+}
+
+// Adjoint of Eq. 6 for one hit, scattered to the raw surfel parameters.
+__device__ __forceinline__ void surfel_adjoint(const SceneDev& sc, int id, float3 o, float3 d, const DevParams& P,
+                                               float g_alpha, float3 g_x, float g_t_direct, float3 g_n, float3 g_a,
+                                               float g_m, float g_r, float* __restrict__ d_surfel) {
+  const float3 mu = f3(sc.mu[3 * id], sc.mu[3 * id + 1], sc.mu[3 * id + 2]);
+  const float3 tu = f3(sc.tu[3 * id], sc.tu[3 * id + 1], sc.tu[3 * id + 2]);
+  const float3 tv = f3(sc.tv[3 * id], sc.tv[3 * id + 1], sc.tv[3 * id + 2]);
+  const float su = sc.scale[2 * id], sv = sc.scale[2 * id + 1], op = sc.opacity[id];
+  const float3 c = cross3(tu, tv);
+  const float cl = sqrtf(dot3(c, c));
+  const float3 nh = c * (1.0f / cl);
+  const float den = dot3(d, c);
+  const float3 pm = mu - o;
+  const float t = dot3(pm, c) / den;
+  const float3 q = d * t - pm;  // x - mu
+  const float u = dot3(q, tu) / su, v = dot3(q, tv) / sv;
+  const float Gs = expf(-0.5f * (u * u + v * v));
+  const float oG = op * Gs;
+  const bool capped = oG > P.alpha_max;
+  const float g_o = capped ? 0.0f : g_alpha * Gs;
+  const float g_r2 = capped ? 0.0f : -0.5f * g_alpha * oG;
+  const float g_u = 2.0f * u * g_r2, g_v = 2.0f * v * g_r2;
+  const float3 g_q = tu * (g_u / su) + tv * (g_v / sv);
+  float3 g_tu = q * (g_u / su), g_tv = q * (g_v / sv);
+  const float g_su = -g_u * u / su, g_sv = -g_v * v / sv;
+  const float g_t = g_t_direct + dot3(g_x, d) + dot3(g_q, d);
+  const float3 g_mu = c * (g_t / den) - g_q;
+  float3 g_c = q * (-g_t / den);
+  const float3 g_nh = dot3(d, nh) < 0.0f ? g_n : -g_n;
+  add3(g_c, (g_nh - nh * dot3(nh, g_nh)) * (1.0f / cl));
+  add3(g_tu, cross3(tv, g_c));
+  add3(g_tv, cross3(g_c, tu));
+  float* o17 = d_surfel + (size_t)LF_G_STRIDE * id;
+  atomicAdd(o17 + 0, g_mu.x); atomicAdd(o17 + 1, g_mu.y); atomicAdd(o17 + 2, g_mu.z);
+  atomicAdd(o17 + 3, g_tu.x); atomicAdd(o17 + 4, g_tu.y); atomicAdd(o17 + 5, g_tu.z);
+  atomicAdd(o17 + 6, g_tv.x); atomicAdd(o17 + 7, g_tv.y); atomicAdd(o17 + 8, g_tv.z);
+  atomicAdd(o17 + 9, g_su); atomicAdd(o17 + 10, g_sv);
+  atomicAdd(o17 + 11, g_o);
+  atomicAdd(o17 + 12, g_a.x); atomicAdd(o17 + 13, g_a.y); atomicAdd(o17 + 14, g_a.z);
+  atomicAdd(o17 + 15, g_m);
+  atomicAdd(o17 + 16, g_r);
+}
+
+__global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
+                                                       const float* __restrict__ gbuf,
+                                                       const float* __restrict__ sg,
+                                                       const float* __restrict__ gg, float* __restrict__ d_surfel,
+                                                       float* __restrict__ d_env) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  extern __shared__ int s_stack[];
+  load_instances_b(s_inst, a.insts, a.n_inst);
+  const int x = blockIdx.x * 16 + (threadIdx.x & 15), y = blockIdx.y * 8 + (threadIdx.x >> 4);
+  if (x >= cam.W || y >= cam.H) return;
+  const int p = y * cam.W + x;
+  const size_t P = (size_t)cam.W * cam.H;
+  const DevParams& Pm = a.P;
+  const float* gb = gbuf + p;
+  auto ch = [&](int c) { return __ldg(gb + (size_t)c * P); };
+  auto up = [&](int c) { return gg ? __ldg(gg + (size_t)c * P + p) : 0.0f; };
+  const float3 o = cam.eye;
+  const float3 d = f3(ch(LF_CH_DIR), ch(LF_CH_DIR + 1), ch(LF_CH_DIR + 2));
+  const float T = ch(LF_CH_T), W = ch(LF_CH_W), depth = ch(LF_CH_DEPTH), nlen = ch(LF_CH_NLEN);
+  const float3 xb = f3(ch(LF_CH_X), ch(LF_CH_X + 1), ch(LF_CH_X + 2));
+  const float3 nb = f3(ch(LF_CH_N), ch(LF_CH_N + 1), ch(LF_CH_N + 2));
+  const float3 ab = f3(ch(LF_CH_A), ch(LF_CH_A + 1), ch(LF_CH_A + 2));
+  const float mb = ch(LF_CH_M), rb = ch(LF_CH_R);
+  const int hits = (int)ch(LF_CH_HITS);
+  // upstream gradients on the record
+  float3 g_n = f3(up(LF_CH_N), up(LF_CH_N + 1), up(LF_CH_N + 2));
+  float3 g_a = f3(up(LF_CH_A), up(LF_CH_A + 1), up(LF_CH_A + 2));
+  float g_m = up(LF_CH_M), g_r = up(LF_CH_R), g_T = up(LF_CH_T);
+  const float g_W = up(LF_CH_W), g_depth = up(LF_CH_DEPTH);
+  const float3 g_x = f3(up(LF_CH_X), up(LF_CH_X + 1), up(LF_CH_X + 2));
+  const float3 g_rho = f3(up(LF_CH_RHO), up(LF_CH_RHO + 1), up(LF_CH_RHO + 2));
+  if (sg) {
+    g_n = g_n + f3(__ldg(sg + 0 * P + p), __ldg(sg + 1 * P + p), __ldg(sg + 2 * P + p));
+    g_a = g_a + f3(__ldg(sg + 3 * P + p), __ldg(sg + 4 * P + p), __ldg(sg + 5 * P + p));
+    g_m += __ldg(sg + 6 * P + p);
+    g_r += __ldg(sg + 7 * P + p);
+    g_T += __ldg(sg + 8 * P + p);
+  }
+  // rho = sum w a + T E(d)
+  if (gg) {
+    const float3 Ed = env_lookup(a.env, d);
+    g_T += dot3(g_rho, Ed);
+    env_scatter(a.env, d_env, d, g_rho * T);
+  }
+  if (hits <= 0) return;
+  const float inv = 1.0f / (W + Pm.eps_w);
+  const float3 gSx = g_x * inv, gSa = g_a * inv + g_rho;
+  const float gSt = g_depth * inv, gSm = g_m * inv, gSr = g_r * inv;
+  float3 gmv = f3(0.f, 0.f, 0.f), mv = f3(0.f, 0.f, 0.f);
+  if (nlen >= 1e-12f) {
+    gmv = (g_n - nb * dot3(nb, g_n)) * (1.0f / nlen);
+    mv = nb * nlen;
+  }
+  const float3 gSn = gmv * inv;
+  const float gW = g_W - inv * (dot3(g_x, xb) + g_depth * depth + dot3(g_a, ab) + g_m * mb + g_r * rb + dot3(gmv, mv));
+  float S = g_T * T;
+  float Tn = T;
+  int remaining = hits;
+  float bound_t = ch(LF_CH_TSTOP);
+  int bound_id = (int)ch(LF_CH_IDSTOP);
+  bool inclusive = true;
+  FarK kb;
+  kb.insts = s_inst;
+  kb.o = o;
+  kb.d = d;
+  kb.P = Pm;
+  const Ray ray = make_ray(o, d);
+  Counters cnt;
+  for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
+    kb.reset(bound_t, bound_id, inclusive);
+    traverse(s_inst, a.n_inst, ray, kb, s_stack + threadIdx.x, TB, a.status, cnt);
+    const int n = kb.cnt;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (j < n && remaining > 0) {
+        const int code = kb.bc[j];
+        const Inst& I = s_inst[code >> 24];
+        const int l = code & 0xffffff;
+        const float4 g0 = __ldg(I.geo + 3 * l), g1 = __ldg(I.geo + 3 * l + 1), g2 = __ldg(I.geo + 3 * l + 2);
+        const float4 mt = __ldg(I.mat + l);
+        float t, alpha;
+        hit_surfel(g0, g1, g2, o, d, Pm, t, alpha);
+        const float3 nj = record_normal(g1, g2, d);
+        const float3 xj = o + d * t;
+        const float Tj = Tn / (1.0f - alpha);
+        const float w = Tj * alpha;
+        const float gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y +
+                         gSa.z * mt.z + gSm * mt.w + gSr * g2.w;
+        const float g_alpha = Tj * gw - S / (1.0f - alpha);
+        S += gw * w;
+        Tn = Tj;
+        surfel_adjoint(sc, __float_as_int(g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
+                       gSr * w, d_surfel);
+        --remaining;
+      }
+    }
+    if (remaining > 0) {
+      if (n < K) {  // the forward composited more hits than the re-traversal finds
+        report(a.status, LF_ERR_ROUND_LIMIT);
+        break;
+      }
+      bound_t = kb.bt[K - 1];
+      bound_id = code_id(s_inst, kb.bc[K - 1]);
+      inclusive = false;
+    }
+  }
+}
+
+cudaError_t launch_shade_backward(const TraceArgs& a, const float* gbuf, int n_pix, int spp, uint32_t k0,
+                                  uint32_t k1, const float* dL_drgb, float* shade_grad, float* d_env,
+                                  cudaStream_t st) {
+  const int ppb = TB / G;
+  k_shade_backward<<<(n_pix + ppb - 1) / ppb, TB, STACK_SMEM, st>>>(a, gbuf, n_pix, spp, k0, k1, dL_drgb,
+                                                                   shade_grad, d_env);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
+                                  const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
+                                  cudaStream_t st) {
+  dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
+  k_trace_backward<<<grid, TB, STACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env);
+  return cudaGetLastError();
+}
+
+}  // namespace lf

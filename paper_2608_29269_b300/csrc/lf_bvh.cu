@@ -1,0 +1,460 @@
+// Two-level LBVH build and refit (one BLAS per object, Eq. 2), the rigid
+// object transform, and the environment importance-sampling tables.
+#include <climits>
+
+#include "lf_kernels.h"
+
+namespace lf {
+
+// ---------------------------------------------------------------- AABB + bounds
+// Support ellipse of surfel i at radius R = sqrt(support_r2): in axis k its
+// half extent is R * sqrt((s_u tu_k)^2 + (s_v tv_k)^2).  Boxes are padded by a
+// small relative margin so that FP32 slab tests never miss an accepted hit.
+__device__ __forceinline__ void surfel_box(const SceneDev& s, int i, float R, float3& lo, float3& hi) {
+  const float su = s.scale[2 * i], sv = s.scale[2 * i + 1];
+  float m[3], e[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m[k] = s.mu[3 * i + k];
+    const float a = su * s.tu[3 * i + k], b = sv * s.tv[3 * i + k];
+    e[k] = R * sqrtf(a * a + b * b);
+  }
+  float p0 = 1e-5f * (1.0f + fabsf(m[0]) + e[0]), p1 = 1e-5f * (1.0f + fabsf(m[1]) + e[1]),
+        p2 = 1e-5f * (1.0f + fabsf(m[2]) + e[2]);
+  lo = f3(m[0] - e[0] - p0, m[1] - e[1] - p1, m[2] - e[2] - p2);
+  hi = f3(m[0] + e[0] + p0, m[1] + e[1] + p1, m[2] + e[2] + p2);
+}
+
+__device__ __forceinline__ int ordered(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Centroid bounds per object: grid.y = object, blocks stride over its range.
+__global__ void k_object_bounds(SceneDev s, const int* __restrict__ offsets, int* __restrict__ bounds) {
+  const int obj = blockIdx.y;
+  const int beg = offsets[obj], end = offsets[obj + 1];
+  float lo[3] = {BIG_F, BIG_F, BIG_F}, hi[3] = {-BIG_F, -BIG_F, -BIG_F};
+  for (int i = beg + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float v = s.mu[3 * i + k];
+      lo[k] = fminf(lo[k], v);
+      hi[k] = fmaxf(hi[k], v);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+    }
+  }
+  if ((threadIdx.x & 31) == 0 && end > beg) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(bounds + 6 * obj + k, ordered(lo[k]));
+      atomicMax(bounds + 6 * obj + 3 + k, ordered(hi[k]));
+    }
+  }
+}
+
+__global__ void k_bounds_init(int* bounds, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) bounds[i] = (i % 6) < 3 ? ordered(BIG_F) : ordered(-BIG_F);
+}
+
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__device__ __forceinline__ int object_of(const int* offsets, int n_obj, int i) {
+  int lo = 0, hi = n_obj - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// 30-bit Morton code of the surfel centre in its object's centroid bounds.
+__global__ void k_morton(SceneDev s, const int* __restrict__ offsets, int n_obj, const int* __restrict__ bounds,
+                         unsigned* __restrict__ keys, unsigned* __restrict__ vals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int obj = object_of(offsets, n_obj, i);
+  unsigned c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float lo = unordered(bounds[6 * obj + k]), hi = unordered(bounds[6 * obj + 3 + k]);
+    const float ext = hi - lo;
+    float u = ext > 0.0f ? (s.mu[3 * i + k] - lo) / ext : 0.5f;
+    u = fminf(fmaxf(u, 0.0f), 1.0f);
+    c[k] = min(1023u, (unsigned)(u * 1024.0f));
+  }
+  keys[i] = (spread10(c[0]) << 2) | (spread10(c[1]) << 1) | spread10(c[2]);
+  vals[i] = (unsigned)i;
+}
+
+// ---------------------------------------------------------------- radix sort
+// One stable LSD pass over 8-bit digits: per-tile histograms, a global
+// digit-major exclusive scan, and a scatter that ranks equal digits within a
+// warp with __match_any_sync and across warps with per-warp counters.
+constexpr int RS_THREADS = 256, RS_ITEMS = 16, RS_TILE = RS_THREADS * RS_ITEMS, RS_WARPS = RS_THREADS / 32;
+
+__device__ __forceinline__ unsigned rs_digit(unsigned key, unsigned val, int shift, const int* offsets, int n_obj) {
+  if (shift < 0) return (unsigned)object_of(offsets, n_obj, (int)val);  // object pass
+  return (key >> shift) & 255u;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const unsigned* __restrict__ keys,
+                                                           const unsigned* __restrict__ vals, int n, int shift,
+                                                           const int* offsets, int n_obj, unsigned* counts,
+                                                           int n_tiles) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * RS_TILE;
+  for (int k = threadIdx.x; k < RS_TILE; k += RS_THREADS) {
+    const int i = base + k;
+    if (i < n) atomicAdd(&h[rs_digit(keys[i], vals[i], shift, offsets, n_obj)], 1u);
+  }
+  __syncthreads();
+  counts[threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of counts[256 * n_tiles] in one block (digit-major order).
+__global__ void __launch_bounds__(1024) k_radix_scan(unsigned* counts, int total) {
+  __shared__ unsigned part[1024];
+  const int per = (total + 1023) / 1024;
+  const int beg = threadIdx.x * per, end = min(total, beg + per);
+  unsigned s = 0;
+  for (int i = beg; i < end; ++i) s += counts[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned run = part[threadIdx.x] - s;
+  for (int i = beg; i < end; ++i) {
+    unsigned c = counts[i];
+    counts[i] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const unsigned* __restrict__ keys_in,
+                                                              const unsigned* __restrict__ vals_in,
+                                                              unsigned* __restrict__ keys_out,
+                                                              unsigned* __restrict__ vals_out, int n, int shift,
+                                                              const int* offsets, int n_obj,
+                                                              const unsigned* __restrict__ offs, int n_tiles) {
+  __shared__ unsigned cnt[RS_WARPS][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < RS_WARPS * 256; k += RS_THREADS) (&cnt[0][0])[k] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * RS_TILE + warp * (RS_ITEMS * 32);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned pos[RS_ITEMS], dig[RS_ITEMS], key[RS_ITEMS], val[RS_ITEMS];
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const int i = base + it * 32 + lane;
+    const bool valid = i < n;
+    key[it] = valid ? keys_in[i] : 0u;
+    val[it] = valid ? vals_in[i] : 0u;
+    const unsigned d = valid ? rs_digit(key[it], val[it], shift, offsets, n_obj) : 256u;
+    dig[it] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned rank = __popc(peers & lt_mask);
+    const unsigned before = valid ? cnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && rank == 0) cnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+    pos[it] = before + rank;
+  }
+  __syncthreads();
+  {  // exclusive prefix over warps, one digit per thread
+    const int d = threadIdx.x;
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      unsigned c = cnt[w][d];
+      cnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const int i = base + it * 32 + lane;
+    if (i < n) {
+      const unsigned d = dig[it];
+      const unsigned dst = offs[d * n_tiles + blockIdx.x] + cnt[warp][d] + pos[it];
+      keys_out[dst] = key[it];
+      vals_out[dst] = val[it];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Karras hierarchy
+// Longest common prefix of keys i and j of one object (duplicates ordered by
+// index), -1 outside [0, n).
+__device__ __forceinline__ int delta(const unsigned* k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const unsigned a = k[i], b = k[j];
+  if (a == b) return 32 + __clz((unsigned)(i ^ j));
+  return __clz(a ^ b);
+}
+
+__global__ void k_hierarchy(const unsigned* __restrict__ skeys, const int* __restrict__ leaf_off,
+                            const int* __restrict__ node_off, int n_obj, int n_nodes_total,
+                            float4* __restrict__ nodes, int* __restrict__ leaf_parent,
+                            int* __restrict__ node_parent) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_nodes_total) return;
+  const int obj = object_of(node_off, n_obj, g);
+  const int i = g - node_off[obj];
+  const int lb = leaf_off[obj], n = leaf_off[obj + 1] - lb, nb = node_off[obj];
+  const unsigned* k = skeys + lb;
+  const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(k, n, i, i - d);
+  int lmax = 2;
+  while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta(k, n, i, j);
+  int s = 0;
+  for (int div = 2;; div <<= 1) {
+    const int t = (l + div - 1) / div;
+    if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    if (t <= 1) break;
+  }
+  const int gamma = i + s * d + min(d, 0);
+  const int left = (min(i, j) == gamma) ? ~gamma : gamma;
+  const int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  nodes[4 * (nb + i) + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
+  if (left < 0) leaf_parent[lb + gamma] = (i << 1) | 0; else node_parent[nb + gamma] = (i << 1) | 0;
+  if (right < 0) leaf_parent[lb + gamma + 1] = (i << 1) | 1; else node_parent[nb + gamma + 1] = (i << 1) | 1;
+  if (i == 0) node_parent[nb] = -1;
+}
+
+// ---------------------------------------------------------------- pack + fit
+__device__ __forceinline__ void write_child_box(float4* node, int side, float3 lo, float3 hi) {
+  float* f = reinterpret_cast<float*>(node);
+  const int b = side == 0 ? 0 : 6;
+  __stcg(f + b + 0, lo.x); __stcg(f + b + 1, lo.y); __stcg(f + b + 2, lo.z);
+  __stcg(f + b + 3, hi.x); __stcg(f + b + 4, hi.y); __stcg(f + b + 5, hi.z);
+}
+
+// One thread per leaf of the selected objects: pack the surfel's records,
+// compute its box and propagate boxes to the root; the second child to
+// arrive at a node forms the union (atomic visit counter per node).
+__global__ void k_pack_fit(SceneDev s, FitArgs a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_leaves) return;
+  const int L = a.first_leaf + g;
+  const int obj = object_of(a.leaf_off, a.n_obj, L);
+  const int lb = a.leaf_off[obj], n = a.leaf_off[obj + 1] - lb, nb = a.node_off[obj];
+  const int i = (int)a.sorted_ids[L];
+  // pack
+  const float su = s.scale[2 * i], sv = s.scale[2 * i + 1];
+  const float3 mu = f3(s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]);
+  const float3 tu = f3(s.tu[3 * i], s.tu[3 * i + 1], s.tu[3 * i + 2]);
+  const float3 tv = f3(s.tv[3 * i], s.tv[3 * i + 1], s.tv[3 * i + 2]);
+  a.geo[3 * L + 0] = make_float4(mu.x, mu.y, mu.z, s.opacity[i]);
+  a.geo[3 * L + 1] = make_float4(tu.x / su, tu.y / su, tu.z / su, __int_as_float(i));
+  a.geo[3 * L + 2] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, s.roughness[i]);
+  a.mat[L] = make_float4(s.albedo[3 * i], s.albedo[3 * i + 1], s.albedo[3 * i + 2], s.metallic[i]);
+  float3 lo, hi;
+  surfel_box(s, i, a.R, lo, hi);
+  Inst* inst = a.insts + obj;
+  if (n == 1) {
+    inst->lo[0] = lo.x; inst->lo[1] = lo.y; inst->lo[2] = lo.z;
+    inst->hi[0] = hi.x; inst->hi[1] = hi.y; inst->hi[2] = hi.z;
+    return;
+  }
+  int link = a.leaf_parent[L];
+  for (int guard = 0; guard < n; ++guard) {
+    if (link < 0 || (link >> 1) >= n - 1) {  // malformed hierarchy: leave the boxes, report
+      report(a.status, LF_ERR_INVALID);
+      return;
+    }
+    const int p = link >> 1, side = link & 1;
+    float4* node = a.nodes + 4 * (nb + p);
+    write_child_box(node, side, lo, hi);
+    __threadfence();
+    if (atomicAdd(a.flags + nb + p, 1) == 0) return;
+    __threadfence();
+    const float* f = reinterpret_cast<const float*>(node);
+    lo = f3(fminf(__ldcg(f + 0), __ldcg(f + 6)), fminf(__ldcg(f + 1), __ldcg(f + 7)), fminf(__ldcg(f + 2), __ldcg(f + 8)));
+    hi = f3(fmaxf(__ldcg(f + 3), __ldcg(f + 9)), fmaxf(__ldcg(f + 4), __ldcg(f + 10)), fmaxf(__ldcg(f + 5), __ldcg(f + 11)));
+    if (p == 0) {
+      inst->lo[0] = lo.x; inst->lo[1] = lo.y; inst->lo[2] = lo.z;
+      inst->hi[0] = hi.x; inst->hi[1] = hi.y; inst->hi[2] = hi.z;
+      return;
+    }
+    link = a.node_parent[nb + p];
+  }
+  report(a.status, LF_ERR_INVALID);
+}
+
+// ---------------------------------------------------------------- rigid transform
+__global__ void k_rigid(SceneDev s, int beg, int end, Mat34 T) {
+  const int i = beg + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= end) return;
+  float m[3] = {s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]};
+  float u[3] = {s.tu[3 * i], s.tu[3 * i + 1], s.tu[3 * i + 2]};
+  float v[3] = {s.tv[3 * i], s.tv[3 * i + 1], s.tv[3 * i + 2]};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    s.mu[3 * i + r] = T.R[3 * r] * m[0] + T.R[3 * r + 1] * m[1] + T.R[3 * r + 2] * m[2] + T.t[r];
+    s.tu[3 * i + r] = T.R[3 * r] * u[0] + T.R[3 * r + 1] * u[1] + T.R[3 * r + 2] * u[2];
+    s.tv[3 * i + r] = T.R[3 * r] * v[0] + T.R[3 * r + 1] * v[1] + T.R[3 * r + 2] * v[2];
+  }
+}
+
+__global__ void k_material(SceneDev s, int beg, int end, float3 rgb, int set_rgb, float metal, float rough) {
+  const int i = beg + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= end) return;
+  if (set_rgb) { s.albedo[3 * i] = rgb.x; s.albedo[3 * i + 1] = rgb.y; s.albedo[3 * i + 2] = rgb.z; }
+  if (metal >= 0.0f) s.metallic[i] = metal;
+  if (rough >= 0.0f) s.roughness[i] = rough;
+}
+
+// ---------------------------------------------------------------- environment tables
+// Texel weight (Rec.709 luminance + 1e-6) * sin(theta at the row centre) in
+// FP64 with explicit rounding (no contraction); sequential sums per row.
+__global__ void k_env_rows(const float* __restrict__ rgb, const double* __restrict__ sin_row, int H, int W,
+                           double* __restrict__ rowsum, float* __restrict__ pmf_col, float* __restrict__ cdf_col) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= H) return;
+  const double st = sin_row[r];
+  double acc = 0.0;
+  for (int c = 0; c < W; ++c) {
+    const float* t = rgb + 3 * ((size_t)r * W + c);
+    double lum = __dadd_rn(__dmul_rn(0.2126, (double)t[0]), __dmul_rn(0.7152, (double)t[1]));
+    lum = __dadd_rn(lum, __dmul_rn(0.0722, (double)t[2]));
+    lum = __dadd_rn(lum, 1e-6);
+    acc = __dadd_rn(acc, __dmul_rn(lum, st));
+  }
+  rowsum[r] = acc;
+  double pc = 0.0;
+  for (int c = 0; c < W; ++c) {
+    const float* t = rgb + 3 * ((size_t)r * W + c);
+    double lum = __dadd_rn(__dmul_rn(0.2126, (double)t[0]), __dmul_rn(0.7152, (double)t[1]));
+    lum = __dadd_rn(lum, __dmul_rn(0.0722, (double)t[2]));
+    lum = __dadd_rn(lum, 1e-6);
+    const double w = __dmul_rn(lum, st);
+    pc = __dadd_rn(pc, w);
+    pmf_col[(size_t)r * W + c] = (float)__ddiv_rn(w, acc);
+    cdf_col[(size_t)r * W + c] = (float)__ddiv_rn(pc, acc);
+  }
+}
+
+__global__ void k_env_marginal(const double* __restrict__ rowsum, int H, float* __restrict__ pmf_row,
+                               float* __restrict__ cdf_row) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double total = 0.0;
+  for (int r = 0; r < H; ++r) total = __dadd_rn(total, rowsum[r]);
+  double pre = 0.0;
+  for (int r = 0; r < H; ++r) {
+    pre = __dadd_rn(pre, rowsum[r]);
+    pmf_row[r] = (float)__ddiv_rn(rowsum[r], total);
+    cdf_row[r] = (float)__ddiv_rn(pre, total);
+  }
+}
+
+__global__ void k_philox(const uint4* __restrict__ ctr, int n, uint32_t k0, uint32_t k1, uint4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_object_bounds(const SceneDev& s, const int* offsets_dev, int n_obj, int max_obj_n, int* bounds,
+                                 cudaStream_t st) {
+  k_bounds_init<<<(6 * n_obj + 127) / 128, 128, 0, st>>>(bounds, 6 * n_obj);
+  dim3 grid(max(1, min(256, (max_obj_n + 255) / 256)), n_obj);
+  k_object_bounds<<<grid, 256, 0, st>>>(s, offsets_dev, bounds);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_morton(const SceneDev& s, const int* offsets_dev, int n_obj, const int* bounds, unsigned* keys,
+                          unsigned* vals, cudaStream_t st) {
+  k_morton<<<(s.n + 255) / 256, 256, 0, st>>>(s, offsets_dev, n_obj, bounds, keys, vals);
+  return cudaGetLastError();
+}
+
+int radix_tiles(int n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+// Sorts (keys, vals) by the 30-bit key, then stably by object of vals.
+// Results end in keys/vals; alt buffers are scratch of the same size.
+cudaError_t launch_radix_sort(unsigned* keys, unsigned* vals, unsigned* keys_alt, unsigned* vals_alt, int n,
+                              const int* offsets_dev, int n_obj, unsigned* counts, cudaStream_t st) {
+  const int tiles = radix_tiles(n);
+  const int shifts[5] = {0, 8, 16, 24, -1};
+  unsigned *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  for (int p = 0; p < 5; ++p) {
+    k_radix_hist<<<tiles, RS_THREADS, 0, st>>>(ki, vi, n, shifts[p], offsets_dev, n_obj, counts, tiles);
+    k_radix_scan<<<1, 1024, 0, st>>>(counts, 256 * tiles);
+    k_radix_scatter<<<tiles, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shifts[p], offsets_dev, n_obj, counts,
+                                                 tiles);
+    unsigned* t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  // five passes: the result is in the alternate buffers; copy back
+  cudaMemcpyAsync(keys, ki, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(vals, vi, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hierarchy(const unsigned* skeys, const int* leaf_off, const int* node_off, int n_obj,
+                             int n_nodes_total, float4* nodes, int* leaf_parent, int* node_parent, cudaStream_t st) {
+  if (n_nodes_total > 0)
+    k_hierarchy<<<(n_nodes_total + 127) / 128, 128, 0, st>>>(skeys, leaf_off, node_off, n_obj, n_nodes_total,
+                                                            nodes, leaf_parent, node_parent);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fit(const SceneDev& s, const FitArgs& a, cudaStream_t st) {
+  if (a.n_leaves > 0) k_pack_fit<<<(a.n_leaves + 127) / 128, 128, 0, st>>>(s, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rigid(const SceneDev& s, int beg, int end, const Mat34& T, cudaStream_t st) {
+  if (end > beg) k_rigid<<<(end - beg + 255) / 256, 256, 0, st>>>(s, beg, end, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int set_rgb, float metal, float rough,
+                            cudaStream_t st) {
+  if (end > beg) k_material<<<(end - beg + 255) / 256, 256, 0, st>>>(s, beg, end, rgb, set_rgb, metal, rough);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, int W, double* rowsum, float* pmf_row,
+                              float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st) {
+  k_env_rows<<<(H + 63) / 64, 64, 0, st>>>(rgb, sin_row, H, W, rowsum, pmf_col, cdf_col);
+  k_env_marginal<<<1, 1, 0, st>>>(rowsum, H, pmf_row, cdf_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st) {
+  if (n > 0)
+    k_philox<<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<const uint4*>(ctr), n, k0, k1,
+                                             reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace lf

@@ -1,0 +1,645 @@
+// Device-side building blocks of the surfel ray tracer (sm_103a).
+//
+// Record layouts (library-owned, in BVH leaf order per object):
+//   geo[3*l+0] = (mu.xyz, opacity)
+//   geo[3*l+1] = (tu/s_u .xyz, surfel id as int bits)
+//   geo[3*l+2] = (tv/s_v .xyz, roughness)
+//   mat[l]     = (albedo.rgb, metallic)
+//   BVH2 node (64 B, child boxes stored in the parent):
+//     n0 = (L.lo.xyz, L.hi.x)  n1 = (L.hi.yz, R.lo.xy)  n2 = (R.lo.z, R.hi.xyz)
+//     n3 = (left code, right code, -, -) ; code >= 0 internal node, code < 0 leaf ~code
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lightfuse.h"
+
+namespace lf {
+
+constexpr int K = LF_KBUF;
+constexpr int STACK = LF_STACK_DEPTH;
+constexpr float PI_F = 3.14159265358979323846f;
+constexpr float INV_PI_F = 0.318309886183790671538f;
+constexpr float INV_2PI_F = 0.159154943091895335769f;
+constexpr float BIG_F = 3.0e38f;
+
+struct DevParams {
+  float T_min, alpha_min, alpha_max, support_r2, eps_w, t_min, ray_offset, p_spec;
+  int max_rounds, brdf_mode, sampling_mode;
+};
+
+// One TLAS entry: an object's BLAS in world space (Eq. 2 after its transform).
+struct __align__(16) Inst {
+  float lo[3];
+  int root;  // child code of the BLAS root (>= 0 node, < 0 leaf ~code); INT_MIN: empty
+  float hi[3];
+  int n_leaves;
+  const float4* nodes;
+  const float4* geo;
+  const float4* mat;
+  int id_base;  // surfel id of the object's first surfel
+  int pad;
+};
+static_assert(sizeof(Inst) == 64, "Inst is 64 bytes");
+
+struct EnvDev {
+  const float* rgb;  // H x W x 3
+  const float* pmf_row;
+  const float* cdf_row;
+  const float* pmf_col;
+  const float* cdf_col;
+  int H, W;
+};
+
+struct CamDev {
+  float3 eye, f, r, u;
+  float sx_scale, sy_scale;  // tan(fovy/2) * aspect, tan(fovy/2)
+  int W, H;
+};
+
+// ------------------------------------------------------------------ status
+__device__ __forceinline__ void report(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ vectors
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul3(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * (1.0f / sqrtf(dot3(a, a))); }
+__device__ __forceinline__ void add3(float3& a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; }
+
+// Correctly rounded, contraction-free forms used by the intersection so that
+// every kernel (forward, shading, adjoint) computes bit-identical hits.
+__device__ __forceinline__ float dot_rn(float3 a, float3 b) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+__device__ __forceinline__ float3 cross_rn(float3 a, float3 b) {
+  return f3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+            __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds, two 32x32->64 products per
+// round, Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// The nine uniforms of (pixel, sample): NEE (0,1), lobe 2, BSDF (3,4),
+// secondary NEE #1 (5,6), #2 (7,8).  Counter (pixel, sample, group, 0).
+__device__ __forceinline__ void sample_uniforms(uint32_t pixel, uint32_t s, uint32_t k0, uint32_t k1, float u[9]) {
+  uint4 a = philox4x32_10(make_uint4(pixel, s, 0u, 0u), k0, k1);
+  uint4 b = philox4x32_10(make_uint4(pixel, s, 1u, 0u), k0, k1);
+  uint4 c = philox4x32_10(make_uint4(pixel, s, 2u, 0u), k0, k1);
+  u[0] = unit24(a.x); u[1] = unit24(a.y); u[2] = unit24(a.z); u[3] = unit24(a.w);
+  u[4] = unit24(b.x); u[5] = unit24(b.y); u[6] = unit24(b.z); u[7] = unit24(b.w);
+  u[8] = unit24(c.x);
+}
+
+// ------------------------------------------------------------------ Eq. 6
+// Plane hit of a packed surfel record; t and alpha~ on acceptance.
+__device__ __forceinline__ bool hit_surfel(const float4 g0, const float4 g1, const float4 g2, const float3 o,
+                                           const float3 d, const DevParams& P, float& t, float& alpha) {
+  const float3 a = f3(g1.x, g1.y, g1.z), b = f3(g2.x, g2.y, g2.z);
+  const float3 c = cross_rn(a, b);
+  const float3 p = f3(__fsub_rn(g0.x, o.x), __fsub_rn(g0.y, o.y), __fsub_rn(g0.z, o.z));
+  t = __fdiv_rn(dot_rn(p, c), dot_rn(d, c));
+  if (!(t > P.t_min) || !(t < BIG_F)) return false;
+  const float3 q = f3(__fmaf_rn(t, d.x, -p.x), __fmaf_rn(t, d.y, -p.y), __fmaf_rn(t, d.z, -p.z));
+  const float u = dot_rn(q, a), v = dot_rn(q, b);
+  const float r2 = __fmaf_rn(u, u, __fmul_rn(v, v));
+  if (!(r2 <= P.support_r2)) return false;
+  alpha = fminf(P.alpha_max, __fmul_rn(g0.w, expf(__fmul_rn(-0.5f, r2))));
+  return alpha >= P.alpha_min;
+}
+
+// Normal of a packed record facing the ray (two-sided surfels).
+__device__ __forceinline__ float3 record_normal(const float4 g1, const float4 g2, const float3 d) {
+  float3 c = cross_rn(f3(g1.x, g1.y, g1.z), f3(g2.x, g2.y, g2.z));
+  float3 n = c * (1.0f / sqrtf(dot3(c, c)));
+  return dot3(d, n) < 0.0f ? n : -n;
+}
+
+// ------------------------------------------------------------------ environment
+struct Bilin {
+  int idx[4];
+  float w[4];
+};
+
+__device__ __forceinline__ void dir_angles(float3 w, float& th, float& ph) {
+  th = acosf(fminf(1.0f, fmaxf(-1.0f, w.y)));
+  ph = atan2f(w.x, -w.z) + PI_F;
+}
+
+__device__ __forceinline__ Bilin env_bilinear(const EnvDev& e, float3 w) {
+  float th, ph;
+  dir_angles(w, th, ph);
+  float u = ph * INV_2PI_F * (float)e.W - 0.5f, v = th * INV_PI_F * (float)e.H - 0.5f;
+  float x0f = floorf(u), y0f = floorf(v);
+  float fx = u - x0f, fy = v - y0f;
+  int x0 = (int)x0f, y0 = (int)y0f;
+  int x0m = ((x0 % e.W) + e.W) % e.W, x1m = (((x0 + 1) % e.W) + e.W) % e.W;
+  int y0c = min(e.H - 1, max(0, y0)), y1c = min(e.H - 1, max(0, y0 + 1));
+  Bilin b;
+  b.idx[0] = y0c * e.W + x0m; b.w[0] = (1.0f - fx) * (1.0f - fy);
+  b.idx[1] = y0c * e.W + x1m; b.w[1] = fx * (1.0f - fy);
+  b.idx[2] = y1c * e.W + x0m; b.w[2] = (1.0f - fx) * fy;
+  b.idx[3] = y1c * e.W + x1m; b.w[3] = fx * fy;
+  return b;
+}
+
+__device__ __forceinline__ float3 env_lookup(const EnvDev& e, float3 w) {
+  Bilin b = env_bilinear(e, w);
+  float3 s = f3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float* t = e.rgb + 3 * b.idx[k];
+    s.x += b.w[k] * __ldg(t);
+    s.y += b.w[k] * __ldg(t + 1);
+    s.z += b.w[k] * __ldg(t + 2);
+  }
+  return s;
+}
+
+// First index i in [0, n) with f[i] > u (f non-decreasing, f[n-1] == 1 > u).
+__device__ __forceinline__ int first_greater(const float* __restrict__ f, int n, float u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(f + mid) > u) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float env_pdf(const EnvDev& e, float3 w) {
+  float th, ph;
+  dir_angles(w, th, ph);
+  int r = min(e.H - 1, max(0, (int)floorf(th * INV_PI_F * (float)e.H)));
+  int c = min(e.W - 1, max(0, (int)floorf(ph * INV_2PI_F * (float)e.W)));
+  float st = fmaxf(sinf(th), 1e-12f);
+  return __ldg(e.pmf_row + r) * __ldg(e.pmf_col + r * e.W + c) * ((float)e.H * (float)e.W) /
+         (2.0f * PI_F * PI_F * st);
+}
+
+__device__ __forceinline__ void env_sample(const EnvDev& e, float u1, float u2, float3& w, float& pdf) {
+  int r = first_greater(e.cdf_row, e.H, u1);
+  float lo = r > 0 ? __ldg(e.cdf_row + r - 1) : 0.0f, hi = __ldg(e.cdf_row + r);
+  float fr = fminf(fmaxf((u1 - lo) / (hi - lo), 0.0f), 1.0f);
+  const float* row = e.cdf_col + r * e.W;
+  int c = first_greater(row, e.W, u2);
+  float clo = c > 0 ? __ldg(row + c - 1) : 0.0f, chi = __ldg(row + c);
+  float fc = fminf(fmaxf((u2 - clo) / (chi - clo), 0.0f), 1.0f);
+  float th = PI_F * ((float)r + fr) / (float)e.H;
+  float ph = 2.0f * PI_F * ((float)c + fc) / (float)e.W - PI_F;
+  float st, ct, sp, cp;
+  sincosf(th, &st, &ct);
+  sincosf(ph, &sp, &cp);
+  w = f3(st * sp, ct, -st * cp);
+  pdf = __ldg(e.pmf_row + r) * __ldg(e.pmf_col + r * e.W + c) * ((float)e.H * (float)e.W) /
+        (2.0f * PI_F * PI_F * fmaxf(st, 1e-12f));
+}
+
+// ------------------------------------------------------------------ BRDF
+// Metallic-roughness: k_d/pi + F D G / (4 cos_i cos_o); GGX D (Walter et al.
+// 2007), separable Smith G, Schlick F; k_d = a (1-m), F0 = 0.04 (1-m) + a m,
+// alpha_g = r^2.  brdf_mode 1: a / pi.
+__device__ __forceinline__ float3 brdf_eval(float3 n, float3 wo, float3 wi, float3 a, float m, float r, int mode) {
+  float ci = dot3(n, wi), co = dot3(n, wo);
+  if (!(ci > 0.0f) || !(co > 0.0f)) return f3(0.f, 0.f, 0.f);
+  if (mode == 1) return a * INV_PI_F;
+  float one_m = 1.0f - m;
+  float3 F0 = f3(0.04f * one_m + a.x * m, 0.04f * one_m + a.y * m, 0.04f * one_m + a.z * m);
+  float ag = r * r, a2 = ag * ag;
+  float3 h = normalize3(wi + wo);
+  float nh = dot3(n, h), oh = dot3(wo, h);
+  float den = nh * nh * (a2 - 1.0f) + 1.0f;
+  float D = a2 / (PI_F * den * den);
+  float Qi = 2.0f / (ci + sqrtf(a2 + (1.0f - a2) * ci * ci));
+  float Qo = 2.0f / (co + sqrtf(a2 + (1.0f - a2) * co * co));
+  float spec = 0.25f * D * Qi * Qo;
+  float x = 1.0f - oh, x2 = x * x, fw = x2 * x2 * x;
+  return f3(a.x * one_m * INV_PI_F + (F0.x + (1.0f - F0.x) * fw) * spec,
+            a.y * one_m * INV_PI_F + (F0.y + (1.0f - F0.y) * fw) * spec,
+            a.z * one_m * INV_PI_F + (F0.z + (1.0f - F0.z) * fw) * spec);
+}
+
+// Adjoint of brdf_eval for fixed directions: adds d(gf . f) to gn, ga, gm, gr.
+__device__ __forceinline__ void brdf_adjoint(float3 n, float3 wo, float3 wi, float3 a, float m, float r, int mode,
+                                             float3 gf, float3& gn, float3& ga, float& gm, float& gr) {
+  float ci = dot3(n, wi), co = dot3(n, wo);
+  if (!(ci > 0.0f) || !(co > 0.0f)) return;
+  if (mode == 1) { add3(ga, gf * INV_PI_F); return; }
+  float one_m = 1.0f - m;
+  float3 F0 = f3(0.04f * one_m + a.x * m, 0.04f * one_m + a.y * m, 0.04f * one_m + a.z * m);
+  float ag = r * r, a2 = ag * ag;
+  float3 h = normalize3(wi + wo);
+  float nh = dot3(n, h), oh = dot3(wo, h);
+  float den = nh * nh * (a2 - 1.0f) + 1.0f;
+  float D = a2 / (PI_F * den * den);
+  float si = sqrtf(a2 + (1.0f - a2) * ci * ci), so = sqrtf(a2 + (1.0f - a2) * co * co);
+  float Qi = 2.0f / (ci + si), Qo = 2.0f / (co + so);
+  float spec = 0.25f * D * Qi * Qo;
+  float x = 1.0f - oh, x2 = x * x, fw = x2 * x2 * x;
+  float3 F = f3(F0.x + (1.0f - F0.x) * fw, F0.y + (1.0f - F0.y) * fw, F0.z + (1.0f - F0.z) * fw);
+  // diffuse k_d / pi with k_d = a (1 - m)
+  float3 gkd = gf * INV_PI_F;
+  add3(ga, gkd * one_m);
+  gm -= dot3(gkd, a);
+  // F = F0 (1 - fw) + fw ; F0 = 0.04 (1 - m) + a m
+  float3 gF0 = gf * (spec * (1.0f - fw));
+  add3(ga, gF0 * m);
+  gm += gF0.x * (a.x - 0.04f) + gF0.y * (a.y - 0.04f) + gF0.z * (a.z - 0.04f);
+  float gspec = dot3(gf, F);
+  // spec = D Qi Qo / 4
+  float gD = gspec * 0.25f * Qi * Qo, gQi = gspec * 0.25f * D * Qo, gQo = gspec * 0.25f * D * Qi;
+  // Q(c) = 2 / (c + s(c)), s = sqrt(a2 + (1 - a2) c^2)
+  float dQi_dc = -0.5f * Qi * Qi * (1.0f + (1.0f - a2) * ci / si);
+  float dQo_dc = -0.5f * Qo * Qo * (1.0f + (1.0f - a2) * co / so);
+  float dQi_da2 = -0.5f * Qi * Qi * (1.0f - ci * ci) / (2.0f * si);
+  float dQo_da2 = -0.5f * Qo * Qo * (1.0f - co * co) / (2.0f * so);
+  // D = a2 / (pi den^2), den = nh^2 (a2 - 1) + 1
+  float dD_dnh = -4.0f * a2 * nh * (a2 - 1.0f) / (PI_F * den * den * den);
+  float dD_da2 = (den - 2.0f * a2 * nh * nh) / (PI_F * den * den * den);
+  float ga2 = gD * dD_da2 + gQi * dQi_da2 + gQo * dQo_da2;
+  gr += ga2 * 4.0f * r * ag;  // d(r^4)/dr
+  add3(gn, wi * (gQi * dQi_dc) + wo * (gQo * dQo_dc) + h * (gD * dD_dnh));
+}
+
+// ------------------------------------------------------------------ sampling
+// Orthonormal basis (b1, b2, n) after Duff et al. 2017.
+__device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
+  float sgn = copysignf(1.0f, n.z);
+  float a = -1.0f / (sgn + n.z);
+  float b = n.x * n.y * a;
+  b1 = f3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
+  b2 = f3(b, sgn + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float ggx_D(float nh, float a2) {
+  float den = nh * nh * (a2 - 1.0f) + 1.0f;
+  return a2 / (PI_F * den * den);
+}
+
+// GGX half vector with density D(h)(n.h) (Walter et al. 2007), mirrored.
+__device__ __forceinline__ float3 sample_ggx(float3 n, float3 wo, float r, float u1, float u2) {
+  float ag = r * r, a2 = ag * ag;
+  float c2 = (1.0f - u1) / (1.0f + (a2 - 1.0f) * u1);
+  float ct = sqrtf(fmaxf(0.0f, c2)), st = sqrtf(fmaxf(0.0f, 1.0f - c2));
+  float sp, cp;
+  sincosf(2.0f * PI_F * u2, &sp, &cp);
+  float3 b1, b2;
+  onb(n, b1, b2);
+  float3 h = b1 * (st * cp) + b2 * (st * sp) + n * ct;
+  return h * (2.0f * dot3(wo, h)) - wo;
+}
+
+// Cosine-weighted hemisphere (Malley's method).
+__device__ __forceinline__ float3 sample_cos(float3 n, float u1, float u2) {
+  float rr = sqrtf(u1), sp, cp;
+  sincosf(2.0f * PI_F * u2, &sp, &cp);
+  float3 b1, b2;
+  onb(n, b1, b2);
+  return b1 * (rr * cp) + b2 * (rr * sp) + n * sqrtf(fmaxf(0.0f, 1.0f - u1));
+}
+
+__device__ __forceinline__ float pdf_bsdf(float3 n, float3 wo, float3 wi, float r, float p_spec) {
+  float pc = fmaxf(0.0f, dot3(n, wi)) * INV_PI_F;
+  float pg = 0.0f;
+  if (p_spec > 0.0f) {
+    float3 hs = wi + wo;
+    float hl = sqrtf(dot3(hs, hs));
+    if (hl > 0.0f) {
+      float3 h = hs * (1.0f / hl);
+      float nh = dot3(n, h), oh = dot3(wo, h);
+      if (nh > 0.0f && oh > 0.0f) {
+        float ag = r * r;
+        pg = ggx_D(nh, ag * ag) * nh / (4.0f * oh);
+      }
+    }
+  }
+  return p_spec * pg + (1.0f - p_spec) * pc;
+}
+
+// ------------------------------------------------------------------ camera
+__device__ __forceinline__ float3 camera_dir(const CamDev& c, int p) {
+  int x = p % c.W, y = p / c.W;
+  float sx = (((float)x + 0.5f) / (float)c.W * 2.0f - 1.0f) * c.sx_scale;
+  float sy = (1.0f - ((float)y + 0.5f) / (float)c.H * 2.0f) * c.sy_scale;
+  return normalize3(c.f + c.r * sx + c.u * sy);
+}
+
+// ------------------------------------------------------------------ traversal
+struct Ray {
+  float3 o, d, inv, oinv;
+};
+
+__device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
+  Ray r;
+  r.o = o;
+  r.d = d;
+  float ix = 1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x));
+  float iy = 1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y));
+  float iz = 1.0f / (fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z));
+  r.inv = f3(ix, iy, iz);
+  r.oinv = f3(o.x * ix, o.y * iy, o.z * iz);
+  return r;
+}
+
+// Slab test of [lo, hi] against the ray clipped to [tlo, thi].
+__device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, float hy, float hz, const Ray& r,
+                                     float tlo, float thi, float& tnear) {
+  float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
+  float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
+  float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
+  tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
+  float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
+  return tnear <= tfar;
+}
+
+struct Counters {
+  unsigned nodes = 0, tests = 0;
+};
+
+// Depth-first traversal of every instance's BLAS.  The visitor supplies the
+// culling interval [tlo(), thi()], consumes leaves and may end the ray early.
+// `stack` points at this thread's first entry; entries are `stride` ints apart.
+template <class V>
+__device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
+                                         int stride, int* status, Counters& cnt) {
+  for (int ii = 0; ii < n_inst; ++ii) {
+    const Inst& I = insts[ii];
+    if (I.root == INT_MIN) continue;
+    float tn;
+    if (!slab(I.lo[0], I.lo[1], I.lo[2], I.hi[0], I.hi[1], I.hi[2], ray, vis.tlo(), vis.thi(), tn)) continue;
+    int node = I.root, sp = 0;
+    const float4* __restrict__ nodes = I.nodes;
+    // A tree of n leaves has n - 1 internal nodes; a depth-first walk visits
+    // each at most once.  The cap only guards against a malformed tree.
+    int budget = 2 * I.n_leaves + 8;
+    while (true) {
+      if (--budget < 0) {
+        report(status, LF_ERR_STACK);
+        vis.abort();
+        return;
+      }
+      if (node < 0) {
+        ++cnt.tests;
+        vis.leaf(ii, ~node, I);
+        if (vis.done()) return;
+      } else {
+        ++cnt.nodes;
+        const float4* N = nodes + 4 * node;
+        const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), e = __ldg(N + 3);
+        const float lo = vis.tlo(), hi = vis.thi();
+        float tl, tr;
+        const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
+        const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
+        const int cl = __float_as_int(e.x), cr = __float_as_int(e.y);
+        if (hl && hr) {
+          if (sp >= STACK) {
+            report(status, LF_ERR_STACK);
+            vis.abort();
+            return;
+          }
+          const bool lfirst = tl <= tr;
+          stack[(sp++) * stride] = lfirst ? cr : cl;
+          node = lfirst ? cl : cr;
+          continue;
+        }
+        if (hl) { node = cl; continue; }
+        if (hr) { node = cr; continue; }
+      }
+      if (sp == 0) break;
+      node = stack[(--sp) * stride];
+    }
+  }
+}
+
+__device__ __forceinline__ int code_id(const Inst* insts, int code) {
+  const Inst& I = insts[code >> 24];
+  return __float_as_int(__ldg(&I.geo[3 * (code & 0xffffff) + 1].w));
+}
+
+// Collects the K smallest keys (t, id) strictly greater than (last_t, last_id).
+struct NearK {
+  float bt[K];
+  int bc[K];
+  int cnt;
+  float last_t;
+  int last_id;
+  const Inst* insts;
+  float3 o, d;
+  DevParams P;
+
+  __device__ __forceinline__ void reset(float lt, int lid) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) { bt[j] = BIG_F; bc[j] = 0; }
+    cnt = 0;
+    last_t = lt;
+    last_id = lid;
+  }
+  __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, last_t); }
+  __device__ __forceinline__ float thi() const { return cnt >= K ? bt[K - 1] : BIG_F; }
+  __device__ __forceinline__ bool done() const { return false; }
+  __device__ __forceinline__ void abort() { cnt = 0; }
+  __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
+    const float4* g = I.geo + 3 * l;
+    const float4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
+    float t, alpha;
+    if (!hit_surfel(g0, g1, g2, o, d, P, t, alpha)) return;
+    const int id = __float_as_int(g1.w);
+    if (t < last_t || (t == last_t && id <= last_id)) return;
+    if (cnt >= K && (t > bt[K - 1] || (t == bt[K - 1] && id > code_id(insts, bc[K - 1])))) return;
+    int p = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) p += (bt[j] < t || (bt[j] == t && bt[j] < BIG_F && code_id(insts, bc[j]) < id)) ? 1 : 0;
+#pragma unroll
+    for (int j = K - 1; j > 0; --j)
+      if (j > p) { bt[j] = bt[j - 1]; bc[j] = bc[j - 1]; }
+    const int code = (ii << 24) | l;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j == p) { bt[j] = t; bc[j] = code; }
+    cnt = min(cnt + 1, K);
+  }
+};
+
+// Collects the K largest keys below a bound (inclusive on the first round).
+struct FarK {
+  float bt[K];
+  int bc[K];
+  int cnt;
+  float bound_t;
+  int bound_id;
+  bool inclusive;
+  const Inst* insts;
+  float3 o, d;
+  DevParams P;
+
+  __device__ __forceinline__ void reset(float bt0, int bid, bool incl) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) { bt[j] = -BIG_F; bc[j] = 0; }
+    cnt = 0;
+    bound_t = bt0;
+    bound_id = bid;
+    inclusive = incl;
+  }
+  __device__ __forceinline__ float tlo() const { return cnt >= K ? fmaxf(P.t_min, bt[K - 1]) : P.t_min; }
+  __device__ __forceinline__ float thi() const { return bound_t; }
+  __device__ __forceinline__ bool done() const { return false; }
+  __device__ __forceinline__ void abort() { cnt = 0; }
+  __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
+    const float4* g = I.geo + 3 * l;
+    const float4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
+    float t, alpha;
+    if (!hit_surfel(g0, g1, g2, o, d, P, t, alpha)) return;
+    const int id = __float_as_int(g1.w);
+    if (t > bound_t || (t == bound_t && (inclusive ? id > bound_id : id >= bound_id))) return;
+    if (cnt >= K && (t < bt[K - 1] || (t == bt[K - 1] && id < code_id(insts, bc[K - 1])))) return;
+    int p = 0;  // entries with a larger key come first
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      p += (bt[j] > t || (bt[j] == t && bt[j] > -BIG_F && code_id(insts, bc[j]) > id)) ? 1 : 0;
+#pragma unroll
+    for (int j = K - 1; j > 0; --j)
+      if (j > p) { bt[j] = bt[j - 1]; bc[j] = bc[j - 1]; }
+    const int code = (ii << 24) | l;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j == p) { bt[j] = t; bc[j] = code; }
+    cnt = min(cnt + 1, K);
+  }
+};
+
+// Shadow ray: V = prod(1 - alpha~) over all accepted hits; 0 once below T_min.
+struct ShadowV {
+  float V;
+  bool stop;
+  float3 o, d;
+  DevParams P;
+  __device__ __forceinline__ float tlo() const { return P.t_min; }
+  __device__ __forceinline__ float thi() const { return BIG_F; }
+  __device__ __forceinline__ bool done() const { return stop; }
+  __device__ __forceinline__ void abort() { stop = true; }
+  __device__ __forceinline__ void leaf(int, int l, const Inst& I) {
+    const float4* g = I.geo + 3 * l;
+    float t, alpha;
+    if (!hit_surfel(__ldg(g), __ldg(g + 1), __ldg(g + 2), o, d, P, t, alpha)) return;
+    V *= (1.0f - alpha);
+    if (V < P.T_min) { V = 0.0f; stop = true; }
+  }
+};
+
+__device__ __forceinline__ float trace_shadow(const Inst* insts, int n_inst, float3 o, float3 d,
+                                              const DevParams& P, int* stack, int stride, int* status,
+                                              Counters& cnt) {
+  ShadowV v;
+  v.V = 1.0f;
+  v.stop = false;
+  v.o = o;
+  v.d = d;
+  v.P = P;
+  Ray ray = make_ray(o, d);
+  traverse(insts, n_inst, ray, v, stack, stride, status, cnt);
+  return v.V;
+}
+
+// Composited surface record of one ray (Eq. 7).
+struct Surface {
+  float T, W, depth, m, r, nlen, t_stop;
+  float3 x, n, a;
+  float3 Sa;  // sum w a (un-normalised)
+  int hits, id_stop;
+};
+
+// Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop).
+__device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, float3 o, float3 d,
+                                                const DevParams& P, int* stack, int stride, int* status,
+                                                Counters& cnt, Surface& s, unsigned& composited) {
+  NearK kb;
+  kb.insts = insts;
+  kb.o = o;
+  kb.d = d;
+  kb.P = P;
+  Ray ray = make_ray(o, d);
+  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
+  float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
+  int hits = 0, id_stop = -1;
+  float t_stop = 0.0f;
+  float last_t = -BIG_F;
+  int last_id = -1;
+  bool done = false;
+  for (int round = 0; round < P.max_rounds && !done; ++round) {
+    kb.reset(last_t, last_id);
+    traverse(insts, n_inst, ray, kb, stack, stride, status, cnt);
+    const int n = kb.cnt;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (j < n && !done) {
+        const int code = kb.bc[j];
+        const Inst& I = insts[code >> 24];
+        const int l = code & 0xffffff;
+        const float4 g0 = __ldg(I.geo + 3 * l), g1 = __ldg(I.geo + 3 * l + 1), g2 = __ldg(I.geo + 3 * l + 2);
+        const float4 mt = __ldg(I.mat + l);
+        float t, alpha;
+        hit_surfel(g0, g1, g2, o, d, P, t, alpha);
+        const float3 nj = record_normal(g1, g2, d);
+        const float w = T * alpha;
+        W += w;
+        add3(Sx, (o + d * t) * w);
+        St += w * t;
+        add3(Sn, nj * w);
+        add3(Sa, f3(mt.x, mt.y, mt.z) * w);
+        Sm += w * mt.w;
+        Sr += w * g2.w;
+        T *= (1.0f - alpha);
+        ++hits;
+        t_stop = t;
+        id_stop = __float_as_int(g1.w);
+        if (T < P.T_min) done = true;
+      }
+    }
+    if (!done && n < K) done = true;
+    if (!done) {
+      last_t = kb.bt[K - 1];
+      last_id = code_id(insts, kb.bc[K - 1]);
+      if (round == P.max_rounds - 1) report(status, LF_ERR_ROUND_LIMIT);
+    }
+  }
+  composited += (unsigned)hits;
+  const float inv = 1.0f / (W + P.eps_w);
+  s.T = T;
+  s.W = W;
+  s.x = Sx * inv;
+  s.depth = St * inv;
+  s.a = Sa * inv;
+  s.Sa = Sa;
+  s.m = Sm * inv;
+  s.r = Sr * inv;
+  const float3 mv = Sn * inv;
+  s.nlen = sqrtf(dot3(mv, mv));
+  s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
+  s.hits = hits;
+  s.id_stop = id_stop;
+  s.t_stop = t_stop;
+}
+
+}  // namespace lf

@@ -1,0 +1,59 @@
+// Context object behind the opaque lf_ctx handle (shared by lf_api.cu and
+// lf_serve.cu).
+#pragma once
+#include <climits>
+#include <string>
+#include <vector>
+
+#include "lf_kernels.h"
+
+struct EnvSlot {
+  const float* rgb = nullptr;  // caller-owned texels
+  int H = 0, W = 0;
+  float* tables = nullptr;     // pmf_row (H) | cdf_row (H) | pmf_col (H*W) | cdf_col (H*W)
+  double* rowsum = nullptr;
+  double* sin_row = nullptr;
+  std::vector<double> sin_host;
+  size_t cap = 0;
+  int cap_h = 0;
+  bool set = false;
+};
+
+struct lf_ctx {
+  lf_params params{};
+  lf::DevParams dp{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int* status_dev = nullptr;
+  unsigned long long* counters = nullptr;
+  std::string err;
+  // scene (caller-owned arrays) and its object layout
+  lf::SceneDev scene{};
+  bool built = false;
+  int n = 0, n_obj = 0, n_nodes = 0;
+  std::vector<int> offsets, node_off_h;
+  int* offsets_dev = nullptr;
+  int* node_off_dev = nullptr;
+  int* bounds = nullptr;
+  // library-owned BVH storage
+  float4* geo = nullptr;
+  float4* mat = nullptr;
+  float4* nodes = nullptr;
+  int* leaf_parent = nullptr;
+  int* node_parent = nullptr;
+  int* flags = nullptr;
+  unsigned* keys = nullptr;
+  unsigned* vals = nullptr;  // leaf -> surfel id after the build
+  unsigned* keys_alt = nullptr;
+  unsigned* vals_alt = nullptr;
+  unsigned* counts = nullptr;
+  size_t cap_n = 0;
+  lf::Inst* insts_dev = nullptr;
+  std::vector<lf::Inst> insts_h;
+  EnvSlot env[LF_MAX_ENVS];
+};
+
+// Repack + refit objects [first_obj, last_obj] (lf_api.cu).
+lf_status lf_ctx_fit(lf_ctx* c, int first_obj, int last_obj);
+lf::TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id);
+lf::CamDev lf_ctx_cam(const lf_camera& c);

@@ -1,0 +1,75 @@
+// Internal launcher interface between the C ABI (lf_api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lf_common.cuh"
+
+namespace lf {
+
+struct SceneDev {
+  float *mu, *tu, *tv, *scale, *opacity, *albedo, *metallic, *roughness;
+  int n;
+};
+
+struct Mat34 {
+  float R[9], t[3];
+};
+
+struct FitArgs {
+  int first_leaf, n_leaves, n_obj;
+  const int* leaf_off;  // device, n_obj + 1
+  const int* node_off;  // device, n_obj + 1
+  const unsigned* sorted_ids;
+  float4* geo;
+  float4* mat;
+  float4* nodes;
+  int* flags;
+  const int* leaf_parent;
+  const int* node_parent;
+  Inst* insts;
+  float R;  // support radius
+  int* status;
+};
+
+// BVH build / refit (lf_bvh.cu)
+cudaError_t launch_object_bounds(const SceneDev& s, const int* offsets_dev, int n_obj, int max_obj_n, int* bounds,
+                                 cudaStream_t st);
+cudaError_t launch_morton(const SceneDev& s, const int* offsets_dev, int n_obj, const int* bounds, unsigned* keys,
+                          unsigned* vals, cudaStream_t st);
+int radix_tiles(int n);
+cudaError_t launch_radix_sort(unsigned* keys, unsigned* vals, unsigned* keys_alt, unsigned* vals_alt, int n,
+                              const int* offsets_dev, int n_obj, unsigned* counts, cudaStream_t st);
+cudaError_t launch_hierarchy(const unsigned* skeys, const int* leaf_off, const int* node_off, int n_obj,
+                             int n_nodes_total, float4* nodes, int* leaf_parent, int* node_parent, cudaStream_t st);
+cudaError_t launch_pack_fit(const SceneDev& s, const FitArgs& a, cudaStream_t st);
+cudaError_t launch_rigid(const SceneDev& s, int beg, int end, const Mat34& T, cudaStream_t st);
+cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int set_rgb, float metal, float rough,
+                            cudaStream_t st);
+cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, int W, double* rowsum, float* pmf_row,
+                              float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st);
+
+// Rendering (lf_render.cu)
+struct TraceArgs {
+  const Inst* insts;
+  int n_inst;
+  DevParams P;
+  EnvDev env;
+  int* status;
+  unsigned long long* counters;  // nullable: [nodes, tests, composited, rays]
+};
+
+cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, cudaStream_t st);
+cudaError_t launch_shade(const TraceArgs& a, const float* gbuf, int n_pix, int spp, uint32_t k0, uint32_t k1,
+                         float* rgb, unsigned long long* ray_count, cudaStream_t st);
+
+// Adjoint (lf_backward.cu)
+constexpr int SHADE_GRAD_CH = 9;  // per pixel: g_n (3), g_a (3), g_m, g_r, g_T
+cudaError_t launch_shade_backward(const TraceArgs& a, const float* gbuf, int n_pix, int spp, uint32_t k0,
+                                  uint32_t k1, const float* dL_drgb, float* shade_grad, float* d_env,
+                                  cudaStream_t st);
+cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
+                                  const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
+                                  cudaStream_t st);
+
+}  // namespace lf

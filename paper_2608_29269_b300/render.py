@@ -1,0 +1,49 @@
+"""torch.autograd.Function around lf_trace_primary / lf_shade_bounce /
+lf_trace_backward (the hand-written adjoint; no autograd tape is recorded
+for the renderer itself)."""
+from __future__ import annotations
+
+import torch
+
+from . import _native as N
+from .tracer import GRAD_SLICES, SCENE_FIELDS, Tracer
+
+
+class SurfelRender(torch.autograd.Function):
+    """rgb, gbuf = SurfelRender.apply(tracer, cam, env_id, spp, seed, env_rgb, *scene_tensors)
+
+    The scene tensors must be the ones the tracer was built with (the kernels
+    read the packed BVH records of those tensors).  Gradients flow to every
+    surfel attribute and to the environment texels under the path-replay
+    freeze of the shading (Sec. 3.3).
+    """
+
+    @staticmethod
+    def forward(ctx, tracer: Tracer, cam, env_id: int, spp: int, seed: int, env_rgb, *scene):
+        gbuf = tracer.trace_primary(cam, env_id)
+        rgb = tracer.shade(cam, gbuf, env_id, spp, seed)
+        ctx.tracer, ctx.cam, ctx.env_id, ctx.spp, ctx.seed = tracer, cam, env_id, spp, seed
+        ctx.save_for_backward(gbuf, env_rgb)
+        ctx.mark_non_differentiable(gbuf)
+        return rgb, gbuf
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_gbuf):
+        gbuf, env_rgb = ctx.saved_tensors
+        tr = ctx.tracer
+        d_surfel = torch.zeros((tr.scene.n, N.G_STRIDE), device=gbuf.device, dtype=torch.float32)
+        d_env = torch.zeros_like(env_rgb) if ctx.needs_input_grad[5] else None
+        tr.backward(ctx.cam, gbuf, ctx.env_id, ctx.spp, ctx.seed,
+                    dL_drgb=g_rgb.contiguous() if g_rgb is not None else None,
+                    dL_dgbuf=None, d_surfel=d_surfel, d_env=d_env)
+        grads = []
+        for k in SCENE_FIELDS:
+            a, b = GRAD_SLICES[k]
+            t = getattr(tr.scene, k)
+            grads.append(d_surfel[:, a:b].reshape(t.shape))
+        return (None, None, None, None, None, d_env, *grads)
+
+
+def render(tracer: Tracer, cam, env_id: int = 0, spp: int = 16, seed: int = 0):
+    s = tracer.scene
+    return SurfelRender.apply(tracer, cam, env_id, spp, seed, tracer.envs[env_id], *s.tensors())

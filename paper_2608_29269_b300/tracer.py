@@ -1,0 +1,217 @@
+"""Python face of liblightfuse.so: argument marshalling around the C ABI.
+
+Device memory and streams come from PyTorch; every step of the path runs in
+the library's CUDA kernels.  There is no CPU fallback: constructing a Tracer
+without the built extension or without a CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import torch
+
+from . import _native as N
+
+SCENE_FIELDS = ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic", "roughness"]
+SCENE_WIDTH = dict(mu=3, tu=3, tv=3, scale=2, opacity=1, albedo=3, metallic=1, roughness=1)
+GRAD_SLICES = dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
+                   metallic=(15, 16), roughness=(16, 17))
+
+
+def default_params(**kw) -> N.LfParams:
+    p = N.LfParams()
+    _check(N.load().lf_params_default(C.byref(p)))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(st, ctx=None):
+    if st != N.LF_OK:
+        msg = N.load().lf_last_error(ctx).decode() if ctx else ""
+        raise N.LightFuseError(st, msg)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def camera_struct(cam) -> N.LfCamera:
+    c = N.LfCamera()
+    c.eye[:] = [float(v) for v in cam.eye]
+    c.target[:] = [float(v) for v in cam.target]
+    c.up[:] = [float(v) for v in cam.up]
+    c.fovy_deg = float(cam.fovy_deg)
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    return c
+
+
+@dataclass
+class SceneTensors:
+    """Surfel attributes (Eq. 1) as FP32 CUDA tensors, object k owning
+    surfels [object_offsets[k], object_offsets[k+1]) (object 0: background)."""
+    mu: torch.Tensor
+    tu: torch.Tensor
+    tv: torch.Tensor
+    scale: torch.Tensor
+    opacity: torch.Tensor
+    albedo: torch.Tensor
+    metallic: torch.Tensor
+    roughness: torch.Tensor
+    object_offsets: Sequence[int] = field(default_factory=list)
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+    @classmethod
+    def from_numpy(cls, scene, device="cuda"):
+        kw = {k: torch.as_tensor(getattr(scene, k), dtype=torch.float32, device=device).contiguous()
+              for k in SCENE_FIELDS}
+        return cls(**kw, object_offsets=[int(v) for v in scene.object_offsets])
+
+    def tensors(self):
+        return [getattr(self, k) for k in SCENE_FIELDS]
+
+
+class Tracer:
+    """One lf_ctx: a built scene, its BVH and up to 16 environment maps."""
+
+    def __init__(self, params: Optional[N.LfParams] = None, stream: Optional[torch.cuda.Stream] = None, **kw):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Tracer needs a CUDA device")
+        self.lib = N.load()
+        self.params = params if params is not None else default_params(**kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(self.lib.lf_create(C.byref(self.params), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.ctx = h
+        self.scene: Optional[SceneTensors] = None
+        self.envs = {}
+        self._counters = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st):
+        _check(st, self.ctx)
+
+    def sync(self):
+        self.check(self.lib.lf_sync(self.ctx))
+
+    # ------------------------------------------------------------ scene
+    def build(self, scene: SceneTensors):
+        for k in SCENE_FIELDS:
+            t = getattr(scene, k)
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{k}: expected a contiguous float32 CUDA tensor")
+            if t.numel() != scene.n * SCENE_WIDTH[k]:
+                raise ValueError(f"{k}: expected {scene.n} x {SCENE_WIDTH[k]} values")
+        offs = list(scene.object_offsets) or [0, scene.n]
+        arr = (C.c_int * len(offs))(*offs)
+        s = N.LfScene(*[_ptr(getattr(scene, k)) for k in SCENE_FIELDS], scene.n, arr, len(offs) - 1)
+        self.check(self.lib.lf_bvh_build(self.ctx, C.byref(s)))
+        self.scene = scene
+        self._offsets = offs
+
+    def refit(self, object_id: int, R, t):
+        Rf = (C.c_float * 9)(*[float(v) for v in torch.as_tensor(R).reshape(-1).tolist()])
+        tf = (C.c_float * 3)(*[float(v) for v in torch.as_tensor(t).reshape(-1).tolist()])
+        self.check(self.lib.lf_bvh_refit(self.ctx, int(object_id), Rf, tf))
+
+    def sync_scene(self, object_id: int = -1):
+        self.check(self.lib.lf_scene_sync(self.ctx, int(object_id)))
+
+    def set_material(self, object_id: int, rgb=None, metallic: float = -1.0, roughness: float = -1.0):
+        c = (C.c_float * 3)(*[float(v) for v in rgb]) if rgb is not None else None
+        self.check(self.lib.lf_material_set(self.ctx, int(object_id), c, float(metallic), float(roughness)))
+
+    def set_env(self, env_id: int, rgb: torch.Tensor):
+        if rgb.dtype != torch.float32 or rgb.dim() != 3 or rgb.shape[2] != 3:
+            raise ValueError("environment: expected an (H, W, 3) float32 CUDA tensor")
+        rgb = rgb.contiguous()
+        self.check(self.lib.lf_env_set(self.ctx, int(env_id), _ptr(rgb), rgb.shape[0], rgb.shape[1]))
+        self.envs[env_id] = rgb
+
+    def env_tables(self, env_id: int):
+        e = self.envs[env_id]
+        H, W = e.shape[0], e.shape[1]
+        out = [torch.empty(H, device=e.device), torch.empty(H, device=e.device),
+               torch.empty(H * W, device=e.device), torch.empty(H * W, device=e.device)]
+        self.check(self.lib.lf_env_tables(self.ctx, int(env_id), *[_ptr(t) for t in out]))
+        return dict(pmf_row=out[0], cdf_row=out[1], pmf_col=out[2].view(H, W), cdf_col=out[3].view(H, W))
+
+    # ------------------------------------------------------------ rendering
+    def trace_primary(self, cam, env_id: int = 0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((N.LF_GBUF_CHANNELS, cam.height, cam.width), device="cuda", dtype=torch.float32)
+        c = camera_struct(cam)
+        self.check(self.lib.lf_trace_primary(self.ctx, C.byref(c), int(env_id), _ptr(out)))
+        return out
+
+    def shade(self, cam, gbuf: torch.Tensor, env_id: int = 0, spp: int = 16, seed: int = 0,
+              out: Optional[torch.Tensor] = None, ray_count: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 3), device="cuda", dtype=torch.float32)
+        c = camera_struct(cam)
+        self.check(self.lib.lf_shade_bounce(self.ctx, C.byref(c), _ptr(gbuf), int(env_id), int(spp),
+                                            C.c_uint64(seed), _ptr(out), _ptr(ray_count)))
+        return out
+
+    def scratch_bytes(self, cam) -> int:
+        return int(self.lib.lf_backward_scratch_bytes(cam.width, cam.height))
+
+    def backward(self, cam, gbuf, env_id, spp, seed, dL_drgb=None, dL_dgbuf=None, d_surfel=None, d_env=None,
+                 scratch=None):
+        """Accumulates into d_surfel (N, 17) and d_env (H, W, 3); returns them."""
+        if d_surfel is None:
+            d_surfel = torch.zeros((self.scene.n, N.G_STRIDE), device="cuda", dtype=torch.float32)
+        if scratch is None and dL_drgb is not None:
+            scratch = torch.empty(self.scratch_bytes(cam) // 4, device="cuda", dtype=torch.float32)
+        c = camera_struct(cam)
+        nbytes = scratch.numel() * scratch.element_size() if scratch is not None else 0
+        self.check(self.lib.lf_trace_backward(self.ctx, C.byref(c), _ptr(gbuf), int(env_id), int(spp),
+                                              C.c_uint64(seed), _ptr(dL_drgb), _ptr(dL_dgbuf), _ptr(d_surfel),
+                                              _ptr(d_env), _ptr(scratch), nbytes))
+        return d_surfel, d_env
+
+    def set_counters(self, counters: Optional[torch.Tensor]):
+        """counters: int64 CUDA tensor of 4 ([nodes, tests, composited, rays]) or None."""
+        self._counters = counters
+        self.check(self.lib.lf_set_counters(self.ctx, _ptr(counters)))
+
+    def philox(self, ctr: torch.Tensor, k0: int, k1: int) -> torch.Tensor:
+        out = torch.empty_like(ctr)
+        self.check(self.lib.lf_philox(self.ctx, _ptr(ctr), ctr.shape[0], C.c_uint32(k0), C.c_uint32(k1), _ptr(out)))
+        return out
+
+    def bvh_nodes(self, object_id: int):
+        n_int, root = C.c_int(), C.c_int()
+        self.check(self.lib.lf_bvh_info(self.ctx, int(object_id), C.byref(n_int), C.byref(root)))
+        import numpy as np
+        buf = np.zeros((max(1, n_int.value), 16), np.float32)
+        self.check(self.lib.lf_bvh_copy_nodes(self.ctx, int(object_id), buf.ctypes.data_as(C.c_void_p),
+                                              buf.nbytes))
+        return buf[: n_int.value], root.value
+
+
+def split_surfel_grad(d_surfel: torch.Tensor):
+    """(N, 17) gradient -> dict of per-attribute gradients."""
+    return {k: d_surfel[:, a:b].reshape(-1) if b - a == 1 else d_surfel[:, a:b] for k, (a, b) in GRAD_SLICES.items()}

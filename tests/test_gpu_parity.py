@@ -1,0 +1,197 @@
+"""CUDA path against the FP64 oracle on the same seeded inputs (through the C ABI).
+
+Tolerances: 1e-4 absolute per channel (radiance clamped to [0,1]) on every
+pixel the oracle does not flag as sitting on a discontinuity; hit counts
+identical there; the flagged fraction is reported and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import scenes as S
+from tests._helpers import OCH, compare_gbuf, flagged, gbuf_at, gpu_tracer
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def test_philox_matches_known_answers_and_oracle():
+    import torch
+    tr, _ = gpu_tracer(S.scene_c1(), [S.env_uniform(1.0, 8, 16)])
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = [0, 0, 0, 0]
+    for k0, k1 in [(0, 0), (0xa4093822, 0x299f31d0), (12345, 678)]:
+        g = tr.philox(torch.as_tensor(ctr.view(np.int32), device="cuda"), k0, k1).cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(g, oracle.philox(ctr, k0, k1))
+    g = tr.philox(torch.as_tensor(np.zeros((1, 4), np.int32), device="cuda"), 0, 0).cpu().numpy().view(np.uint32)
+    assert [hex(int(v)) for v in g[0]] == ["0x6627e8d5", "0xe169c58d", "0xbc57ac4c", "0x9b00dbd8"]
+
+
+@pytest.mark.parametrize("env", [S.env_sky_sun(0), S.env_smooth(1, 64, 128)])
+def test_env_tables_match_oracle(env):
+    tr, _ = gpu_tracer(S.scene_c1(), [env])
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in tr.env_tables(0).items()}
+    o = oracle.env_tables(env)
+    # both sides sum in FP64 in the same order; the FP32 tables must agree exactly
+    for k in ["cdf_row", "cdf_col"]:
+        np.testing.assert_array_equal(g[k], o[k].astype(np.float32).astype(np.float64))
+    for k in ["pmf_row", "pmf_col"]:
+        np.testing.assert_allclose(g[k], o[k], rtol=1.2e-7, atol=0)
+
+
+def _c1_inputs():
+    return S.scene_c1(0), S.camera_c1(), S.env_uniform(1.0)
+
+
+def test_c1_primary_gbuffer_parity():
+    sc, cam, env = _c1_inputs()
+    tr, _ = gpu_tracer(sc, [env])
+    g = tr.trace_primary(cam, 0)
+    tr.sync()
+    pix = np.arange(cam.n_pixels, dtype=np.int32)
+    o = oracle.render(sc, cam, env, pix, shade=False)
+    gg = gbuf_at(g, pix)
+    flag = flagged(o["margins"])
+    ok = ~flag
+    assert flag.mean() < 0.01
+    assert (o["ch"][:, OCH["hits"]] > 0).sum() > 400
+    np.testing.assert_array_equal(gg[ok, 18], o["ch"][ok, OCH["hits"]])
+    errs = compare_gbuf(gg, o["ch"], ok)
+    print("C1 gbuf max errors:", errs, "flagged:", int(flag.sum()))
+    assert max(errs.values()) <= TOL, errs
+
+
+@pytest.mark.parametrize("params", [dict(), dict(sampling_mode=1), dict(sampling_mode=2), dict(brdf_mode=1)])
+def test_c1_shaded_parity(params):
+    sc, cam, _ = _c1_inputs()
+    env = S.env_sky_sun(3)
+    tr, _ = gpu_tracer(sc, [env], **params)
+    g = tr.trace_primary(cam, 0)
+    rgb = tr.shade(cam, g, 0, spp=8, seed=77)
+    tr.sync()
+    pix = np.arange(cam.n_pixels, dtype=np.int32)
+    o = oracle.render(sc, cam, env, pix, spp=8, seed=77, params=params)
+    flag = flagged(o["margins"])
+    ok = ~flag
+    rg = rgb.reshape(-1, 3).cpu().numpy().astype(np.float64)
+    d = np.abs(np.clip(rg, 0, 1) - np.clip(o["rgb"], 0, 1))[ok]
+    rel = (np.abs(rg - o["rgb"]) / np.maximum(1.0, np.abs(o["rgb"])))[ok]
+    print(params, "C1 shaded: max clamped abs err", d.max(), "max rel", rel.max(), "flagged", int(flag.sum()))
+    assert flag.mean() < 0.02
+    assert d.max() <= TOL
+
+
+def test_c2_one_bounce_parity_on_pixel_subset():
+    """200k-surfel room, 800x800, 16 spp: full GPU frame, oracle on seeded pixels."""
+    sc, cam, env = S.scene_c2(0), S.camera_c2(), S.env_sky_sun(0)
+    tr, _ = gpu_tracer(sc, [env])
+    g = tr.trace_primary(cam, 0)
+    rgb = tr.shade(cam, g, 0, spp=16, seed=1234)
+    tr.sync()
+    pix = S.pixel_subset(cam.width, cam.height, 192, seed=5)
+    o = oracle.render(sc, cam, env, pix, spp=16, seed=1234)
+    flag = flagged(o["margins"])
+    ok = ~flag
+    gg = gbuf_at(g, pix)
+    errs = compare_gbuf(gg, o["ch"], ok)
+    rg = rgb.reshape(-1, 3).cpu().numpy()[pix].astype(np.float64)
+    d = np.abs(np.clip(rg, 0, 1) - np.clip(o["rgb"], 0, 1))[ok]
+    print("C2 gbuf errs", errs, "rgb max", d.max(), "flagged", int(flag.sum()), "of", len(pix))
+    assert (o["ch"][:, OCH["hits"]] > 0).mean() > 0.9
+    assert flag.mean() < 0.05
+    np.testing.assert_array_equal(gg[ok, 18], o["ch"][ok, OCH["hits"]])
+    assert max(errs.values()) <= TOL
+    assert d.max() <= TOL
+
+
+def test_refit_matches_rebuild_bitwise():
+    """Refit keeps the topology; the hit sets, and so the G-buffer, equal a fresh build."""
+    import torch
+    sc, cam, env = S.scene_c2(0, per_face=3000, per_object=8000), S.camera_c2(200, 200), S.env_sky_sun(1)
+    tr, st = gpu_tracer(sc, [env])
+    rng = np.random.default_rng(4)
+    for obj in [1, 3]:
+        lo, hi = sc.object_offsets[obj], sc.object_offsets[obj + 1]
+        R, t = S.rigid_motion(rng, sc.mu[lo:hi].mean(0))
+        tr.refit(obj, R, t)
+    g1 = tr.trace_primary(cam, 0).clone()
+    tr.sync()
+    moved = st.mu.cpu().numpy()
+    ref = sc.copy()
+    ref.mu, ref.tu, ref.tv = moved, st.tu.cpu().numpy(), st.tv.cpu().numpy()
+    tr2, _ = gpu_tracer(ref, [env])
+    g2 = tr2.trace_primary(cam, 0)
+    tr2.sync()
+    assert torch.equal(g1, g2)
+    # and the moved object really moved
+    assert not np.allclose(moved[sc.object_offsets[1]:sc.object_offsets[2]], sc.mu[sc.object_offsets[1]:sc.object_offsets[2]])
+
+
+def test_bvh_boxes_nest_and_cover_every_leaf():
+    sc = S.scene_c2(0, per_face=2000, per_object=5000)
+    tr, _ = gpu_tracer(sc, [S.env_uniform(1.0, 8, 16)])
+    for obj in range(sc.n_objects):
+        nodes, root = tr.bvh_nodes(obj)
+        n_leaves = sc.object_offsets[obj + 1] - sc.object_offsets[obj]
+        assert len(nodes) == n_leaves - 1 and root == 0
+        seen = np.zeros(n_leaves, int)
+        # child codes: >= 0 internal, < 0 leaf ~code
+        codes = nodes[:, 12:14].copy().view(np.int32)
+        box = lambda n, side: (nodes[n, 0:3], nodes[n, 3:6]) if side == 0 else (nodes[n, 6:9], nodes[n, 9:12])
+        stack = [0]
+        while stack:
+            n = stack.pop()
+            for side in (0, 1):
+                c = int(codes[n, side])
+                if c >= 0:
+                    lo, hi = box(n, side)
+                    for cs in (0, 1):
+                        clo, chi = box(c, cs)
+                        assert np.all(clo >= lo) and np.all(chi <= hi)
+                    stack.append(c)
+                else:
+                    seen[~c] += 1
+        assert np.all(seen == 1)
+
+
+def test_c3_gradient_parity():
+    """Adjoint vs the oracle's reverse-mode gradient (1e-3 relative), 512 surfels, 32x32, 4 spp."""
+    import torch
+    full = S.scene_c2(0)
+    cam = S.camera_c2(32, 32)
+    sc = S.scene_c3_subset(full, cam, 512, seed=0)
+    env = S.env_sky_sun(0)
+    tr, st = gpu_tracer(sc, [env])
+    pix = np.arange(cam.n_pixels, dtype=np.int32)
+    o = oracle.render(sc, cam, env, pix, spp=4, seed=3)
+    ok = ~flagged(o["margins"], dict(FLAG_GRAD))
+    rng = np.random.default_rng(8)
+    g_rgb = rng.normal(size=(cam.n_pixels, 3)) * ok[:, None]
+    g_ch = rng.normal(size=(cam.n_pixels, 17)) * 0.2 * ok[:, None]
+    d_s, d_e = oracle.grad(sc, cam, env, pix, 4, 3, g_rgb, g_ch)
+    g = tr.trace_primary(cam, 0)
+    tr.shade(cam, g, 0, spp=4, seed=3)
+    gg = torch.zeros((24, cam.height * cam.width), device="cuda")
+    gg[:17] = torch.as_tensor(g_ch.T, dtype=torch.float32, device="cuda")
+    d_surf = torch.zeros((sc.n, 17), device="cuda")
+    d_env = torch.zeros((env.height, env.width, 3), device="cuda")
+    tr.backward(cam, g, 0, 4, 3, dL_drgb=torch.as_tensor(g_rgb, dtype=torch.float32, device="cuda").contiguous(),
+                dL_dgbuf=gg.contiguous(), d_surfel=d_surf, d_env=d_env)
+    tr.sync()
+    gs, ge = d_surf.cpu().numpy().astype(np.float64), d_env.cpu().numpy().astype(np.float64)
+    report = {}
+    for name, (a, b) in dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
+                             metallic=(15, 16), roughness=(16, 17)).items():
+        ref, got = d_s[:, a:b], gs[:, a:b]
+        floor = 1e-3 * np.abs(ref).max()
+        rel = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
+        report[name] = float(rel.max())
+    floor = 1e-3 * np.abs(d_e).max()
+    report["env"] = float((np.abs(ge - d_e) / np.maximum(np.abs(d_e), floor)).max())
+    print("gradient rel errors:", report, "nonzero surfels", int((np.abs(d_s).sum(1) > 0).sum()))
+    assert (np.abs(d_s).sum(1) > 0).sum() > 50
+    assert max(report.values()) <= 1e-3, report
+
+
+FLAG_GRAD = dict(support=2e-5, alpha=2e-5, tmin=1e-3, tie=1e-6, stop=2e-5, cos=2e-6, frame=2e-6, cap=1e-5)

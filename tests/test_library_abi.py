@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every symbol include/lightfuse.h
+declares (no GPU needed: only host-side calls are made)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lightfuse.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lf_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_29269_b300.build import build
+    from paper_2608_29269_b300 import _native
+    build()
+    return _native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_declares_every_symbol():
+    from paper_2608_29269_b300 import _native
+    assert sorted(s[0] for s in _native.SIGNATURES) == declared_functions()
+
+
+def test_host_only_calls(lib):
+    from paper_2608_29269_b300 import _native as N
+    p = N.LfParams()
+    assert lib.lf_params_default(C.byref(p)) == 0
+    assert abs(p.alpha_max - 0.99) < 1e-7 and p.max_rounds == 64
+    assert lib.lf_params_default(None) == N.LF_ERR_INVALID
+    assert lib.lf_backward_scratch_bytes(800, 800) == 9 * 4 * 800 * 800
+    assert lib.lf_backward_scratch_bytes(0, 5) == 0
+    assert lib.lf_create(C.byref(p), None, None) == N.LF_ERR_INVALID
+    bad = N.LfParams()
+    lib.lf_params_default(C.byref(bad))
+    bad.alpha_max = 1.5
+    h = C.c_void_p()
+    assert lib.lf_create(C.byref(bad), None, C.byref(h)) == N.LF_ERR_INVALID
+    assert lib.lf_sync(None) == N.LF_ERR_INVALID
+    assert lib.lf_destroy(None) == N.LF_ERR_INVALID
+    assert lib.lf_last_error(None) == b"null context"
+
+
+def test_params_agree_with_oracle_readings(lib):
+    """Both sides state the same readings of the paper's open constants."""
+    import oracle
+    from paper_2608_29269_b300 import _native as N
+    p = N.LfParams()
+    lib.lf_params_default(C.byref(p))
+    o = oracle.default_params()
+    for k in ["T_min", "alpha_min", "alpha_max", "support_r2", "eps_w", "t_min", "ray_offset", "p_spec"]:
+        assert abs(getattr(p, k) - o[k]) <= 1e-7 * max(1.0, abs(o[k])), k
+
+
+def test_product_path_fails_loudly_without_extension(tmp_path):
+    from paper_2608_29269_b300 import _native
+    saved = _native._lib
+    _native._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            _native.load(str(tmp_path / "missing.so"))
+    finally:
+        _native._lib = saved
