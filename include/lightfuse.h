@@ -114,7 +114,8 @@ enum {
   LF_CH_TSTOP = 19,  /* ray distance of the last composited hit       */
   LF_CH_IDSTOP = 20, /* surfel id of the last composited hit (-1: none) */
   LF_CH_DIR = 21,    /* primary ray direction (3)                     */
-  LF_GBUF_CHANNELS = 24,
+  LF_CH_TSTOP_LO = 24, /* low part of the stop depth (double-float key) */
+  LF_GBUF_CHANNELS = 25,
   LF_GBUF_DIFF = 17  /* channels 0..16 accept an upstream gradient    */
 };
 

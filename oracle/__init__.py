@@ -118,8 +118,10 @@ class _SceneHandle:
 
 
 def _camera(cam):
-    return _Camera((C.c_double * 3)(*cam.eye), (C.c_double * 3)(*cam.target), (C.c_double * 3)(*cam.up),
-                   float(cam.fovy_deg), int(cam.width), int(cam.height))
+    # the camera reaches the renderer as FP32 values
+    f = lambda v: [float(np.float32(x)) for x in v]
+    return _Camera((C.c_double * 3)(*f(cam.eye)), (C.c_double * 3)(*f(cam.target)), (C.c_double * 3)(*f(cam.up)),
+                   float(np.float32(cam.fovy_deg)), int(cam.width), int(cam.height))
 
 
 def _params(p):
@@ -130,7 +132,10 @@ def _params(p):
 
 def render(scene, cam, env, pixels=None, spp=0, seed=0, shade=True, params=None, scene0=None, env0=None,
            threads=0):
-    """Render camera pixels.  Returns dict(ch=(n,NCH), rgb=(n,3), margins=(n,8), rays=int).
+    """Render camera pixels.
+
+    Returns dict(ch=(n,NCH), rgb=(n,3), margins=(n,8) of the primary ray,
+    margins_shade=(n,8) of the shading rays, rays=int).
 
     scene0/env0: parameters the frozen path-replay data come from (default:
     the same as scene/env).
@@ -146,14 +151,14 @@ def render(scene, cam, env, pixels=None, spp=0, seed=0, shade=True, params=None,
     rgb_env0 = _f32(env0.rgb) if env0 is not None else rgb_env
     ch = np.zeros((n, len(CHANNELS)), np.float64)
     rgb = np.zeros((n, 3), np.float64)
-    mg = np.zeros((n, len(MARGINS)), np.float64)
+    mg = np.zeros((n, 2, len(MARGINS)), np.float64)
     cam_c = _camera(cam)
     prm = _params(params)
     rays = L.or_render(C.byref(sh.s), C.byref(sh0.s), C.byref(cam_c), _p(rgb_env, C.c_float),
                        _p(rgb_env0, C.c_float), env.height, env.width, C.byref(prm), _p(pixels, C.c_int), n,
                        int(spp), C.c_uint64(seed), int(bool(shade)), _p(ch, C.c_double), _p(rgb, C.c_double),
                        _p(mg, C.c_double), int(threads))
-    return dict(ch=ch, rgb=rgb, margins=mg, rays=int(rays))
+    return dict(ch=ch, rgb=rgb, margins=mg[:, 0].copy(), margins_shade=mg[:, 1].copy(), rays=int(rays))
 
 
 def grad(scene, cam, env, pixels, spp, seed, dL_drgb=None, dL_dch=None, shade=True, params=None, threads=0):

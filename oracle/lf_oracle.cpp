@@ -165,7 +165,12 @@ template <class S> V3<S> lift(const V3<double>& a) { return {S(a.x), S(a.y), S(a
 
 using D3 = V3<double>;
 inline double norm(const D3& a) { return std::sqrt(dot(a, a)); }
-inline D3 normalize(const D3& a) { return scl(a, 1.0 / norm(a)); }
+// Division (not a multiply by the reciprocal) keeps the unit normal of an
+// axis-aligned plane exact, so coplanar surfels get exactly equal depths.
+inline D3 normalize(const D3& a) {
+  const double l = norm(a);
+  return {a.x / l, a.y / l, a.z / l};
+}
 
 // ------------------------------------------------------------------------
 // Inputs.
@@ -429,17 +434,35 @@ void collect(const SceneD& sc, const Params& P, const D3& o, const D3& d, std::v
 }
 
 // Margins of the acceptance decisions of the candidates with t <= t_limit.
+// A decision counts only when flipping it could move the result by more than
+// IMPACT: accepting or dropping a candidate at the support edge changes its
+// weight by T_before * o exp(-R^2/2), at the opacity threshold by
+// T_before * alpha_min, where T_before is the transmittance in front of it
+// (`prof` holds (t_j, T after hit j) of the composited hits).
+const double IMPACT = 1e-5;
+
+double T_before(const std::vector<std::pair<double, double>>* prof, double t) {
+  if (!prof) return 1.0;
+  double T = 1.0;
+  for (const auto& h : *prof) {
+    if (h.first < t) T = h.second; else break;
+  }
+  return T;
+}
+
 void candidate_margins(const Params& P, const std::vector<Cand>& cands, const std::vector<double>& op,
-                       double t_limit, Margins* mg) {
+                       double t_limit, Margins* mg, const std::vector<std::pair<double, double>>* prof) {
   if (!mg) return;
   for (const Cand& c : cands) {
     if (c.t > t_limit) continue;
     bool in_front = c.t > P.t_min, in_support = c.r2 <= P.support_r2, dense = c.alpha >= P.alpha_min;
+    const double Tb = T_before(prof, c.t);
+    const double a_edge = op[c.id] * std::exp(-0.5 * P.support_r2);
     // Support edge: matters when the candidate would pass the opacity test there.
-    if (in_front && op[c.id] * std::exp(-0.5 * P.support_r2) >= P.alpha_min)
+    if (in_front && a_edge >= P.alpha_min && Tb * a_edge >= IMPACT)
       mg->put(M_SUPPORT, (c.r2 - P.support_r2) / P.support_r2);
-    if (in_front && in_support) mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
-    if (in_support && dense) mg->put(M_TMIN, (c.t - P.t_min) / P.t_min);
+    if (in_front && in_support && Tb * P.alpha_min >= IMPACT) mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
+    if (in_support && dense && Tb * c.alpha >= IMPACT) mg->put(M_TMIN, (c.t - P.t_min) / P.t_min);
   }
 }
 
@@ -456,9 +479,11 @@ template <class S> struct Record {
 
 template <class S, class SP, class EP>
 Record<S> composite(SP& surf, EP& env, const Params& P, const D3& o, const D3& d,
-                    const std::vector<Cand>& acc, Margins* mg) {
+                    const std::vector<Cand>& acc, Margins* mg,
+                    std::vector<std::pair<double, double>>* prof = nullptr) {
   using std::sqrt;
   Record<S> rec;
+  if (prof) prof->clear();
   S T(1.0), W(0.0), St(0.0), Sm(0.0), Sr(0.0);
   V3<S> Sx, Sn, Sa;
   size_t j = 0;
@@ -478,10 +503,14 @@ Record<S> composite(SP& surf, EP& env, const Params& P, const D3& o, const D3& d
     rec.t_stop = acc[j].t;
     rec.id_stop = acc[j].id;
     rec.sig = (rec.sig ^ (uint32_t)acc[j].id) * 16777619u;
+    if (prof) prof->push_back({acc[j].t, val(T)});
     if (mg) {
       mg->put(M_STOP, (val(T) - P.T_min) / P.T_min);
       mg->put(M_CAP, val(h.oG) - P.alpha_max);
-      if (j + 1 < acc.size()) mg->put(M_TIE, (acc[j + 1].t - acc[j].t) / std::max(1.0, std::fabs(acc[j].t)));
+      // Exactly equal depths (coplanar surfels) are ordered by id on both
+      // sides; only distinct but nearly equal depths may swap in FP32.
+      if (j + 1 < acc.size() && acc[j + 1].t != acc[j].t)
+        mg->put(M_TIE, (acc[j + 1].t - acc[j].t) / std::max(1.0, std::fabs(acc[j].t)));
     }
     if (val(T) < P.T_min) { ++j; break; }
   }
@@ -505,14 +534,13 @@ double shadow(const SceneD& sc, const Params& P, const D3& o, const D3& d, std::
   for (const Cand& c : acc) V *= (1.0 - c.alpha);
   if (mg) {
     mg->put(M_STOP, (V - P.T_min) / P.T_min);
-    if (V > 0.5 * P.T_min) {
-      for (const Cand& c : cands) {
-        bool in_front = c.t > P.t_min, in_support = c.r2 <= P.support_r2, dense = c.alpha >= P.alpha_min;
-        if (in_front && sc.op[c.id] * std::exp(-0.5 * P.support_r2) >= P.alpha_min)
-          mg->put(M_SUPPORT, (c.r2 - P.support_r2) / P.support_r2);
-        if (in_front && in_support) mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
-        if (in_support && dense) mg->put(M_TMIN, (c.t - P.t_min) / P.t_min);
-      }
+    for (const Cand& c : cands) {
+      bool in_front = c.t > P.t_min, in_support = c.r2 <= P.support_r2, dense = c.alpha >= P.alpha_min;
+      const double a_edge = sc.op[c.id] * std::exp(-0.5 * P.support_r2);
+      if (in_front && a_edge >= P.alpha_min && V * a_edge >= IMPACT)
+        mg->put(M_SUPPORT, (c.r2 - P.support_r2) / P.support_r2);
+      if (in_front && in_support && V * P.alpha_min >= IMPACT) mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
+      if (in_support && dense && V * c.alpha >= IMPACT) mg->put(M_TMIN, (c.t - P.t_min) / P.t_min);
     }
   }
   return V < P.T_min ? 0.0 : V;
@@ -613,11 +641,15 @@ Cam make_cam(const double eye[3], const double target[3], const double up[3], do
   c.W = W; c.H = H;
   return c;
 }
+// The pixel ray is the FP64 pinhole direction rounded once to FP32: the
+// renderer's rays are FP32 vectors, and rounding the same FP64 direction on
+// both sides makes them trace the same ray.
 D3 cam_dir(const Cam& c, int p) {
   int x = p % c.W, y = p / c.W;
   double sx = (((double)x + 0.5) / c.W * 2.0 - 1.0) * c.th * c.aspect;
   double sy = (1.0 - ((double)y + 0.5) / c.H * 2.0) * c.th;
-  return normalize(c.f + scl(c.r, sx) + scl(c.u, sy));
+  D3 d = normalize(c.f + scl(c.r, sx) + scl(c.u, sy));
+  return {(double)(float)d.x, (double)(float)d.y, (double)(float)d.z};
 }
 
 // ------------------------------------------------------------------------
@@ -633,6 +665,7 @@ struct SampleFz {
 
 struct Work {  // per-thread scratch
   std::vector<Cand> cands, acc;
+  std::vector<std::pair<double, double>> prof;
 };
 
 void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Record<double>& rec,
@@ -643,7 +676,10 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
   D3 wo = scl(d, -1.0), n = rec.n;
   D3 xs = rec.x + scl(n, P.ray_offset);
   double co = dot(n, wo);
-  if (mg) { mg->put(M_COS, co); mg->put(M_FRAME, n.z); }
+  // View-side cosine (the Lambert term makes the estimator jump at 0) and the
+  // sign of n_z that orients the sampling frame (an exact 0 is the same on
+  // both sides).
+  if (mg) { mg->put(M_COS, co); if (n.z != 0.0) mg->put(M_FRAME, n.z); }
   if (co <= 0.0) return;
   const double ps = P.brdf_mode == 1 ? 0.0 : P.p_spec;
   SurfelValues sv{&sc};
@@ -655,7 +691,6 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
     if (P.sampling_mode != 1) {  // (i) environment NEE at the primary record
       env_sample(env0, u[0], u[1], fz.we, fz.pe);
       double ce = dot(n, fz.we);
-      if (mg) mg->put(M_COS, ce);
       if (ce > 0.0 && fz.pe > 0.0) {
         fz.e_ok = 1;
         fz.Ve = shadow(sc, P, xs, fz.we, wk.cands, wk.acc, mg);
@@ -667,7 +702,6 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
     // (ii) BSDF continuation from the cosine/GGX mixture
     fz.wi = (u[2] < ps) ? sample_ggx(n, wo, rec.r, u[3], u[4]) : sample_cos(n, u[3], u[4]);
     double ci = dot(n, fz.wi);
-    if (mg) mg->put(M_COS, ci);
     double pb = pdf_bsdf(n, wo, fz.wi, rec.r, ps);
     if (!(ci > 0.0 && pb > 0.0)) continue;
     fz.b_ok = 1;
@@ -675,8 +709,8 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
     double pe_i = env_pdf(env0, fz.wi);
     fz.wbsdf = P.sampling_mode == 1 ? 1.0 : pb * pb / (pb * pb + pe_i * pe_i);
     collect(sc, P, xs, fz.wi, wk.cands, wk.acc);
-    Record<double> r2 = composite<double>(sv, ev, P, xs, fz.wi, wk.acc, mg);
-    candidate_margins(P, wk.cands, sc.op, r2.hits && val(r2.T) < P.T_min ? r2.t_stop : 1e300, mg);
+    Record<double> r2 = composite<double>(sv, ev, P, xs, fz.wi, wk.acc, mg, &wk.prof);
+    candidate_margins(P, wk.cands, sc.op, r2.hits && val(r2.T) < P.T_min ? r2.t_stop : 1e300, mg, &wk.prof);
     if (rays) ++*rays;
     fz.T2 = r2.T;
     if (r2.hits == 0) continue;
@@ -688,7 +722,6 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
     for (int q = 0; q < 2; ++q) {
       env_sample(env0, u[5 + 2 * q], u[6 + 2 * q], fz.wq[q], fz.pq[q]);
       double cq = dot(n2, fz.wq[q]);
-      if (mg) mg->put(M_COS, cq);
       if (!(cq > 0.0 && co2 > 0.0 && fz.pq[q] > 0.0)) continue;
       fz.q_ok[q] = 1;
       fz.Vq[q] = shadow(sc, P, xs2, fz.wq[q], wk.cands, wk.acc, mg);
@@ -885,8 +918,8 @@ void or_trace_rays(const or_scene* sc_in, const float* env_rgb, int H, int W, co
     D3 o{orig[3 * i], orig[3 * i + 1], orig[3 * i + 2]}, d{dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2]};
     Margins mg;
     collect(sc, P, o, d, wk.cands, wk.acc);
-    Record<double> r = composite<double>(sv, ev, P, o, d, wk.acc, &mg);
-    candidate_margins(P, wk.cands, sc.op, r.hits && r.T < P.T_min ? r.t_stop : 1e300, &mg);
+    Record<double> r = composite<double>(sv, ev, P, o, d, wk.acc, &mg, &wk.prof);
+    candidate_margins(P, wk.cands, sc.op, r.hits && r.T < P.T_min ? r.t_stop : 1e300, &mg, &wk.prof);
     double* ch = ch_out + (size_t)i * NCH;
     record_to_channels(r, ch);
     ch[CH_NLEN] = r.nlen; ch[CH_HITS] = r.hits; ch[CH_TSTOP] = r.t_stop; ch[CH_IDSTOP] = r.id_stop;
@@ -909,7 +942,8 @@ void or_shadow_rays(const or_scene* sc_in, const or_params* pp, const double* or
 // Render a set of camera pixels.  `sc0`/`env0` are the parameters the frozen
 // sample data come from (path replay); pass the same pointers as `sc`/`env`
 // for an ordinary render.  Outputs per pixel: NCH channels, RGB radiance
-// (when shade != 0), NMARGIN margins (nullable).  Returns the number of rays
+// (when shade != 0), 2 x NMARGIN margins (nullable): those of the primary
+// ray, then those of the shading rays.  Returns the number of rays
 // traced (primary + shadow + continuation).
 int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera* cam_in, const float* env_rgb,
                   const float* env0_rgb, int H, int W, const or_params* pp, const int* pixels, int n_pix, int spp,
@@ -934,11 +968,11 @@ int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera
     for (int i = 0; i < n_pix; ++i) {
       int p = pixels[i];
       D3 d = cam_dir(cam, p);
-      Margins mg;
+      Margins mg, mgs;  // primary ray; shading rays
       int64_t rays = 1;
       collect(sc, P, cam.eye, d, wk.cands, wk.acc);
-      Record<double> r = composite<double>(sv, ev, P, cam.eye, d, wk.acc, &mg);
-      candidate_margins(P, wk.cands, sc.op, r.hits && r.T < P.T_min ? r.t_stop : 1e300, &mg);
+      Record<double> r = composite<double>(sv, ev, P, cam.eye, d, wk.acc, &mg, &wk.prof);
+      candidate_margins(P, wk.cands, sc.op, r.hits && r.T < P.T_min ? r.t_stop : 1e300, &mg, &wk.prof);
       double* ch = ch_out + (size_t)i * NCH;
       record_to_channels(r, ch);
       ch[CH_NLEN] = r.nlen; ch[CH_HITS] = r.hits; ch[CH_TSTOP] = r.t_stop; ch[CH_IDSTOP] = r.id_stop;
@@ -949,11 +983,15 @@ int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera
           collect(base, P, cam.eye, d, wk.cands, wk.acc);
           r0 = composite<double>(sv0, ev0, P, cam.eye, d, wk.acc, nullptr);
         }
-        frozen_samples(base, e0, P, r0, d, (uint32_t)p, spp, seed, wk, fzs, &mg, &rays);
+        frozen_samples(base, e0, P, r0, d, (uint32_t)p, spp, seed, wk, fzs, &mgs, &rays);
         V3<double> L = eval_pixel<double>(r, ev, P, d, fzs, spp);
         rgb_out[3 * i] = L.x; rgb_out[3 * i + 1] = L.y; rgb_out[3 * i + 2] = L.z;
       }
-      if (margins) for (int k = 0; k < NMARGIN; ++k) margins[(size_t)i * NMARGIN + k] = mg.m[k];
+      if (margins)
+        for (int k = 0; k < NMARGIN; ++k) {
+          margins[(size_t)i * 2 * NMARGIN + k] = mg.m[k];
+          margins[(size_t)i * 2 * NMARGIN + NMARGIN + k] = mgs.m[k];
+        }
       total_rays += rays;
     }
   }

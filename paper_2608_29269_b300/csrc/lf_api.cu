@@ -47,24 +47,23 @@ void free_scene_storage(lf_ctx* c) {
   c->cap_n = 0;
 }
 
+// Camera basis in FP64: f = normalize(target - eye), r = normalize(f x up),
+// u = r x f; th = tan(fovy / 2).
 CamDev to_cam(const lf_camera& c) {
   double e[3] = {c.eye[0], c.eye[1], c.eye[2]};
-  double f[3] = {c.target[0] - e[0], c.target[1] - e[1], c.target[2] - e[2]};
+  double f[3] = {(double)c.target[0] - e[0], (double)c.target[1] - e[1], (double)c.target[2] - e[2]};
   double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-  for (double& v : f) v /= fl;
+  for (double& v : f) v = v / fl;
   double up[3] = {c.up[0], c.up[1], c.up[2]};
   double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
   double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-  for (double& v : r) v /= rl;
+  for (double& v : r) v = v / rl;
   double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
-  double th = std::tan(0.5 * (double)c.fovy_deg * 3.14159265358979323846 / 180.0);
   CamDev d;
-  d.eye = make_float3((float)e[0], (float)e[1], (float)e[2]);
-  d.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
-  d.r = make_float3((float)r[0], (float)r[1], (float)r[2]);
-  d.u = make_float3((float)u[0], (float)u[1], (float)u[2]);
-  d.sx_scale = (float)(th * (double)c.width / (double)c.height);
-  d.sy_scale = (float)th;
+  d.eye = make_float3(c.eye[0], c.eye[1], c.eye[2]);
+  for (int k = 0; k < 3; ++k) { d.f[k] = f[k]; d.r[k] = r[k]; d.u[k] = u[k]; }
+  d.th = std::tan(0.5 * (double)c.fovy_deg * 3.14159265358979323846 / 180.0);
+  d.aspect = (double)c.width / (double)c.height;
   d.W = c.width;
   d.H = c.height;
   return d;
@@ -238,7 +237,7 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     free_scene_storage(c);
     const size_t cap = (size_t)n + (size_t)n / 8 + 64;
     const size_t tiles = (size_t)radix_tiles((int)cap) + 1;
-    cudaError_t e = dev_alloc(&c->geo, 3 * cap);
+    cudaError_t e = dev_alloc(&c->geo, (size_t)GEO * cap);
     if (e == cudaSuccess) e = dev_alloc(&c->mat, cap);
     if (e == cudaSuccess) e = dev_alloc(&c->nodes, 4 * cap);
     if (e == cudaSuccess) e = dev_alloc(&c->leaf_parent, cap);
@@ -277,7 +276,7 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     I.root = nk >= 2 ? 0 : (nk == 1 ? ~0 : INT_MIN);
     I.n_leaves = nk;
     I.nodes = c->nodes + 4 * (size_t)c->node_off_h[k];
-    I.geo = c->geo + 3 * (size_t)c->offsets[k];
+    I.geo = c->geo + (size_t)GEO * c->offsets[k];
     I.mat = c->mat + (size_t)c->offsets[k];
     I.id_base = c->offsets[k];
     I.pad = 0;

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   float S = g_T * T;
   float Tn = T;
   int remaining = hits;
-  float bound_t = ch(LF_CH_TSTOP);
+  float bound_t = ch(LF_CH_TSTOP), bound_tl = ch(LF_CH_TSTOP_LO);
   int bound_id = (int)ch(LF_CH_IDSTOP);
   bool inclusive = true;
   FarK kb;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   const Ray ray = make_ray(o, d);
   Counters cnt;
   for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
-    kb.reset(bound_t, bound_id, inclusive);
+    kb.reset(bound_t, bound_tl, bound_id, inclusive);
     traverse(s_inst, a.n_inst, ray, kb, s_stack + threadIdx.x, TB, a.status, cnt);
     const int n = kb.cnt;
 #pragma unroll
@@ -287,20 +287,20 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
         const int code = kb.bc[j];
         const Inst& I = s_inst[code >> 24];
         const int l = code & 0xffffff;
-        const float4 g0 = __ldg(I.geo + 3 * l), g1 = __ldg(I.geo + 3 * l + 1), g2 = __ldg(I.geo + 3 * l + 2);
+        const Rec rc = load_rec(I.geo, l);
         const float4 mt = __ldg(I.mat + l);
-        float t, alpha;
-        hit_surfel(g0, g1, g2, o, d, Pm, t, alpha);
-        const float3 nj = record_normal(g1, g2, d);
+        float t, tl, alpha;
+        hit_surfel(rc, o, d, Pm, t, tl, alpha);
+        const float3 nj = record_normal(rc, d);
         const float3 xj = o + d * t;
         const float Tj = Tn / (1.0f - alpha);
         const float w = Tj * alpha;
         const float gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y +
-                         gSa.z * mt.z + gSm * mt.w + gSr * g2.w;
+                         gSa.z * mt.z + gSm * mt.w + gSr * rc.g2.w;
         const float g_alpha = Tj * gw - S / (1.0f - alpha);
         S += gw * w;
         Tn = Tj;
-        surfel_adjoint(sc, __float_as_int(g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
+        surfel_adjoint(sc, __float_as_int(rc.g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
                        gSr * w, d_surfel);
         --remaining;
       }
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
         break;
       }
       bound_t = kb.bt[K - 1];
-      bound_id = code_id(s_inst, kb.bc[K - 1]);
+      code_tail(s_inst, kb.bc[K - 1], o, d, Pm, bound_tl, bound_id);
       inclusive = false;
     }
   }

@@ -273,9 +273,14 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
   const float3 mu = f3(s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]);
   const float3 tu = f3(s.tu[3 * i], s.tu[3 * i + 1], s.tu[3 * i + 2]);
   const float3 tv = f3(s.tv[3 * i], s.tv[3 * i + 1], s.tv[3 * i + 2]);
-  a.geo[3 * L + 0] = make_float4(mu.x, mu.y, mu.z, s.opacity[i]);
-  a.geo[3 * L + 1] = make_float4(tu.x / su, tu.y / su, tu.z / su, __int_as_float(i));
-  a.geo[3 * L + 2] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, s.roughness[i]);
+  // unit normal tu x tv, normalised in FP64 (axis-aligned planes stay exact)
+  const double cx = (double)tu.y * tv.z - (double)tu.z * tv.y, cy = (double)tu.z * tv.x - (double)tu.x * tv.z,
+               cz = (double)tu.x * tv.y - (double)tu.y * tv.x;
+  const double cl = sqrt(cx * cx + cy * cy + cz * cz);
+  a.geo[GEO * L + 0] = make_float4(mu.x, mu.y, mu.z, s.opacity[i]);
+  a.geo[GEO * L + 1] = make_float4(tu.x / su, tu.y / su, tu.z / su, __int_as_float(i));
+  a.geo[GEO * L + 2] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, s.roughness[i]);
+  a.geo[GEO * L + 3] = make_float4((float)(cx / cl), (float)(cy / cl), (float)(cz / cl), 0.0f);
   a.mat[L] = make_float4(s.albedo[3 * i], s.albedo[3 * i + 1], s.albedo[3 * i + 2], s.metallic[i]);
   float3 lo, hi;
   surfel_box(s, i, a.R, lo, hi);

@@ -1,9 +1,11 @@
 // Device-side building blocks of the surfel ray tracer (sm_103a).
 //
 // Record layouts (library-owned, in BVH leaf order per object):
-//   geo[3*l+0] = (mu.xyz, opacity)
-//   geo[3*l+1] = (tu/s_u .xyz, surfel id as int bits)
-//   geo[3*l+2] = (tv/s_v .xyz, roughness)
+//   geo[4*l+0] = (mu.xyz, opacity)
+//   geo[4*l+1] = (tu/s_u .xyz, surfel id as int bits)
+//   geo[4*l+2] = (tv/s_v .xyz, roughness)
+//   geo[4*l+3] = (n^.xyz, 0)  unit normal tu x tv, normalised in FP64 then rounded,
+//                so that exactly coplanar axis-aligned surfels get exactly equal t
 //   mat[l]     = (albedo.rgb, metallic)
 //   BVH2 node (64 B, child boxes stored in the parent):
 //     n0 = (L.lo.xyz, L.hi.x)  n1 = (L.hi.yz, R.lo.xy)  n2 = (R.lo.z, R.hi.xyz)
@@ -51,9 +53,13 @@ struct EnvDev {
   int H, W;
 };
 
+// Pinhole camera with its basis in FP64 (host-computed).  The ray direction
+// of each pixel is evaluated in FP64 and rounded once to FP32, so every pixel
+// traces a reproducible FP32 ray.
 struct CamDev {
-  float3 eye, f, r, u;
-  float sx_scale, sy_scale;  // tan(fovy/2) * aspect, tan(fovy/2)
+  float3 eye;
+  double f[3], r[3], u[3];
+  double th, aspect;  // tan(fovy/2), width/height
   int W, H;
 };
 
@@ -115,26 +121,106 @@ __device__ __forceinline__ void sample_uniforms(uint32_t pixel, uint32_t s, uint
 }
 
 // ------------------------------------------------------------------ Eq. 6
-// Plane hit of a packed surfel record; t and alpha~ on acceptance.
-__device__ __forceinline__ bool hit_surfel(const float4 g0, const float4 g1, const float4 g2, const float3 o,
-                                           const float3 d, const DevParams& P, float& t, float& alpha) {
-  const float3 a = f3(g1.x, g1.y, g1.z), b = f3(g2.x, g2.y, g2.z);
-  const float3 c = cross_rn(a, b);
-  const float3 p = f3(__fsub_rn(g0.x, o.x), __fsub_rn(g0.y, o.y), __fsub_rn(g0.z, o.z));
-  t = __fdiv_rn(dot_rn(p, c), dot_rn(d, c));
+constexpr int GEO = 4;  // float4 per packed surfel record
+
+struct Rec {
+  float4 g0, g1, g2, g3;
+};
+__device__ __forceinline__ Rec load_rec(const float4* geo, int l) {
+  const float4* g = geo + GEO * l;
+  return Rec{__ldg(g), __ldg(g + 1), __ldg(g + 2), __ldg(g + 3)};
+}
+
+// Error-free transformations: TwoSum (Knuth) and TwoProd via FMA.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+// (ah + al) . b as a renormalised double-float (compensated dot product,
+// Ogita, Rump and Oishi 2005).
+__device__ __forceinline__ void dot2(float3 ah, float3 al, float3 b, float& hi, float& lo) {
+  float s, c, p, e, s2, e2;
+  two_prod(ah.x, b.x, s, c);
+  two_prod(ah.y, b.y, p, e);
+  two_sum(s, p, s2, e2);
+  s = s2;
+  c = __fadd_rn(c, __fadd_rn(e, e2));
+  two_prod(ah.z, b.z, p, e);
+  two_sum(s, p, s2, e2);
+  s = s2;
+  c = __fadd_rn(c, __fadd_rn(e, e2));
+  c = __fmaf_rn(al.x, b.x, c);
+  c = __fmaf_rn(al.y, b.y, c);
+  c = __fmaf_rn(al.z, b.z, c);
+  hi = __fadd_rn(s, c);
+  lo = __fsub_rn(c, __fsub_rn(hi, s));
+}
+
+// Plane hit of a packed surfel record (Eq. 6).  A cheap FP32 pass rejects
+// candidates far outside the support; the rest are evaluated with the ray
+// depth t = t + tl as a double-float (error ~1e-14 relative for the FP32
+// inputs), so that the depth order of near-coincident surfels and the
+// support test do not depend on FP32 rounding.  Returns acceptance; on
+// acceptance t (rounded depth), tl (its low part) and alpha~.
+__device__ __forceinline__ bool hit_surfel(const Rec& r, const float3 o, const float3 d, const DevParams& P,
+                                           float& t, float& tl, float& alpha) {
+  const float3 a = f3(r.g1.x, r.g1.y, r.g1.z), b = f3(r.g2.x, r.g2.y, r.g2.z), nh = f3(r.g3.x, r.g3.y, r.g3.z);
+  const float3 p = f3(__fsub_rn(r.g0.x, o.x), __fsub_rn(r.g0.y, o.y), __fsub_rn(r.g0.z, o.z));
+  const float den32 = dot_rn(d, nh);
+  const float t32 = __fdiv_rn(dot_rn(p, nh), den32);
+  if (!(t32 > 0.5f * P.t_min) || !(t32 < BIG_F)) return false;
+  {
+    const float3 q = f3(__fmaf_rn(t32, d.x, -p.x), __fmaf_rn(t32, d.y, -p.y), __fmaf_rn(t32, d.z, -p.z));
+    const float u = dot_rn(q, a), v = dot_rn(q, b);
+    if (!(__fmaf_rn(u, u, __fmul_rn(v, v)) <= 1.001f * P.support_r2)) return false;
+  }
+  // precise depth: p = mu - o exactly, t = (p . n) / (d . n) as a double-float
+  float3 ph, pl;
+  two_sum(r.g0.x, -o.x, ph.x, pl.x);
+  two_sum(r.g0.y, -o.y, ph.y, pl.y);
+  two_sum(r.g0.z, -o.z, ph.z, pl.z);
+  float nhi, nlo, dhi, dlo;
+  dot2(ph, pl, nh, nhi, nlo);
+  dot2(d, f3(0.f, 0.f, 0.f), nh, dhi, dlo);
+  const float t0 = __fdiv_rn(nhi, dhi);
+  const float res = __fadd_rn(__fmaf_rn(-t0, dhi, nhi), __fmaf_rn(-t0, dlo, nlo));
+  const float t1 = __fdiv_rn(res, dhi);
+  t = __fadd_rn(t0, t1);
+  tl = __fsub_rn(t1, __fsub_rn(t, t0));
   if (!(t > P.t_min) || !(t < BIG_F)) return false;
-  const float3 q = f3(__fmaf_rn(t, d.x, -p.x), __fmaf_rn(t, d.y, -p.y), __fmaf_rn(t, d.z, -p.z));
-  const float u = dot_rn(q, a), v = dot_rn(q, b);
-  const float r2 = __fmaf_rn(u, u, __fmul_rn(v, v));
+  // q = o + t d - mu as a double-float, then u = q . tu/s_u, v = q . tv/s_v
+  float3 qh, ql;
+  {
+    float m, me, s, se;
+    two_prod(t, d.x, m, me); two_sum(m, -ph.x, s, se);
+    qh.x = s; ql.x = __fadd_rn(__fadd_rn(me, se), __fmaf_rn(tl, d.x, -pl.x));
+    two_prod(t, d.y, m, me); two_sum(m, -ph.y, s, se);
+    qh.y = s; ql.y = __fadd_rn(__fadd_rn(me, se), __fmaf_rn(tl, d.y, -pl.y));
+    two_prod(t, d.z, m, me); two_sum(m, -ph.z, s, se);
+    qh.z = s; ql.z = __fadd_rn(__fadd_rn(me, se), __fmaf_rn(tl, d.z, -pl.z));
+  }
+  float uh, ul, vh, vl;
+  dot2(qh, ql, a, uh, ul);
+  dot2(qh, ql, b, vh, vl);
+  const float r2 = __fmaf_rn(uh, uh, __fmaf_rn(vh, vh, __fmul_rn(2.0f, __fmaf_rn(uh, ul, __fmul_rn(vh, vl)))));
   if (!(r2 <= P.support_r2)) return false;
-  alpha = fminf(P.alpha_max, __fmul_rn(g0.w, expf(__fmul_rn(-0.5f, r2))));
+  alpha = fminf(P.alpha_max, __fmul_rn(r.g0.w, expf(__fmul_rn(-0.5f, r2))));
   return alpha >= P.alpha_min;
 }
 
+// Sort key of a hit: depth (rounded, low part), then surfel id.
+__device__ __forceinline__ bool key_less(float ta, float la, int ia, float tb, float lb, int ib) {
+  return ta < tb || (ta == tb && (la < lb || (la == lb && ia < ib)));
+}
+
 // Normal of a packed record facing the ray (two-sided surfels).
-__device__ __forceinline__ float3 record_normal(const float4 g1, const float4 g2, const float3 d) {
-  float3 c = cross_rn(f3(g1.x, g1.y, g1.z), f3(g2.x, g2.y, g2.z));
-  float3 n = c * (1.0f / sqrtf(dot3(c, c)));
+__device__ __forceinline__ float3 record_normal(const Rec& r, const float3 d) {
+  const float3 n = f3(r.g3.x, r.g3.y, r.g3.z);
   return dot3(d, n) < 0.0f ? n : -n;
 }
 
@@ -340,10 +426,15 @@ __device__ __forceinline__ float pdf_bsdf(float3 n, float3 wo, float3 wi, float 
 
 // ------------------------------------------------------------------ camera
 __device__ __forceinline__ float3 camera_dir(const CamDev& c, int p) {
-  int x = p % c.W, y = p / c.W;
-  float sx = (((float)x + 0.5f) / (float)c.W * 2.0f - 1.0f) * c.sx_scale;
-  float sy = (1.0f - ((float)y + 0.5f) / (float)c.H * 2.0f) * c.sy_scale;
-  return normalize3(c.f + c.r * sx + c.u * sy);
+  const int x = p % c.W, y = p / c.W;
+  const double sx = __dmul_rn(__dmul_rn(__dsub_rn(__dmul_rn(__ddiv_rn(__dadd_rn((double)x, 0.5), (double)c.W), 2.0), 1.0),
+                                        c.th), c.aspect);
+  const double sy = __dmul_rn(__dsub_rn(1.0, __dmul_rn(__ddiv_rn(__dadd_rn((double)y, 0.5), (double)c.H), 2.0)), c.th);
+  double v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = __dadd_rn(__dadd_rn(c.f[k], __dmul_rn(c.r[k], sx)), __dmul_rn(c.u[k], sy));
+  const double l = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])), __dmul_rn(v[2], v[2])));
+  return f3((float)__ddiv_rn(v[0], l), (float)__ddiv_rn(v[1], l), (float)__ddiv_rn(v[2], l));
 }
 
 // ------------------------------------------------------------------ traversal
@@ -435,42 +526,63 @@ __device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ra
 
 __device__ __forceinline__ int code_id(const Inst* insts, int code) {
   const Inst& I = insts[code >> 24];
-  return __float_as_int(__ldg(&I.geo[3 * (code & 0xffffff) + 1].w));
+  return __float_as_int(__ldg(&I.geo[GEO * (code & 0xffffff) + 1].w));
 }
 
-// Collects the K smallest keys (t, id) strictly greater than (last_t, last_id).
+// Low depth part and id of a buffered hit (recomputed from its record; only
+// needed when two rounded depths are exactly equal).
+__device__ __forceinline__ void code_tail(const Inst* insts, int code, float3 o, float3 d, const DevParams& P,
+                                          float& tl, int& id) {
+  const Inst& I = insts[code >> 24];
+  const Rec r = load_rec(I.geo, code & 0xffffff);
+  float t, alpha;
+  tl = 0.0f;
+  hit_surfel(r, o, d, P, t, tl, alpha);
+  id = __float_as_int(r.g1.w);
+}
+
+// Collects the K smallest keys (t, tl, id) strictly greater than the last
+// round's key.
 struct NearK {
   float bt[K];
   int bc[K];
   int cnt;
-  float last_t;
+  float last_t, last_tl;
   int last_id;
   const Inst* insts;
   float3 o, d;
   DevParams P;
 
-  __device__ __forceinline__ void reset(float lt, int lid) {
+  __device__ __forceinline__ void reset(float lt, float ltl, int lid) {
 #pragma unroll
     for (int j = 0; j < K; ++j) { bt[j] = BIG_F; bc[j] = 0; }
     cnt = 0;
     last_t = lt;
+    last_tl = ltl;
     last_id = lid;
   }
   __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, last_t); }
   __device__ __forceinline__ float thi() const { return cnt >= K ? bt[K - 1] : BIG_F; }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
+  // key of buffered entry j (t known) compared with (t, tl, id)
+  __device__ __forceinline__ bool entry_less(int j, float t, float tl, int id) const {
+    if (bt[j] != t) return bt[j] < t;
+    float etl;
+    int eid;
+    code_tail(insts, bc[j], o, d, P, etl, eid);
+    return key_less(t, etl, eid, t, tl, id);
+  }
   __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
-    const float4* g = I.geo + 3 * l;
-    const float4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
-    float t, alpha;
-    if (!hit_surfel(g0, g1, g2, o, d, P, t, alpha)) return;
-    const int id = __float_as_int(g1.w);
-    if (t < last_t || (t == last_t && id <= last_id)) return;
-    if (cnt >= K && (t > bt[K - 1] || (t == bt[K - 1] && id > code_id(insts, bc[K - 1])))) return;
+    const Rec r = load_rec(I.geo, l);
+    float t, tl, alpha;
+    if (!hit_surfel(r, o, d, P, t, tl, alpha)) return;
+    const int id = __float_as_int(r.g1.w);
+    if (!key_less(last_t, last_tl, last_id, t, tl, id)) return;
+    if (cnt >= K && !( t < bt[K - 1] || (t == bt[K - 1] && !entry_less(K - 1, t, tl, id)))) return;
     int p = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) p += (bt[j] < t || (bt[j] == t && bt[j] < BIG_F && code_id(insts, bc[j]) < id)) ? 1 : 0;
+    for (int j = 0; j < K; ++j) p += (j < cnt && entry_less(j, t, tl, id)) ? 1 : 0;
 #pragma unroll
     for (int j = K - 1; j > 0; --j)
       if (j > p) { bt[j] = bt[j - 1]; bc[j] = bc[j - 1]; }
@@ -487,18 +599,19 @@ struct FarK {
   float bt[K];
   int bc[K];
   int cnt;
-  float bound_t;
+  float bound_t, bound_tl;
   int bound_id;
   bool inclusive;
   const Inst* insts;
   float3 o, d;
   DevParams P;
 
-  __device__ __forceinline__ void reset(float bt0, int bid, bool incl) {
+  __device__ __forceinline__ void reset(float bt0, float btl, int bid, bool incl) {
 #pragma unroll
     for (int j = 0; j < K; ++j) { bt[j] = -BIG_F; bc[j] = 0; }
     cnt = 0;
     bound_t = bt0;
+    bound_tl = btl;
     bound_id = bid;
     inclusive = incl;
   }
@@ -506,18 +619,27 @@ struct FarK {
   __device__ __forceinline__ float thi() const { return bound_t; }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
+  // entry j's key greater than (t, tl, id)?
+  __device__ __forceinline__ bool entry_greater(int j, float t, float tl, int id) const {
+    if (bt[j] != t) return bt[j] > t;
+    float etl;
+    int eid;
+    code_tail(insts, bc[j], o, d, P, etl, eid);
+    return key_less(t, tl, id, t, etl, eid);
+  }
   __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
-    const float4* g = I.geo + 3 * l;
-    const float4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
-    float t, alpha;
-    if (!hit_surfel(g0, g1, g2, o, d, P, t, alpha)) return;
-    const int id = __float_as_int(g1.w);
-    if (t > bound_t || (t == bound_t && (inclusive ? id > bound_id : id >= bound_id))) return;
-    if (cnt >= K && (t < bt[K - 1] || (t == bt[K - 1] && id < code_id(insts, bc[K - 1])))) return;
+    const Rec r = load_rec(I.geo, l);
+    float t, tl, alpha;
+    if (!hit_surfel(r, o, d, P, t, tl, alpha)) return;
+    const int id = __float_as_int(r.g1.w);
+    // must be below the bound (or equal to it on the inclusive first round)
+    const bool below = key_less(t, tl, id, bound_t, bound_tl, bound_id);
+    const bool equal = t == bound_t && tl == bound_tl && id == bound_id;
+    if (!(below || (inclusive && equal))) return;
+    if (cnt >= K && !(t > bt[K - 1] || (t == bt[K - 1] && !entry_greater(K - 1, t, tl, id)))) return;
     int p = 0;  // entries with a larger key come first
 #pragma unroll
-    for (int j = 0; j < K; ++j)
-      p += (bt[j] > t || (bt[j] == t && bt[j] > -BIG_F && code_id(insts, bc[j]) > id)) ? 1 : 0;
+    for (int j = 0; j < K; ++j) p += (j < cnt && entry_greater(j, t, tl, id)) ? 1 : 0;
 #pragma unroll
     for (int j = K - 1; j > 0; --j)
       if (j > p) { bt[j] = bt[j - 1]; bc[j] = bc[j - 1]; }
@@ -540,9 +662,9 @@ struct ShadowV {
   __device__ __forceinline__ bool done() const { return stop; }
   __device__ __forceinline__ void abort() { stop = true; }
   __device__ __forceinline__ void leaf(int, int l, const Inst& I) {
-    const float4* g = I.geo + 3 * l;
-    float t, alpha;
-    if (!hit_surfel(__ldg(g), __ldg(g + 1), __ldg(g + 2), o, d, P, t, alpha)) return;
+    const Rec r = load_rec(I.geo, l);
+    float t, tl, alpha;
+    if (!hit_surfel(r, o, d, P, t, tl, alpha)) return;
     V *= (1.0f - alpha);
     if (V < P.T_min) { V = 0.0f; stop = true; }
   }
@@ -564,7 +686,7 @@ __device__ __forceinline__ float trace_shadow(const Inst* insts, int n_inst, flo
 
 // Composited surface record of one ray (Eq. 7).
 struct Surface {
-  float T, W, depth, m, r, nlen, t_stop;
+  float T, W, depth, m, r, nlen, t_stop, t_stop_lo;
   float3 x, n, a;
   float3 Sa;  // sum w a (un-normalised)
   int hits, id_stop;
@@ -583,12 +705,12 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
   float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
   float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
   int hits = 0, id_stop = -1;
-  float t_stop = 0.0f;
-  float last_t = -BIG_F;
+  float t_stop = 0.0f, t_stop_lo = 0.0f;
+  float last_t = -BIG_F, last_tl = 0.0f;
   int last_id = -1;
   bool done = false;
   for (int round = 0; round < P.max_rounds && !done; ++round) {
-    kb.reset(last_t, last_id);
+    kb.reset(last_t, last_tl, last_id);
     traverse(insts, n_inst, ray, kb, stack, stride, status, cnt);
     const int n = kb.cnt;
 #pragma unroll
@@ -597,11 +719,11 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
         const int code = kb.bc[j];
         const Inst& I = insts[code >> 24];
         const int l = code & 0xffffff;
-        const float4 g0 = __ldg(I.geo + 3 * l), g1 = __ldg(I.geo + 3 * l + 1), g2 = __ldg(I.geo + 3 * l + 2);
+        const Rec rc = load_rec(I.geo, l);
         const float4 mt = __ldg(I.mat + l);
-        float t, alpha;
-        hit_surfel(g0, g1, g2, o, d, P, t, alpha);
-        const float3 nj = record_normal(g1, g2, d);
+        float t, tl, alpha;
+        hit_surfel(rc, o, d, P, t, tl, alpha);
+        const float3 nj = record_normal(rc, d);
         const float w = T * alpha;
         W += w;
         add3(Sx, (o + d * t) * w);
@@ -609,18 +731,19 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
         add3(Sn, nj * w);
         add3(Sa, f3(mt.x, mt.y, mt.z) * w);
         Sm += w * mt.w;
-        Sr += w * g2.w;
+        Sr += w * rc.g2.w;
         T *= (1.0f - alpha);
         ++hits;
         t_stop = t;
-        id_stop = __float_as_int(g1.w);
+        t_stop_lo = tl;
+        id_stop = __float_as_int(rc.g1.w);
         if (T < P.T_min) done = true;
       }
     }
     if (!done && n < K) done = true;
     if (!done) {
       last_t = kb.bt[K - 1];
-      last_id = code_id(insts, kb.bc[K - 1]);
+      code_tail(insts, kb.bc[K - 1], o, d, P, last_tl, last_id);
       if (round == P.max_rounds - 1) report(status, LF_ERR_ROUND_LIMIT);
     }
   }
@@ -640,6 +763,7 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
   s.hits = hits;
   s.id_stop = id_stop;
   s.t_stop = t_stop;
+  s.t_stop_lo = t_stop_lo;
 }
 
 }  // namespace lf

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(TB) k_trace_primary(TraceArgs a, CamDev cam, f
   g[LF_CH_TSTOP * P] = s.t_stop;
   g[LF_CH_IDSTOP * P] = (float)s.id_stop;
   g[(LF_CH_DIR + 0) * P] = d.x; g[(LF_CH_DIR + 1) * P] = d.y; g[(LF_CH_DIR + 2) * P] = d.z;
+  g[LF_CH_TSTOP_LO * P] = s.t_stop_lo;
   add_counters(a.counters, cnt, (unsigned)s.hits, 1u);
 }
 

@@ -13,17 +13,24 @@ import oracle
 MG = {n: i for i, n in enumerate(oracle.MARGINS)}
 OCH = {n: i for i, n in enumerate(oracle.CHANNELS)}
 
-# Relative margins under which a pixel is flagged.  The FP32 kernel computes
-# u^2 + v^2, alpha~ and T with relative errors of a few 1e-6 at most; ties
-# within 1e-6 (relative) may reorder; the cosine tests decide on FP32 dot
-# products of unit vectors.
-FLAG = dict(support=2e-5, alpha=2e-5, tmin=1e-3, tie=1e-6, stop=2e-5, cos=2e-6, frame=2e-6)
+# Relative margins under which a pixel is flagged.
+#  Primary rays are the same FP32 ray on both sides and the kernel evaluates
+#  depth and u^2 + v^2 in double-float, so only FP32 storage of the packed
+#  axes (~1e-7), the FP32 exp and the FP32 transmittance product remain.
+#  Shading rays start from an FP32 composite and FP32-sampled directions
+#  (~1e-7 relative), which moves hit points by up to ~3e-5 of the smallest
+#  surfel scale.
+FLAG = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-10, stop=2e-5, cos=2e-6, frame=2e-6)
+FLAG_SHADE = dict(support=4e-5, alpha=4e-5, tmin=1e-3, tie=1e-8, stop=2e-5, cos=2e-6, frame=2e-6)
 
 
-def flagged(margins, kinds=FLAG):
+def flagged(margins, kinds=FLAG, margins_shade=None, kinds_shade=FLAG_SHADE):
     f = np.zeros(len(margins), bool)
     for k, thr in kinds.items():
         f |= margins[:, MG[k]] < thr
+    if margins_shade is not None:
+        for k, thr in kinds_shade.items():
+            f |= margins_shade[:, MG[k]] < thr
     return f
 
 
