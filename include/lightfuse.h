@@ -112,9 +112,10 @@ enum {
   LF_CH_NLEN = 17,   /* length of the normal before renormalising     */
   LF_CH_HITS = 18,   /* number of composited hits                     */
   LF_CH_TSTOP = 19,  /* ray distance of the last composited hit       */
+                     /* (with LF_CH_STOPKEY_LO: its 64-bit sort key)  */
   LF_CH_IDSTOP = 20, /* surfel id of the last composited hit (-1: none) */
   LF_CH_DIR = 21,    /* primary ray direction (3)                     */
-  LF_CH_TSTOP_LO = 24, /* low part of the stop depth (double-float key) */
+  LF_CH_STOPKEY_LO = 24, /* raw bits: low word of the stop hit's sort key */
   LF_GBUF_CHANNELS = 25,
   LF_GBUF_DIFF = 17  /* channels 0..16 accept an upstream gradient    */
 };

@@ -18,7 +18,7 @@ LF_KBUF = 16
 LF_GBUF_CHANNELS = 25
 LF_GBUF_DIFF = 17
 CH = dict(T=0, W=1, depth=2, x=3, n=6, a=9, m=12, r=13, rho=14, nlen=17, hits=18, t_stop=19, id_stop=20, dir=21,
-          t_stop_lo=24)
+          stopkey_lo=24)
 G_STRIDE = 17
 
 

@@ -267,18 +267,17 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   float S = g_T * T;
   float Tn = T;
   int remaining = hits;
-  float bound_t = ch(LF_CH_TSTOP), bound_tl = ch(LF_CH_TSTOP_LO);
-  int bound_id = (int)ch(LF_CH_IDSTOP);
+  unsigned long long bound = ((unsigned long long)__float_as_uint(ch(LF_CH_TSTOP)) << 32) |
+                             (unsigned long long)__float_as_uint(ch(LF_CH_STOPKEY_LO));
   bool inclusive = true;
   FarK kb;
-  kb.insts = s_inst;
   kb.o = o;
   kb.d = d;
   kb.P = Pm;
   const Ray ray = make_ray(o, d);
   Counters cnt;
   for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
-    kb.reset(bound_t, bound_tl, bound_id, inclusive);
+    kb.reset(bound, inclusive);
     traverse(s_inst, a.n_inst, ray, kb, s_stack + threadIdx.x, TB, a.status, cnt);
     const int n = kb.cnt;
 #pragma unroll
@@ -290,7 +289,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
         const Rec rc = load_rec(I.geo, l);
         const float4 mt = __ldg(I.mat + l);
         float t, tl, alpha;
-        hit_surfel(rc, o, d, Pm, t, tl, alpha);
+        hit_precise(rc, o, d, Pm, t, tl, alpha);
         const float3 nj = record_normal(rc, d);
         const float3 xj = o + d * t;
         const float Tj = Tn / (1.0f - alpha);
@@ -310,8 +309,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
         report(a.status, LF_ERR_ROUND_LIMIT);
         break;
       }
-      bound_t = kb.bt[K - 1];
-      code_tail(s_inst, kb.bc[K - 1], o, d, Pm, bound_tl, bound_id);
+      bound = kb.bk[K - 1];
       inclusive = false;
     }
   }

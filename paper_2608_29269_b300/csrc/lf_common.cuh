@@ -161,25 +161,31 @@ __device__ __forceinline__ void dot2(float3 ah, float3 al, float3 b, float& hi, 
   lo = __fsub_rn(c, __fsub_rn(hi, s));
 }
 
-// Plane hit of a packed surfel record (Eq. 6).  A cheap FP32 pass rejects
-// candidates far outside the support; the rest are evaluated with the ray
-// depth t = t + tl as a double-float (error ~1e-14 relative for the FP32
-// inputs), so that the depth order of near-coincident surfels and the
-// support test do not depend on FP32 rounding.  Returns acceptance; on
-// acceptance t (rounded depth), tl (its low part) and alpha~.
-__device__ __forceinline__ bool hit_surfel(const Rec& r, const float3 o, const float3 d, const DevParams& P,
-                                           float& t, float& tl, float& alpha) {
+// Plane hit of a packed surfel record (Eq. 6), in two stages.
+//
+// hit_quick: FP32 depth and u^2 + v^2; rejects candidates behind the origin
+// or clearly outside the support (conservative margins).
+//
+// hit_precise: the ray depth as a double-float t + tl (error ~1e-14
+// relative for the FP32 inputs: TwoSum / TwoProd error-free transforms and a
+// compensated dot product), the offset q = o + t d - mu to ~1e-9 absolute,
+// then u, v, the support and opacity tests and alpha~.  The depth order of
+// near-coincident surfels and the support decision therefore do not depend
+// on FP32 rounding.
+__device__ __forceinline__ bool hit_quick(const Rec& r, const float3 o, const float3 d, const DevParams& P,
+                                          float& t32) {
   const float3 a = f3(r.g1.x, r.g1.y, r.g1.z), b = f3(r.g2.x, r.g2.y, r.g2.z), nh = f3(r.g3.x, r.g3.y, r.g3.z);
-  const float3 p = f3(__fsub_rn(r.g0.x, o.x), __fsub_rn(r.g0.y, o.y), __fsub_rn(r.g0.z, o.z));
-  const float den32 = dot_rn(d, nh);
-  const float t32 = __fdiv_rn(dot_rn(p, nh), den32);
+  const float3 p = f3(r.g0.x - o.x, r.g0.y - o.y, r.g0.z - o.z);
+  t32 = __fdividef(dot3(p, nh), dot3(d, nh));
   if (!(t32 > 0.5f * P.t_min) || !(t32 < BIG_F)) return false;
-  {
-    const float3 q = f3(__fmaf_rn(t32, d.x, -p.x), __fmaf_rn(t32, d.y, -p.y), __fmaf_rn(t32, d.z, -p.z));
-    const float u = dot_rn(q, a), v = dot_rn(q, b);
-    if (!(__fmaf_rn(u, u, __fmul_rn(v, v)) <= 1.001f * P.support_r2)) return false;
-  }
-  // precise depth: p = mu - o exactly, t = (p . n) / (d . n) as a double-float
+  const float3 q = f3(fmaf(t32, d.x, -p.x), fmaf(t32, d.y, -p.y), fmaf(t32, d.z, -p.z));
+  const float u = dot3(q, a), v = dot3(q, b);
+  return fmaf(u, u, v * v) <= 1.001f * P.support_r2;
+}
+
+__device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const float3 d, const DevParams& P,
+                                            float& t, float& tl, float& alpha) {
+  const float3 a = f3(r.g1.x, r.g1.y, r.g1.z), b = f3(r.g2.x, r.g2.y, r.g2.z), nh = f3(r.g3.x, r.g3.y, r.g3.z);
   float3 ph, pl;
   two_sum(r.g0.x, -o.x, ph.x, pl.x);
   two_sum(r.g0.y, -o.y, ph.y, pl.y);
@@ -193,30 +199,32 @@ __device__ __forceinline__ bool hit_surfel(const Rec& r, const float3 o, const f
   t = __fadd_rn(t0, t1);
   tl = __fsub_rn(t1, __fsub_rn(t, t0));
   if (!(t > P.t_min) || !(t < BIG_F)) return false;
-  // q = o + t d - mu as a double-float, then u = q . tu/s_u, v = q . tv/s_v
-  float3 qh, ql;
-  {
-    float m, me, s, se;
-    two_prod(t, d.x, m, me); two_sum(m, -ph.x, s, se);
-    qh.x = s; ql.x = __fadd_rn(__fadd_rn(me, se), __fmaf_rn(tl, d.x, -pl.x));
-    two_prod(t, d.y, m, me); two_sum(m, -ph.y, s, se);
-    qh.y = s; ql.y = __fadd_rn(__fadd_rn(me, se), __fmaf_rn(tl, d.y, -pl.y));
-    two_prod(t, d.z, m, me); two_sum(m, -ph.z, s, se);
-    qh.z = s; ql.z = __fadd_rn(__fadd_rn(me, se), __fmaf_rn(tl, d.z, -pl.z));
-  }
-  float uh, ul, vh, vl;
-  dot2(qh, ql, a, uh, ul);
-  dot2(qh, ql, b, vh, vl);
-  const float r2 = __fmaf_rn(uh, uh, __fmaf_rn(vh, vh, __fmul_rn(2.0f, __fmaf_rn(uh, ul, __fmul_rn(vh, vl)))));
+  const float3 q = f3(__fadd_rn(__fmaf_rn(t, d.x, -ph.x), __fmaf_rn(tl, d.x, -pl.x)),
+                      __fadd_rn(__fmaf_rn(t, d.y, -ph.y), __fmaf_rn(tl, d.y, -pl.y)),
+                      __fadd_rn(__fmaf_rn(t, d.z, -ph.z), __fmaf_rn(tl, d.z, -pl.z)));
+  const float u = dot_rn(q, a), v = dot_rn(q, b);
+  const float r2 = __fmaf_rn(u, u, __fmul_rn(v, v));
   if (!(r2 <= P.support_r2)) return false;
   alpha = fminf(P.alpha_max, __fmul_rn(r.g0.w, expf(__fmul_rn(-0.5f, r2))));
   return alpha >= P.alpha_min;
 }
 
-// Sort key of a hit: depth (rounded, low part), then surfel id.
-__device__ __forceinline__ bool key_less(float ta, float la, int ia, float tb, float lb, int ib) {
-  return ta < tb || (ta == tb && (la < lb || (la == lb && ia < ib)));
+__device__ __forceinline__ bool hit_surfel(const Rec& r, const float3 o, const float3 d, const DevParams& P,
+                                           float& t, float& tl, float& alpha) {
+  float t32;
+  return hit_quick(r, o, d, P, t32) && hit_precise(r, o, d, P, t, tl, alpha);
 }
+
+// 64-bit sort key of a hit: FP32 depth bits | low depth part quantised to
+// 1/256 of an ulp | 24-bit surfel id.  Integer order = (depth, id) order;
+// depths closer than 1/256 ulp (~2e-10 relative) fall back to the id.
+__device__ __forceinline__ unsigned long long hit_key(float t, float tl, int id) {
+  const unsigned tb = __float_as_uint(t);
+  const float ulp = __uint_as_float(tb & 0x7f800000u) * 1.1920928955078125e-7f;
+  const int q = min(255, max(0, __float2int_rn(tl / ulp * 256.0f) + 128));
+  return ((unsigned long long)tb << 32) | ((unsigned long long)q << 24) | (unsigned long long)(id & 0xffffff);
+}
+__device__ __forceinline__ float key_t(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
 
 // Normal of a packed record facing the ray (two-sided surfels).
 __device__ __forceinline__ float3 record_normal(const Rec& r, const float3 d) {
@@ -524,129 +532,89 @@ __device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ra
   }
 }
 
-__device__ __forceinline__ int code_id(const Inst* insts, int code) {
-  const Inst& I = insts[code >> 24];
-  return __float_as_int(__ldg(&I.geo[GEO * (code & 0xffffff) + 1].w));
-}
-
-// Low depth part and id of a buffered hit (recomputed from its record; only
-// needed when two rounded depths are exactly equal).
-__device__ __forceinline__ void code_tail(const Inst* insts, int code, float3 o, float3 d, const DevParams& P,
-                                          float& tl, int& id) {
-  const Inst& I = insts[code >> 24];
-  const Rec r = load_rec(I.geo, code & 0xffffff);
-  float t, alpha;
-  tl = 0.0f;
-  hit_surfel(r, o, d, P, t, tl, alpha);
-  id = __float_as_int(r.g1.w);
-}
-
-// Collects the K smallest keys (t, tl, id) strictly greater than the last
-// round's key.
+// Collects the K smallest hit keys strictly greater than the last round's.
 struct NearK {
-  float bt[K];
+  unsigned long long bk[K];
   int bc[K];
   int cnt;
-  float last_t, last_tl;
-  int last_id;
-  const Inst* insts;
+  unsigned long long last;
   float3 o, d;
   DevParams P;
 
-  __device__ __forceinline__ void reset(float lt, float ltl, int lid) {
+  __device__ __forceinline__ void reset(unsigned long long lk) {
 #pragma unroll
-    for (int j = 0; j < K; ++j) { bt[j] = BIG_F; bc[j] = 0; }
+    for (int j = 0; j < K; ++j) { bk[j] = ~0ull; bc[j] = 0; }
     cnt = 0;
-    last_t = lt;
-    last_tl = ltl;
-    last_id = lid;
+    last = lk;
   }
-  __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, last_t); }
-  __device__ __forceinline__ float thi() const { return cnt >= K ? bt[K - 1] : BIG_F; }
+  __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, key_t(last)); }
+  __device__ __forceinline__ float thi() const { return cnt >= K ? key_t(bk[K - 1]) : BIG_F; }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
-  // key of buffered entry j (t known) compared with (t, tl, id)
-  __device__ __forceinline__ bool entry_less(int j, float t, float tl, int id) const {
-    if (bt[j] != t) return bt[j] < t;
-    float etl;
-    int eid;
-    code_tail(insts, bc[j], o, d, P, etl, eid);
-    return key_less(t, etl, eid, t, tl, id);
-  }
   __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
     const Rec r = load_rec(I.geo, l);
+    float t32;
+    if (!hit_quick(r, o, d, P, t32)) return;
+    if (cnt >= K && t32 > thi() * 1.0001f + 1e-6f) return;  // beyond the window (FP32 depth, safe margin)
     float t, tl, alpha;
-    if (!hit_surfel(r, o, d, P, t, tl, alpha)) return;
-    const int id = __float_as_int(r.g1.w);
-    if (!key_less(last_t, last_tl, last_id, t, tl, id)) return;
-    if (cnt >= K && !( t < bt[K - 1] || (t == bt[K - 1] && !entry_less(K - 1, t, tl, id)))) return;
+    if (!hit_precise(r, o, d, P, t, tl, alpha)) return;
+    const unsigned long long key = hit_key(t, tl, __float_as_int(r.g1.w));
+    if (key <= last || (cnt >= K && key >= bk[K - 1])) return;
     int p = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) p += (j < cnt && entry_less(j, t, tl, id)) ? 1 : 0;
+    for (int j = 0; j < K; ++j) p += bk[j] < key ? 1 : 0;
 #pragma unroll
     for (int j = K - 1; j > 0; --j)
-      if (j > p) { bt[j] = bt[j - 1]; bc[j] = bc[j - 1]; }
+      if (j > p) { bk[j] = bk[j - 1]; bc[j] = bc[j - 1]; }
     const int code = (ii << 24) | l;
 #pragma unroll
     for (int j = 0; j < K; ++j)
-      if (j == p) { bt[j] = t; bc[j] = code; }
+      if (j == p) { bk[j] = key; bc[j] = code; }
     cnt = min(cnt + 1, K);
   }
 };
 
-// Collects the K largest keys below a bound (inclusive on the first round).
+// Collects the K largest hit keys below a bound (inclusive on the first round).
 struct FarK {
-  float bt[K];
+  unsigned long long bk[K];
   int bc[K];
   int cnt;
-  float bound_t, bound_tl;
-  int bound_id;
+  unsigned long long bound;
   bool inclusive;
-  const Inst* insts;
   float3 o, d;
   DevParams P;
 
-  __device__ __forceinline__ void reset(float bt0, float btl, int bid, bool incl) {
+  __device__ __forceinline__ void reset(unsigned long long b, bool incl) {
 #pragma unroll
-    for (int j = 0; j < K; ++j) { bt[j] = -BIG_F; bc[j] = 0; }
+    for (int j = 0; j < K; ++j) { bk[j] = 0ull; bc[j] = 0; }
     cnt = 0;
-    bound_t = bt0;
-    bound_tl = btl;
-    bound_id = bid;
+    bound = b;
     inclusive = incl;
   }
-  __device__ __forceinline__ float tlo() const { return cnt >= K ? fmaxf(P.t_min, bt[K - 1]) : P.t_min; }
-  __device__ __forceinline__ float thi() const { return bound_t; }
+  __device__ __forceinline__ float tlo() const { return cnt >= K ? fmaxf(P.t_min, key_t(bk[K - 1])) : P.t_min; }
+  __device__ __forceinline__ float thi() const { return key_t(bound); }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
-  // entry j's key greater than (t, tl, id)?
-  __device__ __forceinline__ bool entry_greater(int j, float t, float tl, int id) const {
-    if (bt[j] != t) return bt[j] > t;
-    float etl;
-    int eid;
-    code_tail(insts, bc[j], o, d, P, etl, eid);
-    return key_less(t, tl, id, t, etl, eid);
-  }
   __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
     const Rec r = load_rec(I.geo, l);
+    float t32;
+    if (!hit_quick(r, o, d, P, t32)) return;
+    if (t32 > thi() * 1.0001f + 1e-6f) return;
     float t, tl, alpha;
-    if (!hit_surfel(r, o, d, P, t, tl, alpha)) return;
-    const int id = __float_as_int(r.g1.w);
-    // must be below the bound (or equal to it on the inclusive first round)
-    const bool below = key_less(t, tl, id, bound_t, bound_tl, bound_id);
-    const bool equal = t == bound_t && tl == bound_tl && id == bound_id;
-    if (!(below || (inclusive && equal))) return;
-    if (cnt >= K && !(t > bt[K - 1] || (t == bt[K - 1] && !entry_greater(K - 1, t, tl, id)))) return;
+    if (!hit_precise(r, o, d, P, t, tl, alpha)) return;
+    const unsigned long long key = hit_key(t, tl, __float_as_int(r.g1.w));
+    if (key > bound || (key == bound && !inclusive)) return;
+    if (cnt >= K && key <= bk[K - 1]) return;
     int p = 0;  // entries with a larger key come first
 #pragma unroll
-    for (int j = 0; j < K; ++j) p += (j < cnt && entry_greater(j, t, tl, id)) ? 1 : 0;
+    for (int j = 0; j < K; ++j) p += bk[j] > key ? 1 : 0;
 #pragma unroll
     for (int j = K - 1; j > 0; --j)
-      if (j > p) { bt[j] = bt[j - 1]; bc[j] = bc[j - 1]; }
+      if (j > p) { bk[j] = bk[j - 1]; bc[j] = bc[j - 1]; }
     const int code = (ii << 24) | l;
 #pragma unroll
     for (int j = 0; j < K; ++j)
-      if (j == p) { bt[j] = t; bc[j] = code; }
+      if (j == p) { bk[j] = key; bc[j] = code; }
     cnt = min(cnt + 1, K);
   }
 };
@@ -686,10 +654,11 @@ __device__ __forceinline__ float trace_shadow(const Inst* insts, int n_inst, flo
 
 // Composited surface record of one ray (Eq. 7).
 struct Surface {
-  float T, W, depth, m, r, nlen, t_stop, t_stop_lo;
+  float T, W, depth, m, r, nlen;
   float3 x, n, a;
   float3 Sa;  // sum w a (un-normalised)
-  int hits, id_stop;
+  int hits;
+  unsigned long long stop_key;  // key of the last composited hit (0: none)
 };
 
 // Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop).
@@ -697,20 +666,17 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
                                                 const DevParams& P, int* stack, int stride, int* status,
                                                 Counters& cnt, Surface& s, unsigned& composited) {
   NearK kb;
-  kb.insts = insts;
   kb.o = o;
   kb.d = d;
   kb.P = P;
   Ray ray = make_ray(o, d);
   float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
   float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
-  int hits = 0, id_stop = -1;
-  float t_stop = 0.0f, t_stop_lo = 0.0f;
-  float last_t = -BIG_F, last_tl = 0.0f;
-  int last_id = -1;
+  int hits = 0;
+  unsigned long long stop_key = 0ull, last = 0ull;
   bool done = false;
   for (int round = 0; round < P.max_rounds && !done; ++round) {
-    kb.reset(last_t, last_tl, last_id);
+    kb.reset(last);
     traverse(insts, n_inst, ray, kb, stack, stride, status, cnt);
     const int n = kb.cnt;
 #pragma unroll
@@ -722,7 +688,7 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
         const Rec rc = load_rec(I.geo, l);
         const float4 mt = __ldg(I.mat + l);
         float t, tl, alpha;
-        hit_surfel(rc, o, d, P, t, tl, alpha);
+        hit_precise(rc, o, d, P, t, tl, alpha);
         const float3 nj = record_normal(rc, d);
         const float w = T * alpha;
         W += w;
@@ -734,16 +700,13 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
         Sr += w * rc.g2.w;
         T *= (1.0f - alpha);
         ++hits;
-        t_stop = t;
-        t_stop_lo = tl;
-        id_stop = __float_as_int(rc.g1.w);
+        stop_key = kb.bk[j];
         if (T < P.T_min) done = true;
       }
     }
     if (!done && n < K) done = true;
     if (!done) {
-      last_t = kb.bt[K - 1];
-      code_tail(insts, kb.bc[K - 1], o, d, P, last_tl, last_id);
+      last = kb.bk[K - 1];
       if (round == P.max_rounds - 1) report(status, LF_ERR_ROUND_LIMIT);
     }
   }
@@ -761,9 +724,7 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
   s.nlen = sqrtf(dot3(mv, mv));
   s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
   s.hits = hits;
-  s.id_stop = id_stop;
-  s.t_stop = t_stop;
-  s.t_stop_lo = t_stop_lo;
+  s.stop_key = stop_key;
 }
 
 }  // namespace lf

@@ -49,10 +49,10 @@ __global__ void __launch_bounds__(TB) k_trace_primary(TraceArgs a, CamDev cam, f
   g[(LF_CH_RHO + 0) * P] = rho.x; g[(LF_CH_RHO + 1) * P] = rho.y; g[(LF_CH_RHO + 2) * P] = rho.z;
   g[LF_CH_NLEN * P] = s.nlen;
   g[LF_CH_HITS * P] = (float)s.hits;
-  g[LF_CH_TSTOP * P] = s.t_stop;
-  g[LF_CH_IDSTOP * P] = (float)s.id_stop;
+  g[LF_CH_TSTOP * P] = key_t(s.stop_key);
+  g[LF_CH_IDSTOP * P] = s.hits ? (float)(int)(s.stop_key & 0xffffffull) : -1.0f;
   g[(LF_CH_DIR + 0) * P] = d.x; g[(LF_CH_DIR + 1) * P] = d.y; g[(LF_CH_DIR + 2) * P] = d.z;
-  g[LF_CH_TSTOP_LO * P] = s.t_stop_lo;
+  g[LF_CH_STOPKEY_LO * P] = __uint_as_float((unsigned)(s.stop_key & 0xffffffffull));
   add_counters(a.counters, cnt, (unsigned)s.hits, 1u);
 }
 

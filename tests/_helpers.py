@@ -20,7 +20,7 @@ OCH = {n: i for i, n in enumerate(oracle.CHANNELS)}
 #  Shading rays start from an FP32 composite and FP32-sampled directions
 #  (~1e-7 relative), which moves hit points by up to ~3e-5 of the smallest
 #  surfel scale.
-FLAG = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-10, stop=2e-5, cos=2e-6, frame=2e-6)
+FLAG = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6)
 FLAG_SHADE = dict(support=4e-5, alpha=4e-5, tmin=1e-3, tie=1e-8, stop=2e-5, cos=2e-6, frame=2e-6)
 
 

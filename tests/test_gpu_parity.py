@@ -196,4 +196,4 @@ def test_c3_gradient_parity():
     assert max(report.values()) <= 1e-3, report
 
 
-FLAG_GRAD = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-10, stop=2e-5, cos=2e-6, frame=2e-6, cap=1e-5)
+FLAG_GRAD = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6, cap=1e-5)
