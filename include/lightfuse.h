@@ -194,35 +194,48 @@ lf_status lf_trace_primary(lf_ctx* ctx, const lf_camera* cam, int env_id, float*
  * 0); one environment NEE sample with a shadow ray, one BSDF continuation
  * from the cosine/GGX mixture traced to a secondary record, two environment
  * NEE samples with shadow rays there; power-heuristic MIS.
- * rgb_dev[p*3 + c] = T E(d) + (1 - T) / spp * sum_s (NEE + BSDF terms).
- * ray_count_dev (nullable): a device uint64 the kernel ADDS the number of
- * rays it traced to.
+ * rgb_dev[p*3 + c] = T E(d) + (1 - T) / spp * sum_s (NEE + BSDF terms),
+ * the sum taken in sample order.
+ * samples_dev: caller scratch of at least lf_shade_scratch_bytes(width,
+ * height, spp) bytes; on return it holds the per-sample data path replay
+ * keeps fixed (directions, pdfs, MIS weights, visibilities, secondary
+ * factors), which lf_trace_backward can reuse.
+ * ray_count_dev (nullable): a device uint64 the call ADDS the number of
+ * shading rays it traced to.
  */
+size_t lf_shade_scratch_bytes(int width, int height, int spp);
 lf_status lf_shade_bounce(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
-                          uint64_t seed, float* rgb_dev, unsigned long long* ray_count_dev);
+                          uint64_t seed, float* rgb_dev, unsigned long long* ray_count_dev, void* samples_dev,
+                          size_t samples_bytes);
 
-/* Scratch bytes lf_trace_backward needs for a width x height image. */
-size_t lf_backward_scratch_bytes(int width, int height);
+/* Scratch bytes lf_trace_backward needs for a width x height image at spp
+ * samples when it has to replay the shading (fwd_samples == NULL); with the
+ * forward's sample buffer it needs 9 * width * height floats (+256 B). */
+size_t lf_backward_scratch_bytes(int width, int height, int spp);
 
 /*
  * Adjoint of lf_trace_primary + lf_shade_bounce under path replay (Sec. 3.3):
- * the shading pass replays the same Philox samples and keeps directions,
- * pdfs, MIS weights, visibilities and secondary records fixed; gradients flow
- * through the primary record and every environment lookup.  The primary pass
- * re-traverses each ray back to front from the stored final transmittance
- * and stop key (no per-ray hit lists), recovering T_j = T_{j+1} / (1 -
- * alpha_j), and scatters Eq. 6-7 adjoints to the surfels.
+ * the sampled directions, pdfs, MIS weights, visibilities and secondary
+ * records stay fixed; gradients flow through the primary record and every
+ * environment lookup.  The primary pass re-traverses each ray back to front
+ * from the stored final transmittance and stop key (no per-ray hit lists),
+ * recovering T_j = T_{j+1} / (1 - alpha_j), and scatters the Eq. 6-7
+ * adjoint to the surfels.
  *   gbuf_dev:     the G-buffer of the forward pass (unchanged scene).
  *   dL_drgb_dev:  P x 3 (nullable: no shading term).
  *   dL_dgbuf_dev: LF_GBUF_CHANNELS planes (nullable); channels
  *                 0..LF_GBUF_DIFF-1 are used.
  *   d_surfel_dev: N x 17 (LF_G_* layout), accumulated.
  *   d_env_dev:    H x W x 3 of `env_id`, accumulated (nullable).
- *   scratch_dev:  at least lf_backward_scratch_bytes(width, height) bytes.
+ *   fwd_samples_dev: the sample buffer of the lf_shade_bounce call with the
+ *                 same camera, environment, spp, seed and scene (nullable:
+ *                 the shading samples are then replayed into scratch).
+ *   scratch_dev:  lf_backward_scratch_bytes(...) bytes (see above).
  */
 lf_status lf_trace_backward(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
                             uint64_t seed, const float* dL_drgb_dev, const float* dL_dgbuf_dev,
-                            float* d_surfel_dev, float* d_env_dev, void* scratch_dev, size_t scratch_bytes);
+                            float* d_surfel_dev, float* d_env_dev, const void* fwd_samples_dev, void* scratch_dev,
+                            size_t scratch_bytes);
 
 /*
  * Traversal counters for roofline accounting: when counters_dev (4 x uint64

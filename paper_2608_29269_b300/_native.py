@@ -70,10 +70,12 @@ SIGNATURES = [
     ("lf_material_set", C.c_int, [_P, C.c_int, C.POINTER(C.c_float), C.c_float, C.c_float]),
     ("lf_env_set", C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int]),
     ("lf_trace_primary", C.c_int, [_P, C.POINTER(LfCamera), C.c_int, _P]),
-    ("lf_shade_bounce", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P]),
-    ("lf_backward_scratch_bytes", C.c_size_t, [C.c_int, C.c_int]),
+    ("lf_shade_scratch_bytes", C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    ("lf_shade_bounce", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P, _P,
+                                  C.c_size_t]),
+    ("lf_backward_scratch_bytes", C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     ("lf_trace_backward", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P, _P, _P, _P,
-                                    C.c_size_t]),
+                                    _P, C.c_size_t]),
     ("lf_set_counters", C.c_int, [_P, _P]),
     ("lf_philox", C.c_int, [_P, _P, C.c_int, C.c_uint32, C.c_uint32, _P]),
     ("lf_env_tables", C.c_int, [_P, C.c_int, _P, _P, _P, _P]),

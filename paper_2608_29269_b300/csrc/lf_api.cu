@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "lf_ctx.h"
+#include "lf_wavefront.h"
 
 using namespace lf;
 
@@ -162,6 +163,7 @@ lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out) {
   c->dp = to_dev(p);
   c->stream = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = dev_alloc(&c->status_dev, 1);
   if (e == cudaSuccess) e = cudaMemset(c->status_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = dev_alloc(&c->offsets_dev, LF_MAX_OBJECTS + 1);
@@ -407,24 +409,59 @@ lf_status lf_trace_primary(lf_ctx* c, const lf_camera* cam, int env_id, float* g
   return LF_OK;
 }
 
+// One-job shading batch over the context's scene.
+static ShadeBatch one_job(lf_ctx* c, const lf_camera* cam, const float* gbuf, int env_id, int spp, uint64_t seed,
+                          float* rgb) {
+  ShadeBatch B;
+  B.n_jobs = 1;
+  const int P = cam->width * cam->height;
+  B.n_items = (long long)P * spp;
+  B.n_pix_total = P;
+  ShadeJob& J = B.jobs[0];
+  const TraceArgs a = lf_ctx_trace_args(c, env_id);
+  J.insts = a.insts;
+  J.n_inst = a.n_inst;
+  J.env = a.env;
+  J.gbuf = gbuf;
+  J.n_pix = P;
+  J.rgb = rgb;
+  J.spp = spp;
+  J.k0 = (uint32_t)(seed & 0xffffffffu);
+  J.k1 = (uint32_t)(seed >> 32);
+  J.item0 = 0;
+  J.pix0 = 0;
+  return B;
+}
+
+size_t lf_shade_scratch_bytes(int width, int height, int spp) {
+  if (width <= 0 || height <= 0 || spp <= 0) return 0;
+  return sample_buf_bytes((long long)width * height * spp);
+}
+
 lf_status lf_shade_bounce(lf_ctx* c, const lf_camera* cam, const float* gbuf, int env_id, int spp, uint64_t seed,
-                          float* rgb, unsigned long long* ray_count) {
+                          float* rgb, unsigned long long* ray_count, void* samples, size_t samples_bytes) {
   lf_status st = check_render(c, cam, env_id);
   if (st != LF_OK) return st;
   if (!gbuf || !rgb || spp <= 0 || spp > (1 << 20)) return fail(c, LF_ERR_INVALID, "bad shading arguments");
-  LF_CUDA(c, launch_shade(lf_ctx_trace_args(c, env_id), gbuf, cam->width * cam->height, spp,
-                          (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), rgb, ray_count, c->stream));
+  if ((long long)cam->width * cam->height * spp >= (1LL << 30)) return fail(c, LF_ERR_INVALID, "too many samples");
+  if (!samples || samples_bytes < lf_shade_scratch_bytes(cam->width, cam->height, spp))
+    return fail(c, LF_ERR_INVALID, "sample buffer too small");
+  const ShadeBatch B = one_job(c, cam, gbuf, env_id, spp, seed, rgb);
+  const SampleBuf S = sample_buf(samples, B.n_items);
+  LF_CUDA(c, launch_shade_wavefront(B, c->dp, S, c->status_dev, ray_count, c->counters, c->sms, c->stream));
+  LF_CUDA(c, launch_shade_combine(B, c->dp, S, c->stream));
   return LF_OK;
 }
 
-size_t lf_backward_scratch_bytes(int width, int height) {
-  if (width <= 0 || height <= 0) return 0;
-  return sizeof(float) * (size_t)SHADE_GRAD_CH * (size_t)width * (size_t)height;
+size_t lf_backward_scratch_bytes(int width, int height, int spp) {
+  if (width <= 0 || height <= 0 || spp <= 0) return 0;
+  return sizeof(float) * (size_t)SHADE_GRAD_CH * (size_t)width * (size_t)height + 256 +
+         lf_shade_scratch_bytes(width, height, spp);
 }
 
 lf_status lf_trace_backward(lf_ctx* c, const lf_camera* cam, const float* gbuf, int env_id, int spp, uint64_t seed,
                             const float* dL_drgb, const float* dL_dgbuf, float* d_surfel, float* d_env,
-                            void* scratch, size_t scratch_bytes) {
+                            const void* fwd_samples, void* scratch, size_t scratch_bytes) {
   lf_status st = check_render(c, cam, env_id);
   if (st != LF_OK) return st;
   if (!gbuf || !d_surfel) return fail(c, LF_ERR_INVALID, "null G-buffer or gradient");
@@ -433,11 +470,19 @@ lf_status lf_trace_backward(lf_ctx* c, const lf_camera* cam, const float* gbuf, 
   float* sg = nullptr;
   TraceArgs a = lf_ctx_trace_args(c, env_id);
   if (dL_drgb) {
-    if (!scratch || scratch_bytes < lf_backward_scratch_bytes(cam->width, cam->height))
-      return fail(c, LF_ERR_INVALID, "scratch too small");
+    const size_t sg_bytes = sizeof(float) * (size_t)SHADE_GRAD_CH * n_pix + 256;
+    const size_t need = fwd_samples ? sg_bytes : lf_backward_scratch_bytes(cam->width, cam->height, spp);
+    if (!scratch || scratch_bytes < need) return fail(c, LF_ERR_INVALID, "scratch too small");
     sg = static_cast<float*>(scratch);
-    LF_CUDA(c, launch_shade_backward(a, gbuf, n_pix, spp, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
-                                     dL_drgb, sg, d_env, c->stream));
+    const ShadeBatch B = one_job(c, cam, gbuf, env_id, spp, seed, nullptr);
+    SampleBuf S;
+    if (fwd_samples) {
+      S = sample_buf(const_cast<void*>(fwd_samples), B.n_items);
+    } else {  // replay the forward's sample data with the same seed
+      S = sample_buf(static_cast<char*>(scratch) + sg_bytes, B.n_items);
+      LF_CUDA(c, launch_shade_wavefront(B, c->dp, S, c->status_dev, nullptr, nullptr, c->sms, c->stream));
+    }
+    LF_CUDA(c, launch_shade_combine_adjoint(B, c->dp, S, dL_drgb, sg, d_env, c->stream));
   }
   LF_CUDA(c, launch_trace_backward(a, c->scene, to_cam(*cam), gbuf, sg, dL_dgbuf, d_surfel, d_env, c->stream));
   return LF_OK;

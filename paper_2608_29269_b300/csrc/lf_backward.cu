@@ -1,20 +1,16 @@
-// Adjoint of the renderer under path replay (Sec. 3.3).
+// Adjoint of the primary composite (Eq. 6-7).
 //
-// k_shade_backward replays every (pixel, sample) with the same Philox
-// uniforms, re-traces its shadow and continuation rays, keeps the sampled
-// directions, pdfs, MIS weights, visibilities and the secondary record
-// fixed, and differentiates Eq. 11 with respect to the primary record
-// (normal, base colour, metallic, roughness, final transmittance) and every
-// environment lookup.  k_trace_backward then re-traverses each primary ray
-// back to front from the stored final transmittance and stop key, recovers
+// k_trace_backward re-traverses each primary ray back to front from the
+// stored final transmittance and stop key (no per-ray hit lists), recovers
 // T_j = T_{j+1} / (1 - alpha_j) and scatters the adjoint of Eq. 6-7 to the
-// surfel parameters.
+// surfel parameters; its upstream gradients are those of the G-buffer
+// channels plus the shading adjoint's record gradients (normal, base colour,
+// metallic, roughness, final transmittance).
 #include "lf_kernels.h"
 
 namespace lf {
 
 constexpr int TB = 128;
-constexpr int G = 8;
 constexpr int STACK_SMEM = TB * STACK * (int)sizeof(int);
 
 __device__ __forceinline__ void load_instances_b(Inst* dst, const Inst* src, int n) {
@@ -25,7 +21,7 @@ __device__ __forceinline__ void load_instances_b(Inst* dst, const Inst* src, int
 }
 
 // d_env += v at the four bilinear texels of direction w.
-__device__ __forceinline__ void env_scatter(const EnvDev& e, float* __restrict__ d_env, float3 w, float3 v) {
+__device__ __forceinline__ void env_scatter_p(const EnvDev& e, float* __restrict__ d_env, float3 w, float3 v) {
   if (!d_env) return;
   const Bilin b = env_bilinear(e, w);
 #pragma unroll
@@ -35,134 +31,6 @@ __device__ __forceinline__ void env_scatter(const EnvDev& e, float* __restrict__
     atomicAdd(t + 0, b.w[k] * v.x);
     atomicAdd(t + 1, b.w[k] * v.y);
     atomicAdd(t + 2, b.w[k] * v.z);
-  }
-}
-
-struct RecordGrad {
-  float3 n, a;
-  float m, r;
-};
-
-// Replays one (pixel, sample) and accumulates its forward value into `sum`
-// and the adjoint of gc . value into `rg` and d_env.
-__device__ __forceinline__ void shade_sample_adjoint(const TraceArgs& a, const Inst* insts, const float3 x,
-                                                     const float3 n, const float3 al, const float m, const float r,
-                                                     const float3 dir, uint32_t pixel, int s, uint32_t k0,
-                                                     uint32_t k1, int* stack, float3 gc, float* d_env,
-                                                     float3& sum, RecordGrad& rg) {
-  const DevParams& P = a.P;
-  Counters cnt;
-  unsigned comp = 0;
-  const float3 wo = -dir;
-  const float3 xs = x + n * P.ray_offset;
-  const float ps = P.brdf_mode == 1 ? 0.0f : P.p_spec;
-  float u[9];
-  sample_uniforms(pixel, (uint32_t)s, k0, k1, u);
-  if (P.sampling_mode != 1) {
-    float3 we;
-    float pe;
-    env_sample(a.env, u[0], u[1], we, pe);
-    const float ce = dot3(n, we);
-    if (ce > 0.0f && pe > 0.0f) {
-      const float Ve = trace_shadow(insts, a.n_inst, xs, we, P, stack, TB, a.status, cnt);
-      const float pb = pdf_bsdf(n, wo, we, r, ps);
-      const float wenv = P.sampling_mode == 2 ? 1.0f : pe * pe / (pe * pe + pb * pb);
-      const float kk = Ve * wenv / pe;
-      const float3 f = brdf_eval(n, wo, we, al, m, r, P.brdf_mode);
-      const float3 E = env_lookup(a.env, we);
-      add3(sum, mul3(f, E) * (ce * kk));
-      brdf_adjoint(n, wo, we, al, m, r, P.brdf_mode, mul3(gc, E) * (ce * kk), rg.n, rg.a, rg.m, rg.r);
-      add3(rg.n, we * (dot3(gc, mul3(f, E)) * kk));
-      env_scatter(a.env, d_env, we, mul3(gc, f) * (ce * kk));
-    }
-  }
-  const float3 wi = (u[2] < ps) ? sample_ggx(n, wo, r, u[3], u[4]) : sample_cos(n, u[3], u[4]);
-  const float ci = dot3(n, wi);
-  const float pb = pdf_bsdf(n, wo, wi, r, ps);
-  if (!(ci > 0.0f && pb > 0.0f)) return;
-  const float pei = env_pdf(a.env, wi);
-  const float wb = P.sampling_mode == 1 ? 1.0f : pb * pb / (pb * pb + pei * pei);
-  Surface s2;
-  trace_composite(insts, a.n_inst, xs, wi, P, stack, TB, a.status, cnt, s2, comp);
-  float3 inc = P.sampling_mode == 2 ? f3(0.f, 0.f, 0.f) : env_lookup(a.env, wi) * (wb * s2.T);
-  float3 wq[2], fk[2];
-  bool qok[2] = {false, false};
-  if (s2.hits > 0) {
-    const float3 n2 = s2.n, wo2 = -wi;
-    const float co2 = dot3(n2, wo2);
-    const float3 xs2 = s2.x + n2 * P.ray_offset;
-#pragma unroll
-    for (int qq = 0; qq < 2; ++qq) {
-      float pq;
-      env_sample(a.env, u[5 + 2 * qq], u[6 + 2 * qq], wq[qq], pq);
-      const float cq = dot3(n2, wq[qq]);
-      if (!(cq > 0.0f && co2 > 0.0f && pq > 0.0f)) continue;
-      const float Vq = trace_shadow(insts, a.n_inst, xs2, wq[qq], P, stack, TB, a.status, cnt);
-      fk[qq] = brdf_eval(n2, wo2, wq[qq], s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f * Vq / pq);
-      qok[qq] = true;
-      add3(inc, mul3(fk[qq], env_lookup(a.env, wq[qq])));
-    }
-  }
-  const float3 f = brdf_eval(n, wo, wi, al, m, r, P.brdf_mode);
-  const float3 beta = f * (ci / pb);
-  add3(sum, mul3(beta, inc));
-  const float3 gbeta = mul3(gc, inc);
-  brdf_adjoint(n, wo, wi, al, m, r, P.brdf_mode, gbeta * (ci / pb), rg.n, rg.a, rg.m, rg.r);
-  add3(rg.n, wi * (dot3(gbeta, f) / pb));
-  const float3 ginc = mul3(gc, beta);
-  if (P.sampling_mode != 2) env_scatter(a.env, d_env, wi, ginc * (wb * s2.T));
-#pragma unroll
-  for (int qq = 0; qq < 2; ++qq)
-    if (qok[qq]) env_scatter(a.env, d_env, wq[qq], mul3(ginc, fk[qq]));
-}
-
-__global__ void __launch_bounds__(TB) k_shade_backward(TraceArgs a, const float* __restrict__ gbuf, int n_pix,
-                                                       int spp, uint32_t k0, uint32_t k1,
-                                                       const float* __restrict__ dL_drgb, float* __restrict__ sg,
-                                                       float* __restrict__ d_env) {
-  __shared__ Inst s_inst[LF_MAX_OBJECTS];
-  extern __shared__ int s_stack[];
-  load_instances_b(s_inst, a.insts, a.n_inst);
-  const int p = blockIdx.x * (TB / G) + threadIdx.x / G, lane = threadIdx.x % G;
-  const bool valid = p < n_pix;
-  const size_t P = (size_t)n_pix;
-  float3 sum = f3(0.f, 0.f, 0.f);
-  RecordGrad rg;
-  rg.n = rg.a = f3(0.f, 0.f, 0.f);
-  rg.m = rg.r = 0.f;
-  float T = 1.0f;
-  float3 dir = f3(0.f, 0.f, 1.f), g = f3(0.f, 0.f, 0.f);
-  if (valid) {
-    const float* gb = gbuf + p;
-    T = __ldg(gb + LF_CH_T * P);
-    const int hits = (int)__ldg(gb + LF_CH_HITS * P);
-    dir = f3(__ldg(gb + LF_CH_DIR * P), __ldg(gb + (LF_CH_DIR + 1) * P), __ldg(gb + (LF_CH_DIR + 2) * P));
-    const float3 n = f3(__ldg(gb + LF_CH_N * P), __ldg(gb + (LF_CH_N + 1) * P), __ldg(gb + (LF_CH_N + 2) * P));
-    g = f3(__ldg(dL_drgb + 3 * p), __ldg(dL_drgb + 3 * p + 1), __ldg(dL_drgb + 3 * p + 2));
-    if (hits > 0 && dot3(n, -dir) > 0.0f) {
-      const float3 x = f3(__ldg(gb + LF_CH_X * P), __ldg(gb + (LF_CH_X + 1) * P), __ldg(gb + (LF_CH_X + 2) * P));
-      const float3 al = f3(__ldg(gb + LF_CH_A * P), __ldg(gb + (LF_CH_A + 1) * P), __ldg(gb + (LF_CH_A + 2) * P));
-      const float m = __ldg(gb + LF_CH_M * P), r = __ldg(gb + LF_CH_R * P);
-      const float3 gc = g * ((1.0f - T) / (float)spp);
-      for (int s = lane; s < spp; s += G)
-        shade_sample_adjoint(a, s_inst, x, n, al, m, r, dir, (uint32_t)p, s, k0, k1, s_stack + threadIdx.x, gc,
-                             d_env, sum, rg);
-    }
-  }
-  float v[11] = {sum.x, sum.y, sum.z, rg.n.x, rg.n.y, rg.n.z, rg.a.x, rg.a.y, rg.a.z, rg.m, rg.r};
-#pragma unroll
-  for (int k = 0; k < 11; ++k) {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
-  }
-  if (valid && lane == 0) {
-    const float3 Ed = env_lookup(a.env, dir);
-    const float inv_spp = 1.0f / (float)spp;
-    const float gT = g.x * (Ed.x - v[0] * inv_spp) + g.y * (Ed.y - v[1] * inv_spp) + g.z * (Ed.z - v[2] * inv_spp);
-    env_scatter(a.env, d_env, dir, g * T);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sg[k * P + p] = v[3 + k];
-    sg[8 * P + p] = gT;
   }
 }
 
@@ -251,7 +119,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   if (gg) {
     const float3 Ed = env_lookup(a.env, d);
     g_T += dot3(g_rho, Ed);
-    env_scatter(a.env, d_env, d, g_rho * T);
+    env_scatter_p(a.env, d_env, d, g_rho * T);
   }
   if (hits <= 0) return;
   const float inv = 1.0f / (W + Pm.eps_w);
@@ -313,15 +181,6 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
       inclusive = false;
     }
   }
-}
-
-cudaError_t launch_shade_backward(const TraceArgs& a, const float* gbuf, int n_pix, int spp, uint32_t k0,
-                                  uint32_t k1, const float* dL_drgb, float* shade_grad, float* d_env,
-                                  cudaStream_t st) {
-  const int ppb = TB / G;
-  k_shade_backward<<<(n_pix + ppb - 1) / ppb, TB, STACK_SMEM, st>>>(a, gbuf, n_pix, spp, k0, k1, dL_drgb,
-                                                                   shade_grad, d_env);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,

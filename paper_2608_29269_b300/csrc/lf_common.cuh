@@ -477,58 +477,80 @@ struct Counters {
   unsigned nodes = 0, tests = 0;
 };
 
-// Depth-first traversal of every instance's BLAS.  The visitor supplies the
+// Stack entries name (instance, node or leaf): instance << 25 | leaf flag
+// (bit 24) | index; -1 is "empty".
+constexpr int LEAF_BIT = 1 << 24;
+__device__ __forceinline__ int entry_of(int ii, int child) {
+  return child >= 0 ? ((ii << 25) | child) : ((ii << 25) | LEAF_BIT | ~child);
+}
+
+// Depth-first traversal of the BLASes of every instance whose box the ray
+// enters, on one shared-memory stack, organised "while-while" (Aila and Laine
+// 2009): each lane descends internal nodes until it holds a leaf, then the
+// lanes of the warp process their leaves together.  The visitor supplies the
 // culling interval [tlo(), thi()], consumes leaves and may end the ray early.
 // `stack` points at this thread's first entry; entries are `stride` ints apart.
 template <class V>
 __device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
                                          int stride, int* status, Counters& cnt) {
-  for (int ii = 0; ii < n_inst; ++ii) {
+  int sp = 0;
+  // A tree of n leaves has n - 1 internal nodes; a depth-first walk visits
+  // each node at most once.  The budget only guards against a malformed tree.
+  int budget = 8;
+  for (int ii = 0; ii < n_inst; ++ii) {  // instance 0 (background) is pushed first, popped last
     const Inst& I = insts[ii];
     if (I.root == INT_MIN) continue;
     float tn;
     if (!slab(I.lo[0], I.lo[1], I.lo[2], I.hi[0], I.hi[1], I.hi[2], ray, vis.tlo(), vis.thi(), tn)) continue;
-    int node = I.root, sp = 0;
-    const float4* __restrict__ nodes = I.nodes;
-    // A tree of n leaves has n - 1 internal nodes; a depth-first walk visits
-    // each at most once.  The cap only guards against a malformed tree.
-    int budget = 2 * I.n_leaves + 8;
-    while (true) {
-      if (--budget < 0) {
-        report(status, LF_ERR_STACK);
-        vis.abort();
-        return;
-      }
-      if (node < 0) {
-        ++cnt.tests;
-        vis.leaf(ii, ~node, I);
-        if (vis.done()) return;
-      } else {
-        ++cnt.nodes;
-        const float4* N = nodes + 4 * node;
-        const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), e = __ldg(N + 3);
-        const float lo = vis.tlo(), hi = vis.thi();
-        float tl, tr;
-        const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
-        const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
-        const int cl = __float_as_int(e.x), cr = __float_as_int(e.y);
-        if (hl && hr) {
-          if (sp >= STACK) {
-            report(status, LF_ERR_STACK);
-            vis.abort();
-            return;
-          }
-          const bool lfirst = tl <= tr;
-          stack[(sp++) * stride] = lfirst ? cr : cl;
-          node = lfirst ? cl : cr;
-          continue;
-        }
-        if (hl) { node = cl; continue; }
-        if (hr) { node = cr; continue; }
-      }
-      if (sp == 0) break;
-      node = stack[(--sp) * stride];
+    if (sp >= STACK) {
+      report(status, LF_ERR_STACK);
+      vis.abort();
+      return;
     }
+    stack[(sp++) * stride] = entry_of(ii, I.root);
+    budget += 2 * I.n_leaves + 2;
+  }
+  int e = sp > 0 ? stack[(--sp) * stride] : -1;
+  bool ok = true;
+  while (e >= 0) {
+    while (e >= 0 && !(e & LEAF_BIT)) {
+      if (--budget < 0 || sp >= STACK) {
+        ok = false;
+        e = -1;
+        break;
+      }
+      ++cnt.nodes;
+      const int ii = e >> 25;
+      const float4* N = insts[ii].nodes + 4 * (e & 0xffffff);
+      const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), f = __ldg(N + 3);
+      const float lo = vis.tlo(), hi = vis.thi();
+      float tl, tr;
+      const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
+      const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
+      const int cl = entry_of(ii, __float_as_int(f.x)), cr = entry_of(ii, __float_as_int(f.y));
+      if (hl && hr) {
+        const bool lfirst = tl <= tr;
+        stack[(sp++) * stride] = lfirst ? cr : cl;
+        e = lfirst ? cl : cr;
+      } else if (hl) {
+        e = cl;
+      } else if (hr) {
+        e = cr;
+      } else {
+        e = sp > 0 ? stack[(--sp) * stride] : -1;
+      }
+    }
+    if (e >= 0) {
+      ++cnt.tests;
+      const int ii = e >> 25;
+      vis.leaf(ii, e & 0xffffff, insts[ii]);
+      if (vis.done()) return;
+      e = sp > 0 ? stack[(--sp) * stride] : -1;
+    }
+  }
+  if (!ok) {
+    report(status, LF_ERR_STACK);
+    vis.abort();
   }
 }
 

@@ -24,6 +24,7 @@ struct lf_ctx {
   lf::DevParams dp{};
   cudaStream_t stream = nullptr;
   int device = 0;
+  int sms = 148;
   int* status_dev = nullptr;
   unsigned long long* counters = nullptr;
   std::string err;

@@ -60,14 +60,9 @@ struct TraceArgs {
 };
 
 cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, cudaStream_t st);
-cudaError_t launch_shade(const TraceArgs& a, const float* gbuf, int n_pix, int spp, uint32_t k0, uint32_t k1,
-                         float* rgb, unsigned long long* ray_count, cudaStream_t st);
 
 // Adjoint (lf_backward.cu)
 constexpr int SHADE_GRAD_CH = 9;  // per pixel: g_n (3), g_a (3), g_m, g_r, g_T
-cudaError_t launch_shade_backward(const TraceArgs& a, const float* gbuf, int n_pix, int spp, uint32_t k0,
-                                  uint32_t k1, const float* dL_drgb, float* shade_grad, float* d_env,
-                                  cudaStream_t st);
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
                                   const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
                                   cudaStream_t st);

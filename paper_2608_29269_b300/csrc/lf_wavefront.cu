@@ -1,0 +1,487 @@
+// One-bounce shading (Eq. 10-11) as a wavefront of small kernels, and its
+// path-replay adjoint (Sec. 3.3).
+//
+// Work item = (job, pixel, sample).  Per batch:
+//   k_wf_gen      per item: Philox uniforms; environment NEE direction and
+//                 MIS factor; BSDF continuation direction from the
+//                 cosine/GGX mixture; appends NEE shadow rays to queue A and
+//                 continuation rays to queue B.
+//   k_wf_shadow   queue A: visibility V_e of the NEE rays.
+//   k_wf_continue queue B: k-buffer composite of the continuation ray to the
+//                 secondary record; two environment NEE samples there
+//                 (factor f2 cos / pdf, ray origin), appended to queue C.
+//   k_wf_shadow   queue C: visibility V_q of the secondary NEE rays.
+//   k_wf_combine  per pixel: sum of the per-sample terms in sample order,
+//                 L = T E(d) + (1 - T) / S * sum.
+// The per-sample buffer holds exactly the data path replay keeps fixed
+// (directions, pdfs, MIS weights, visibilities, secondary factors), so the
+// adjoint (k_wf_combine_adjoint) differentiates the combine without
+// re-tracing when it is given the forward's buffer; without it the first
+// four kernels are replayed with the same seed first.
+#include <algorithm>
+
+#include "lf_wavefront.h"
+
+namespace lf {
+
+constexpr int WB = 128;  // threads per block of the wavefront kernels
+constexpr int WSTACK_SMEM = WB * STACK * (int)sizeof(int);
+
+__device__ __forceinline__ int job_of_item(const ShadeBatch& B, long long item) {
+  int lo = 0, hi = B.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.jobs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int job_of_pixel(const ShadeBatch& B, int gp) {
+  int lo = 0, hi = B.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.jobs[mid].pix0 <= gp) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct PixRec {
+  float T;
+  int hits;
+  float3 x, n, a, d;
+  float m, r;
+};
+
+__device__ __forceinline__ PixRec pix_record(const ShadeJob& J, int p) {
+  const size_t P = (size_t)J.n_pix;
+  const float* g = J.gbuf + p;
+  PixRec q;
+  q.T = __ldg(g + LF_CH_T * P);
+  q.hits = (int)__ldg(g + LF_CH_HITS * P);
+  q.x = f3(__ldg(g + LF_CH_X * P), __ldg(g + (LF_CH_X + 1) * P), __ldg(g + (LF_CH_X + 2) * P));
+  q.n = f3(__ldg(g + LF_CH_N * P), __ldg(g + (LF_CH_N + 1) * P), __ldg(g + (LF_CH_N + 2) * P));
+  q.a = f3(__ldg(g + LF_CH_A * P), __ldg(g + (LF_CH_A + 1) * P), __ldg(g + (LF_CH_A + 2) * P));
+  q.m = __ldg(g + LF_CH_M * P);
+  q.r = __ldg(g + LF_CH_R * P);
+  q.d = f3(__ldg(g + LF_CH_DIR * P), __ldg(g + (LF_CH_DIR + 1) * P), __ldg(g + (LF_CH_DIR + 2) * P));
+  return q;
+}
+
+__device__ __forceinline__ float3 pix_origin(const ShadeJob& J, int p, float off) {
+  const size_t P = (size_t)J.n_pix;
+  const float* g = J.gbuf + p;
+  const float3 x = f3(__ldg(g + LF_CH_X * P), __ldg(g + (LF_CH_X + 1) * P), __ldg(g + (LF_CH_X + 2) * P));
+  const float3 n = f3(__ldg(g + LF_CH_N * P), __ldg(g + (LF_CH_N + 1) * P), __ldg(g + (LF_CH_N + 2) * P));
+  return x + n * off;
+}
+
+__device__ __forceinline__ float3 ld3(const float* const* pl, long long i) {
+  return f3(pl[0][i], pl[1][i], pl[2][i]);
+}
+__device__ __forceinline__ void st3(float* const* pl, long long i, float3 v) {
+  pl[0][i] = v.x;
+  pl[1][i] = v.y;
+  pl[2][i] = v.z;
+}
+
+// Warp-aggregated append of `value` to a queue when `pred` holds.  Called by
+// all 32 lanes of the warp together.
+__device__ __forceinline__ void queue_push(int* q, int* counter, int value, bool pred) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) q[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+__device__ __forceinline__ void load_insts(Inst* dst, const Inst* src, int n) {
+  const float4* s = reinterpret_cast<const float4*>(src);
+  float4* d = reinterpret_cast<float4*>(dst);
+  for (int i = threadIdx.x; i < n * 4; i += blockDim.x) d[i] = s[i];
+}
+
+// ---------------------------------------------------------------- generation
+__global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, SampleBuf S) {
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < B.n_items; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    bool e_ok = false, b_ok = false;
+    if (i < B.n_items) {
+    const ShadeJob& J = B.jobs[job_of_item(B, i)];
+    const long long loc = i - J.item0;
+    const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+    const PixRec q = pix_record(J, p);
+    const float3 wo = -q.d, n = q.n;
+    const float ps = P.brdf_mode == 1 ? 0.0f : P.p_spec;
+    float3 we = f3(0.f, 0.f, 1.f), wi = f3(0.f, 0.f, 1.f);
+    float ek = 0.0f, bc = 0.0f, wb = 0.0f;
+    if (q.hits > 0 && dot3(n, wo) > 0.0f) {
+      float u[9];
+      sample_uniforms((uint32_t)p, (uint32_t)s, J.k0, J.k1, u);
+      if (P.sampling_mode != 1) {
+        float pe;
+        env_sample(J.env, u[0], u[1], we, pe);
+        if (dot3(n, we) > 0.0f && pe > 0.0f) {
+          const float pb = pdf_bsdf(n, wo, we, q.r, ps);
+          ek = (P.sampling_mode == 2 ? 1.0f : pe * pe / (pe * pe + pb * pb)) / pe;
+          e_ok = true;
+        }
+      }
+      wi = (u[2] < ps) ? sample_ggx(n, wo, q.r, u[3], u[4]) : sample_cos(n, u[3], u[4]);
+      const float pb = pdf_bsdf(n, wo, wi, q.r, ps);
+      if (dot3(n, wi) > 0.0f && pb > 0.0f) {
+        const float pei = env_pdf(J.env, wi);
+        wb = P.sampling_mode == 1 ? 1.0f : pb * pb / (pb * pb + pei * pei);
+        bc = 1.0f / pb;
+        b_ok = true;
+      }
+    }
+    st3(S.we, i, we);
+    S.ek[i] = ek;
+    st3(S.wi, i, wi);
+    S.bc[i] = bc;
+    S.wb[i] = wb;
+    S.T2[i] = 1.0f;
+    st3(S.fk0, i, f3(0.f, 0.f, 0.f));
+    st3(S.fk1, i, f3(0.f, 0.f, 0.f));
+    }
+    queue_push(S.qA, S.counts + 0, (int)i, e_ok);
+    queue_push(S.qB, S.counts + 1, (int)i, b_ok);
+  }
+}
+
+// ---------------------------------------------------------------- shadow rays
+// which = 0: NEE rays of queue A (origin from the G-buffer, direction we)
+// which = 1: secondary NEE rays of queue C (entry = item * 2 + q)
+__global__ void __launch_bounds__(WB) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S, int which, int* status,
+                                                  unsigned long long* counters) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  __shared__ int s_job;
+  extern __shared__ int s_stack[];
+  const int* q = which == 0 ? S.qA : S.qC;
+  const int n = which == 0 ? S.counts[0] : S.counts[2];
+  Counters cnt;
+  // Jobs of a batch may have different scenes: blocks reload the instance
+  // table when the job of their first entry changes.
+  int loaded = -1;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int e = k < n ? q[k] : q[base];
+    const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+    const int j = job_of_item(B, item);
+    __syncthreads();
+    if (threadIdx.x == 0) s_job = j;
+    __syncthreads();
+    const int bj = s_job;
+    if (bj != loaded) {
+      load_insts(s_inst, B.jobs[bj].insts, B.jobs[bj].n_inst);
+      loaded = bj;
+    }
+    __syncthreads();
+    if (k < n) {
+      const ShadeJob& J = B.jobs[j];
+      const Inst* insts = (j == bj) ? s_inst : J.insts;
+      float3 o, d;
+      if (which == 0) {
+        const long long loc = item - J.item0;
+        o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+        d = ld3(S.we, item);
+      } else {
+        o = ld3(S.xs2, item);
+        d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
+      }
+      const float V = trace_shadow(insts, J.n_inst, o, d, P, s_stack + threadIdx.x, WB, status, cnt);
+      if (which == 0) S.Ve[item] = V;
+      else if (e & 1) S.Vq1[item] = V;
+      else S.Vq0[item] = V;
+    }
+  }
+  if (counters) {
+    atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
+    atomicAdd(counters + 1, (unsigned long long)cnt.tests);
+  }
+}
+
+// ---------------------------------------------------------------- continuation rays
+__global__ void __launch_bounds__(WB) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S, int* status,
+                                                    unsigned long long* counters) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  __shared__ int s_job;
+  extern __shared__ int s_stack[];
+  const int n = S.counts[1];
+  Counters cnt;
+  unsigned comp = 0;
+  int loaded = -1;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    const long long item = (long long)(k < n ? S.qB[k] : S.qB[base]);
+    const int j = job_of_item(B, item);
+    __syncthreads();
+    if (threadIdx.x == 0) s_job = j;
+    __syncthreads();
+    const int bj = s_job;
+    if (bj != loaded) {
+      load_insts(s_inst, B.jobs[bj].insts, B.jobs[bj].n_inst);
+      loaded = bj;
+    }
+    __syncthreads();
+    bool push0 = false, push1 = false;
+    if (k < n) {
+      const ShadeJob& J = B.jobs[j];
+      const Inst* insts = (j == bj) ? s_inst : J.insts;
+      const long long loc = item - J.item0;
+      const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+      const float3 xs = pix_origin(J, p, P.ray_offset);
+      const float3 wi = ld3(S.wi, item);
+      Surface s2;
+      trace_composite(insts, J.n_inst, xs, wi, P, s_stack + threadIdx.x, WB, status, cnt, s2, comp);
+      S.T2[item] = s2.T;
+      if (s2.hits > 0) {
+        const float3 n2 = s2.n, wo2 = -wi;
+        const float co2 = dot3(n2, wo2);
+        st3(S.xs2, item, s2.x + n2 * P.ray_offset);
+        const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
+        const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
+        const float uq[4] = {unit24(gb.y), unit24(gb.z), unit24(gb.w), unit24(gc.x)};
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+          float3 wq;
+          float pq;
+          env_sample(J.env, uq[2 * qq], uq[2 * qq + 1], wq, pq);
+          const float cq = dot3(n2, wq);
+          const bool ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
+          float3 fk = f3(0.f, 0.f, 0.f);
+          if (ok) fk = brdf_eval(n2, wo2, wq, s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f / pq);
+          if (qq == 0) { st3(S.wq0, item, wq); st3(S.fk0, item, fk); push0 = ok; }
+          else { st3(S.wq1, item, wq); st3(S.fk1, item, fk); push1 = ok; }
+        }
+      }
+    }
+    queue_push(S.qC, S.counts + 2, (int)(item * 2), push0);
+    queue_push(S.qC, S.counts + 2, (int)(item * 2 + 1), push1);
+  }
+  if (counters) {
+    atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
+    atomicAdd(counters + 1, (unsigned long long)cnt.tests);
+    atomicAdd(counters + 2, (unsigned long long)comp);
+  }
+}
+
+// ---------------------------------------------------------------- combine
+struct SampleTerms {
+  float3 E_e, E_i, E_q0, E_q1;
+};
+
+// Value of one sample given the (live) primary record.
+__device__ __forceinline__ float3 sample_value(const SampleBuf& S, long long i, const PixRec& q, const EnvDev& env,
+                                               const DevParams& P, SampleTerms& Et) {
+  const float3 wo = -q.d;
+  float3 c = f3(0.f, 0.f, 0.f);
+  const float ek = S.ek[i];
+  if (ek > 0.0f) {
+    const float3 we = ld3(S.we, i);
+    Et.E_e = env_lookup(env, we);
+    const float3 f = brdf_eval(q.n, wo, we, q.a, q.m, q.r, P.brdf_mode);
+    c = mul3(f, Et.E_e) * (dot3(q.n, we) * S.Ve[i] * ek);
+  }
+  const float bc = S.bc[i];
+  if (bc > 0.0f) {
+    const float3 wi = ld3(S.wi, i);
+    const float T2 = S.T2[i];
+    float3 inc = f3(0.f, 0.f, 0.f);
+    if (P.sampling_mode != 2) {
+      Et.E_i = env_lookup(env, wi);
+      inc = Et.E_i * (S.wb[i] * T2);
+    }
+    const float3 fk0 = ld3(S.fk0, i), fk1 = ld3(S.fk1, i);
+    if (fk0.x != 0.f || fk0.y != 0.f || fk0.z != 0.f) {
+      Et.E_q0 = env_lookup(env, ld3(S.wq0, i));
+      add3(inc, mul3(fk0, Et.E_q0) * S.Vq0[i]);
+    }
+    if (fk1.x != 0.f || fk1.y != 0.f || fk1.z != 0.f) {
+      Et.E_q1 = env_lookup(env, ld3(S.wq1, i));
+      add3(inc, mul3(fk1, Et.E_q1) * S.Vq1[i]);
+    }
+    const float3 f = brdf_eval(q.n, wo, wi, q.a, q.m, q.r, P.brdf_mode);
+    add3(c, mul3(f * (dot3(q.n, wi) * bc), inc));
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(WB) k_wf_combine(ShadeBatch B, DevParams P, SampleBuf S) {
+  const int gp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= B.n_pix_total) return;
+  const ShadeJob& J = B.jobs[job_of_pixel(B, gp)];
+  const int p = gp - J.pix0;
+  const PixRec q = pix_record(J, p);
+  float3 sum = f3(0.f, 0.f, 0.f);
+  if (q.hits > 0 && dot3(q.n, -q.d) > 0.0f) {
+    const long long i0 = J.item0 + (long long)p * J.spp;
+    SampleTerms Et;
+    for (int s = 0; s < J.spp; ++s) add3(sum, sample_value(S, i0 + s, q, J.env, P, Et));
+  }
+  const float3 L = env_lookup(J.env, q.d) * q.T + sum * ((1.0f - q.T) / (float)J.spp);
+  J.rgb[3 * p + 0] = L.x;
+  J.rgb[3 * p + 1] = L.y;
+  J.rgb[3 * p + 2] = L.z;
+}
+
+// d_env += v at the four bilinear texels of direction w.
+__device__ __forceinline__ void env_scatter(const EnvDev& e, float* __restrict__ d_env, float3 w, float3 v) {
+  if (!d_env) return;
+  const Bilin b = env_bilinear(e, w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (b.w[k] == 0.0f) continue;
+    float* t = d_env + 3 * b.idx[k];
+    atomicAdd(t + 0, b.w[k] * v.x);
+    atomicAdd(t + 1, b.w[k] * v.y);
+    atomicAdd(t + 2, b.w[k] * v.z);
+  }
+}
+
+// Adjoint of k_wf_combine with the sample data fixed: gradients of g . L with
+// respect to the primary record (normal, base colour, metallic, roughness,
+// T) into `sg` (9 planes) and to the environment texels into d_env.
+__global__ void __launch_bounds__(WB) k_wf_combine_adjoint(ShadeBatch B, DevParams P, SampleBuf S,
+                                                           const float* __restrict__ dL_drgb,
+                                                           float* __restrict__ sg, float* __restrict__ d_env) {
+  const int gp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= B.n_pix_total) return;
+  const ShadeJob& J = B.jobs[job_of_pixel(B, gp)];
+  const int p = gp - J.pix0;
+  const size_t NP = (size_t)J.n_pix;
+  const PixRec q = pix_record(J, p);
+  const float3 g = f3(__ldg(dL_drgb + 3 * p), __ldg(dL_drgb + 3 * p + 1), __ldg(dL_drgb + 3 * p + 2));
+  const float3 wo = -q.d;
+  float3 sum = f3(0.f, 0.f, 0.f), gn = sum, ga = sum;
+  float gm = 0.f, gr = 0.f;
+  if (q.hits > 0 && dot3(q.n, wo) > 0.0f) {
+    const float3 gc = g * ((1.0f - q.T) / (float)J.spp);
+    const long long i0 = J.item0 + (long long)p * J.spp;
+    for (int s = 0; s < J.spp; ++s) {
+      const long long i = i0 + s;
+      const float ek = S.ek[i];
+      if (ek > 0.0f) {
+        const float3 we = ld3(S.we, i);
+        const float3 E = env_lookup(J.env, we);
+        const float3 f = brdf_eval(q.n, wo, we, q.a, q.m, q.r, P.brdf_mode);
+        const float ce = dot3(q.n, we), kk = S.Ve[i] * ek;
+        add3(sum, mul3(f, E) * (ce * kk));
+        brdf_adjoint(q.n, wo, we, q.a, q.m, q.r, P.brdf_mode, mul3(gc, E) * (ce * kk), gn, ga, gm, gr);
+        add3(gn, we * (dot3(gc, mul3(f, E)) * kk));
+        env_scatter(J.env, d_env, we, mul3(gc, f) * (ce * kk));
+      }
+      const float bc = S.bc[i];
+      if (bc > 0.0f) {
+        const float3 wi = ld3(S.wi, i);
+        const float T2 = S.T2[i], wbT = S.wb[i] * T2;
+        float3 inc = f3(0.f, 0.f, 0.f);
+        if (P.sampling_mode != 2) inc = env_lookup(J.env, wi) * wbT;
+        const float3 fk0 = ld3(S.fk0, i), fk1 = ld3(S.fk1, i);
+        const bool q0 = fk0.x != 0.f || fk0.y != 0.f || fk0.z != 0.f;
+        const bool q1 = fk1.x != 0.f || fk1.y != 0.f || fk1.z != 0.f;
+        const float3 wq0 = ld3(S.wq0, i), wq1 = ld3(S.wq1, i);
+        const float V0 = q0 ? S.Vq0[i] : 0.f, V1 = q1 ? S.Vq1[i] : 0.f;
+        if (q0) add3(inc, mul3(fk0, env_lookup(J.env, wq0)) * V0);
+        if (q1) add3(inc, mul3(fk1, env_lookup(J.env, wq1)) * V1);
+        const float ci = dot3(q.n, wi);
+        const float3 f = brdf_eval(q.n, wo, wi, q.a, q.m, q.r, P.brdf_mode);
+        const float3 beta = f * (ci * bc);
+        add3(sum, mul3(beta, inc));
+        const float3 gbeta = mul3(gc, inc);
+        brdf_adjoint(q.n, wo, wi, q.a, q.m, q.r, P.brdf_mode, gbeta * (ci * bc), gn, ga, gm, gr);
+        add3(gn, wi * (dot3(gbeta, f) * bc));
+        const float3 ginc = mul3(gc, beta);
+        if (P.sampling_mode != 2) env_scatter(J.env, d_env, wi, ginc * wbT);
+        if (q0) env_scatter(J.env, d_env, wq0, mul3(ginc, fk0) * V0);
+        if (q1) env_scatter(J.env, d_env, wq1, mul3(ginc, fk1) * V1);
+      }
+    }
+  }
+  const float3 Ed = env_lookup(J.env, q.d);
+  const float inv = 1.0f / (float)J.spp;
+  const float gT = g.x * (Ed.x - sum.x * inv) + g.y * (Ed.y - sum.y * inv) + g.z * (Ed.z - sum.z * inv);
+  env_scatter(J.env, d_env, q.d, g * q.T);
+  sg[0 * NP + p] = gn.x; sg[1 * NP + p] = gn.y; sg[2 * NP + p] = gn.z;
+  sg[3 * NP + p] = ga.x; sg[4 * NP + p] = ga.y; sg[5 * NP + p] = ga.z;
+  sg[6 * NP + p] = gm;
+  sg[7 * NP + p] = gr;
+  sg[8 * NP + p] = gT;
+}
+
+__global__ void k_wf_count(const int* counts, unsigned long long* ray_count) {
+  if (threadIdx.x == 0 && ray_count)
+    atomicAdd(ray_count, (unsigned long long)counts[0] + (unsigned long long)counts[1] + (unsigned long long)counts[2]);
+}
+
+// ---------------------------------------------------------------- host side
+size_t sample_buf_bytes(long long n_items) {
+  const size_t ns = (size_t)n_items;
+  return sizeof(float) * SAMPLE_PLANES * ns + sizeof(int) * 4 * ns + 256;
+}
+
+SampleBuf sample_buf(void* base, long long n_items) {
+  SampleBuf S;
+  float* f = static_cast<float*>(base);
+  const size_t ns = (size_t)n_items;
+  auto take = [&](int k) { float* r = f; f += (size_t)k * ns; return r; };
+  float* p;
+  p = take(3); S.we[0] = p; S.we[1] = p + ns; S.we[2] = p + 2 * ns;
+  S.ek = take(1);
+  S.Ve = take(1);
+  p = take(3); S.wi[0] = p; S.wi[1] = p + ns; S.wi[2] = p + 2 * ns;
+  S.bc = take(1);
+  S.wb = take(1);
+  S.T2 = take(1);
+  p = take(3); S.xs2[0] = p; S.xs2[1] = p + ns; S.xs2[2] = p + 2 * ns;
+  p = take(3); S.wq0[0] = p; S.wq0[1] = p + ns; S.wq0[2] = p + 2 * ns;
+  p = take(3); S.wq1[0] = p; S.wq1[1] = p + ns; S.wq1[2] = p + 2 * ns;
+  p = take(3); S.fk0[0] = p; S.fk0[1] = p + ns; S.fk0[2] = p + 2 * ns;
+  p = take(3); S.fk1[0] = p; S.fk1[1] = p + ns; S.fk1[2] = p + 2 * ns;
+  S.Vq0 = take(1);
+  S.Vq1 = take(1);
+  int* q = reinterpret_cast<int*>(f);
+  S.qA = q;
+  S.qB = q + ns;
+  S.qC = q + 2 * ns;
+  S.counts = q + 4 * ns;
+  return S;
+}
+
+static int wf_grid(long long n, int sms) {
+  const long long blocks = (n + WB - 1) / WB;
+  return (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sms * 16));
+}
+
+cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, int* status,
+                                   unsigned long long* ray_count, unsigned long long* counters, int sms,
+                                   cudaStream_t st) {
+  if (B.n_items <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(S.counts, 0, 4 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_wf_gen<<<wf_grid(B.n_items, sms), WB, 0, st>>>(B, P, S);
+  // queue lengths are known only on the device: the trace kernels size
+  // their loops from the counters (grids cover the worst case).
+  k_wf_shadow<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
+  k_wf_continue<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
+  k_wf_shadow<<<wf_grid(2 * B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 1, status, counters);
+  k_wf_count<<<1, 32, 0, st>>>(S.counts, ray_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade_combine(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, cudaStream_t st) {
+  if (B.n_pix_total > 0) k_wf_combine<<<(B.n_pix_total + WB - 1) / WB, WB, 0, st>>>(B, P, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade_combine_adjoint(const ShadeBatch& B, const DevParams& P, const SampleBuf& S,
+                                         const float* dL_drgb, float* sg, float* d_env, cudaStream_t st) {
+  if (B.n_pix_total > 0)
+    k_wf_combine_adjoint<<<(B.n_pix_total + WB - 1) / WB, WB, 0, st>>>(B, P, S, dL_drgb, sg, d_env);
+  return cudaGetLastError();
+}
+
+}  // namespace lf

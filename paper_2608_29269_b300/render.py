@@ -21,21 +21,22 @@ class SurfelRender(torch.autograd.Function):
     @staticmethod
     def forward(ctx, tracer: Tracer, cam, env_id: int, spp: int, seed: int, env_rgb, *scene):
         gbuf = tracer.trace_primary(cam, env_id)
-        rgb = tracer.shade(cam, gbuf, env_id, spp, seed)
+        samples = tracer.alloc_samples(cam, spp)
+        rgb = tracer.shade(cam, gbuf, env_id, spp, seed, samples=samples)
         ctx.tracer, ctx.cam, ctx.env_id, ctx.spp, ctx.seed = tracer, cam, env_id, spp, seed
-        ctx.save_for_backward(gbuf, env_rgb)
+        ctx.save_for_backward(gbuf, env_rgb, samples)
         ctx.mark_non_differentiable(gbuf)
         return rgb, gbuf
 
     @staticmethod
     def backward(ctx, g_rgb, g_gbuf):
-        gbuf, env_rgb = ctx.saved_tensors
+        gbuf, env_rgb, samples = ctx.saved_tensors
         tr = ctx.tracer
         d_surfel = torch.zeros((tr.scene.n, N.G_STRIDE), device=gbuf.device, dtype=torch.float32)
         d_env = torch.zeros_like(env_rgb) if ctx.needs_input_grad[5] else None
         tr.backward(ctx.cam, gbuf, ctx.env_id, ctx.spp, ctx.seed,
                     dL_drgb=g_rgb.contiguous() if g_rgb is not None else None,
-                    dL_dgbuf=None, d_surfel=d_surfel, d_env=d_env)
+                    dL_dgbuf=None, d_surfel=d_surfel, d_env=d_env, fwd_samples=samples)
         grads = []
         for k in SCENE_FIELDS:
             a, b = GRAD_SLICES[k]

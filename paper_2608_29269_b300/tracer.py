@@ -166,30 +166,46 @@ class Tracer:
         self.check(self.lib.lf_trace_primary(self.ctx, C.byref(c), int(env_id), _ptr(out)))
         return out
 
+    def shade_scratch_bytes(self, cam, spp: int) -> int:
+        return int(self.lib.lf_shade_scratch_bytes(cam.width, cam.height, int(spp)))
+
+    def alloc_samples(self, cam, spp: int) -> torch.Tensor:
+        """Per-sample buffer of lf_shade_bounce (reusable by backward)."""
+        return torch.empty((self.shade_scratch_bytes(cam, spp) + 3) // 4, device="cuda", dtype=torch.float32)
+
     def shade(self, cam, gbuf: torch.Tensor, env_id: int = 0, spp: int = 16, seed: int = 0,
-              out: Optional[torch.Tensor] = None, ray_count: Optional[torch.Tensor] = None) -> torch.Tensor:
+              out: Optional[torch.Tensor] = None, ray_count: Optional[torch.Tensor] = None,
+              samples: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
             out = torch.empty((cam.height, cam.width, 3), device="cuda", dtype=torch.float32)
+        if samples is None:
+            samples = self.alloc_samples(cam, spp)
         c = camera_struct(cam)
         self.check(self.lib.lf_shade_bounce(self.ctx, C.byref(c), _ptr(gbuf), int(env_id), int(spp),
-                                            C.c_uint64(seed), _ptr(out), _ptr(ray_count)))
+                                            C.c_uint64(seed), _ptr(out), _ptr(ray_count), _ptr(samples),
+                                            samples.numel() * samples.element_size()))
         return out
 
-    def scratch_bytes(self, cam) -> int:
-        return int(self.lib.lf_backward_scratch_bytes(cam.width, cam.height))
+    def scratch_bytes(self, cam, spp: int) -> int:
+        return int(self.lib.lf_backward_scratch_bytes(cam.width, cam.height, int(spp)))
 
     def backward(self, cam, gbuf, env_id, spp, seed, dL_drgb=None, dL_dgbuf=None, d_surfel=None, d_env=None,
-                 scratch=None):
-        """Accumulates into d_surfel (N, 17) and d_env (H, W, 3); returns them."""
+                 scratch=None, fwd_samples=None):
+        """Accumulates into d_surfel (N, 17) and d_env (H, W, 3); returns them.
+
+        fwd_samples: the `samples` buffer of the matching shade() call (the
+        shading adjoint then reuses its frozen data instead of replaying).
+        """
         if d_surfel is None:
             d_surfel = torch.zeros((self.scene.n, N.G_STRIDE), device="cuda", dtype=torch.float32)
         if scratch is None and dL_drgb is not None:
-            scratch = torch.empty(self.scratch_bytes(cam) // 4, device="cuda", dtype=torch.float32)
+            nbytes = (9 * cam.width * cam.height * 4 + 256) if fwd_samples is not None else self.scratch_bytes(cam, spp)
+            scratch = torch.empty((nbytes + 3) // 4, device="cuda", dtype=torch.float32)
         c = camera_struct(cam)
         nbytes = scratch.numel() * scratch.element_size() if scratch is not None else 0
         self.check(self.lib.lf_trace_backward(self.ctx, C.byref(c), _ptr(gbuf), int(env_id), int(spp),
                                               C.c_uint64(seed), _ptr(dL_drgb), _ptr(dL_dgbuf), _ptr(d_surfel),
-                                              _ptr(d_env), _ptr(scratch), nbytes))
+                                              _ptr(d_env), _ptr(fwd_samples), _ptr(scratch), nbytes))
         return d_surfel, d_env
 
     def set_counters(self, counters: Optional[torch.Tensor]):

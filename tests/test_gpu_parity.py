@@ -4,6 +4,8 @@ Tolerances: 1e-4 absolute per channel (radiance clamped to [0,1]) on every
 pixel the oracle does not flag as sitting on a discontinuity; hit counts
 identical there; the flagged fraction is reported and bounded.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -173,15 +175,25 @@ def test_c3_gradient_parity():
     g_ch = rng.normal(size=(cam.n_pixels, 17)) * 0.2 * ok[:, None]
     d_s, d_e = oracle.grad(sc, cam, env, pix, 4, 3, g_rgb, g_ch)
     g = tr.trace_primary(cam, 0)
-    tr.shade(cam, g, 0, spp=4, seed=3)
+    samples = tr.alloc_samples(cam, 4)
+    tr.shade(cam, g, 0, spp=4, seed=3, samples=samples)
     gg = torch.zeros((25, cam.height * cam.width), device="cuda")
     gg[:17] = torch.as_tensor(g_ch.T, dtype=torch.float32, device="cuda")
     d_surf = torch.zeros((sc.n, 17), device="cuda")
     d_env = torch.zeros((env.height, env.width, 3), device="cuda")
     tr.backward(cam, g, 0, 4, 3, dL_drgb=torch.as_tensor(g_rgb, dtype=torch.float32, device="cuda").contiguous(),
-                dL_dgbuf=gg.contiguous(), d_surfel=d_surf, d_env=d_env)
+                dL_dgbuf=gg.contiguous(), d_surfel=d_surf, d_env=d_env, fwd_samples=samples)
     tr.sync()
     gs, ge = d_surf.cpu().numpy().astype(np.float64), d_env.cpu().numpy().astype(np.float64)
+    # the replayed adjoint (no forward buffer) gives the same gradients
+    d_surf2, d_env2 = torch.zeros_like(d_surf), torch.zeros_like(d_env)
+    tr.backward(cam, g, 0, 4, 3, dL_drgb=torch.as_tensor(g_rgb, dtype=torch.float32, device="cuda").contiguous(),
+                dL_dgbuf=gg.contiguous(), d_surfel=d_surf2, d_env=d_env2)
+    tr.sync()
+    np.testing.assert_allclose(d_surf2.cpu().numpy(), gs, rtol=1e-5, atol=1e-6 * np.abs(gs).max())
+    np.testing.assert_allclose(d_env2.cpu().numpy(), ge, rtol=1e-5, atol=1e-6 * np.abs(ge).max())
+    np.save("gpurun_out/grad_dump.npy", dict(d_s=d_s, gs=gs, d_e=d_e, ge=ge), allow_pickle=True) \
+        if os.path.isdir("gpurun_out") else None
     report = {}
     for name, (a, b) in dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
                              metallic=(15, 16), roughness=(16, 17)).items():

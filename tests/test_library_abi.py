@@ -42,8 +42,9 @@ def test_host_only_calls(lib):
     assert lib.lf_params_default(C.byref(p)) == 0
     assert abs(p.alpha_max - 0.99) < 1e-7 and p.max_rounds == 64
     assert lib.lf_params_default(None) == N.LF_ERR_INVALID
-    assert lib.lf_backward_scratch_bytes(800, 800) == 9 * 4 * 800 * 800
-    assert lib.lf_backward_scratch_bytes(0, 5) == 0
+    assert lib.lf_shade_scratch_bytes(800, 800, 16) >= 28 * 4 * 800 * 800 * 16
+    assert lib.lf_backward_scratch_bytes(800, 800, 16) >= 9 * 4 * 800 * 800 + lib.lf_shade_scratch_bytes(800, 800, 16)
+    assert lib.lf_backward_scratch_bytes(0, 5, 4) == 0 and lib.lf_shade_scratch_bytes(8, 8, 0) == 0
     assert lib.lf_create(C.byref(p), None, None) == N.LF_ERR_INVALID
     bad = N.LfParams()
     lib.lf_params_default(C.byref(bad))
