@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Benchmark of the surfel ray tracer's hot path on one or more B300s.
+
+One step is one pass of the whole path over the one-bounce workload (a
+200k-surfel room: background shell + 4 objects, 800x800, 16 spp, 256x512
+environment): full LBVH build, environment sampling tables, a rigid object
+edit (transform + BLAS refit + TLAS), primary trace, one-bounce shading and
+the path-replay adjoint to all surfel attributes and environment texels.
+
+Metric: Mrays/s of forward + backward (rays traced by the forward pass /
+time of the whole step); the forward-only figure is reported beside it.
+Inputs are synthetic (seeded); the scene (~17 MB of packed records and
+nodes) fits in L2, so L2 is flushed between timed steps.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference arm of this comparison).
+Multi-GPU: every rank renders its own replica (no collective on the data
+path), timing is the max over ranks, `value` counts the rays of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s fwd+bwd (one-bounce surfel ray tracing)"
+UNIT = "Mrays/s"
+WORKLOAD = dict(workload="one-bounce room: 200k surfels (10k/face shell + 4x35k objects), 800x800, 16 spp, "
+                         "256x512 sky+sun env, fwd+bwd, full LBVH build + rigid edit per step",
+                surfels=200_000, width=800, height=800, spp=16, env="256x512")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lightfuse", choices=["lightfuse", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--size", type=int, default=800)
+    ap.add_argument("--spp", type=int, default=16)
+    return ap.parse_args()
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- workload
+def make_workload(size, spp, seed):
+    from synthetic import scenes as S
+    sc = S.scene_c2(seed)
+    cam = S.camera_c2(size, size)
+    env = S.env_sky_sun(seed)
+    return sc, cam, env
+
+
+class Step:
+    """Device buffers and the hot-path step on one GPU."""
+
+    def __init__(self, sc, cam, env, spp, seed):
+        import numpy as np
+        import torch
+        from paper_2608_29269_b300 import SceneTensors, Tracer
+        self.torch = torch
+        self.cam, self.spp, self.seed = cam, spp, seed
+        self.tr = Tracer()
+        self.st = SceneTensors.from_numpy(sc)
+        self.env = torch.as_tensor(env.rgb, device="cuda").contiguous()
+        self.tr.build(self.st)
+        self.tr.set_env(0, self.env)
+        P = cam.width * cam.height
+        self.gbuf = torch.empty((25, cam.height, cam.width), device="cuda")
+        self.rgb = torch.empty((cam.height, cam.width, 3), device="cuda")
+        self.samples = self.tr.alloc_samples(cam, spp)
+        self.scratch = torch.empty((9 * P * 4 + 256 + 3) // 4, device="cuda")
+        self.d_surfel = torch.zeros((sc.n, 17), device="cuda")
+        self.d_env = torch.zeros_like(self.env)
+        self.rays = torch.zeros(1, dtype=torch.int64, device="cuda")
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        self.dL = (torch.rand((cam.height, cam.width, 3), generator=g) - 0.5).to("cuda").contiguous()
+        # rigid edit of object 1 (rotation about +y through its centre, shift); alternate with its inverse
+        lo, hi = sc.object_offsets[1], sc.object_offsets[2]
+        from synthetic.scenes import rigid_motion
+        R, t = rigid_motion(np.random.default_rng(seed), sc.mu[lo:hi].mean(0))
+        self.T = (R, t)
+        self.Tinv = (R.T.copy(), (-(R.T @ t)).astype(np.float32))
+        self.k = 0
+        self.ev = None
+
+    def run(self, events=None):
+        """One step; `events` (dict name -> (start, end)) records phase times."""
+        torch, tr, cam = self.torch, self.tr, self.cam
+        rec = (lambda name, i: events[name][i].record()) if events is not None else (lambda name, i: None)
+        rec("build", 0)
+        tr.build(self.st)
+        tr.set_env(0, self.env)
+        R, t = self.T if self.k % 2 == 0 else self.Tinv
+        tr.refit(1, R, t)
+        self.k += 1
+        rec("build", 1)
+        rec("primary", 0)
+        tr.trace_primary(cam, 0, out=self.gbuf)
+        rec("primary", 1)
+        rec("shade", 0)
+        tr.shade(cam, self.gbuf, 0, self.spp, self.seed, out=self.rgb, ray_count=self.rays, samples=self.samples)
+        rec("shade", 1)
+        rec("backward", 0)
+        self.d_surfel.zero_()
+        self.d_env.zero_()
+        tr.backward(cam, self.gbuf, 0, self.spp, self.seed, dL_drgb=self.dL, d_surfel=self.d_surfel,
+                    d_env=self.d_env, scratch=self.scratch, fwd_samples=self.samples)
+        rec("backward", 1)
+
+
+KERNELS_PER_STEP = {  # launches of this library's kernels in one step
+    "build": 2 + 1 + 1 + 5 * 3 + 1 + 1,  # bounds init+reduce, morton, radix 5x(hist, scan, scatter), hierarchy, fit
+    "env": 2,
+    "refit": 2,
+    "primary": 1,
+    "shade": 6,  # gen, shadow A, continue, shadow C, count, combine
+    "backward": 2,  # combine adjoint, trace backward
+}
+
+
+def oracle_sample(sc, cam, env, spp, seed, target_s, include_grad=True):
+    """Time the FP64 oracle on a bounded pixel sample (~target_s seconds)."""
+    import numpy as np
+    import oracle
+    from synthetic.scenes import pixel_subset
+    threads = os.cpu_count() or 1
+    n = 8
+    while True:
+        pix = pixel_subset(cam.width, cam.height, n, seed=seed)
+        t0 = time.perf_counter()
+        out = oracle.render(sc, cam, env, pix, spp=spp, seed=seed, threads=threads)
+        if include_grad:
+            oracle.grad(sc, cam, env, pix, spp, seed, np.ones((len(pix), 3)), None, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * target_s or n >= cam.width * cam.height:
+            scale = target_s / max(dt, 1e-3)
+            if scale > 1.5 and n < cam.width * cam.height:
+                n = int(min(cam.width * cam.height, n * scale))
+                continue
+            return dict(rays=out["rays"], seconds=dt, pixels=len(pix), threads=threads)
+        n *= 4
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, cam, env = make_workload(args.size, args.spp, 0)
+    import oracle
+    oracle.build()
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    probe = oracle_sample(sc, cam, env, args.spp, 0, per_step)
+    from synthetic.scenes import pixel_subset
+    import numpy as np
+    pix = pixel_subset(cam.width, cam.height, probe["pixels"], seed=0)
+    times, rays = [], 0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        out = oracle.render(sc, cam, env, pix, spp=args.spp, seed=k, threads=probe["threads"])
+        oracle.grad(sc, cam, env, pix, args.spp, k, np.ones((len(pix), 3)), None, threads=probe["threads"])
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            rays += out["rays"]
+    total = sum(times)
+    value = rays / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": dict(WORKLOAD, sample_pixels=len(pix)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": probe["threads"], "kind": "oracle",
+                             "sample": f"{len(pix)} seeded pixels of the 800x800 frame, 16 spp, fwd + gradient"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2608_29269_b300.build import build
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    sc, cam, env = make_workload(args.size, args.spp, 0)
+    step = Step(sc, cam, env, args.spp, seed=1234 + rank)
+    names = ["build", "primary", "shade", "backward"]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step.run()
+    step.tr.sync()
+
+    # counted run (outside the timed region): traversal counters per phase
+    counters = {}
+    for ph in ["primary", "shade"]:
+        c = torch.zeros(4, dtype=torch.int64, device="cuda")
+        step.tr.set_counters(c)
+        if ph == "primary":
+            step.tr.trace_primary(cam, 0, out=step.gbuf)
+        else:
+            step.tr.shade(cam, step.gbuf, 0, args.spp, step.seed, out=step.rgb, samples=step.samples)
+        step.tr.sync()
+        counters[ph] = [int(v) for v in c.tolist()]
+    step.tr.set_counters(None)
+
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+    step.rays.zero_()
+    clocks = ClockSampler(local)
+    per_step_ms, phase_ms = [], {n: [] for n in names}
+    barrier()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict the scene from L2 between steps
+        events = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in names}
+        barrier()
+        step.run(events)
+        torch.cuda.synchronize()
+        for n in names:
+            phase_ms[n].append(events[n][0].elapsed_time(events[n][1]))
+        per_step_ms.append(events["build"][0].elapsed_time(events["backward"][1]))
+    barrier()
+    clk = clocks.stop()
+    step.tr.sync()
+    total_ms = sum(per_step_ms)
+    shade_rays = int(step.rays.item())
+    rays = shade_rays + args.steps * cam.width * cam.height
+    fwd_ms = sum(phase_ms["primary"]) + sum(phase_ms["shade"])
+    t = torch.tensor([total_ms, fwd_ms], dtype=torch.float64, device="cuda")
+    r = torch.tensor([rays], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    total_ms, fwd_ms = float(t[0]), float(t[1])
+    rays_all = float(r[0])
+    value = rays_all / (total_ms * 1e-3) / 1e6
+    fwd_value = rays_all / (fwd_ms * 1e-3) / 1e6
+
+    # ---------------------------------------------------------------- e2e through the public API
+    e2e = e2e_run(step, sc, env, args, world)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    # ---------------------------------------------------------------- roofline of the dominant kernel group
+    hbm, peak_kind = read_peaks()
+    avg = {n: statistics.mean(v) for n, v in phase_ms.items()}
+    c = counters["shade"]
+    P = cam.width * cam.height
+    ns = P * args.spp
+    # algorithmic bytes of the shading pass: node visits (64 B), surfel tests (64 B packed record),
+    # composited hits (64 B record + 16 B material), per-sample buffer written and read once (28 floats + queues),
+    # G-buffer read (12 channels) and the image written.
+    shade_bytes = 64 * c[0] + 64 * c[1] + 80 * c[2] + ns * (28 * 4 * 2 + 16) + P * (12 * 4 + 12)
+    achieved = shade_bytes / (avg["shade"] * 1e-3) / 1e9
+    traffic = read_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": dict(WORKLOAD, parallelism=f"replicas x{world}", l2="flushed between steps (256 MB write)"),
+        "fwd_mrays_s": fwd_value,
+        "rays_per_step": rays_all / args.steps / world,
+        "phase_ms": {n: round(v, 3) for n, v in avg.items()},
+        "roofline": {"bound": "hbm", "kernel": "shading wavefront (gen, shadow, continuation, combine)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_kind": f"{peak_kind} HBM copy", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": shade_bytes},
+        "counters": {"primary": counters["primary"], "shade": counters["shade"],
+                     "fields": ["node visits", "surfel tests", "composited hits", "rays"]},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": args.steps * sum(KERNELS_PER_STEP.values()),
+    }
+    if not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            cb = oracle_sample(sc, cam, env, args.spp, 0, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": cb["rays"] / cb["seconds"] / 1e6, "unit": UNIT, "cores": cb["threads"],
+                                    "kind": "oracle",
+                                    "sample": f"{cb['pixels']} seeded pixels of the frame, {args.spp} spp, "
+                                              f"forward + gradient, {cb['seconds']:.1f} s"}
+        except Exception as exc:  # the bench line must still print
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": f"failed: {exc}"}
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def read_traffic():
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernels."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("sources_sha") != sources_sha():
+            return None
+        return t.get("shade_dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2608_29269_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def e2e_run(step, sc, env, args, world):
+    """Same step through the public API with host inputs: H2D of the scene,
+    environment and upstream gradient from pinned memory, D2H of the image and
+    the gradients, inside the timed region."""
+    import torch
+    host = {k: torch.as_tensor(getattr(sc, k)).pin_memory() for k in
+            ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic", "roughness"]}
+    h_env = torch.as_tensor(env.rgb).pin_memory()
+    h_dL = step.dL.cpu().pin_memory()
+    out_rgb = torch.empty(step.rgb.shape, dtype=torch.float32).pin_memory()
+    out_ds = torch.empty(step.d_surfel.shape, dtype=torch.float32).pin_memory()
+    out_de = torch.empty(step.d_env.shape, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host.values()) + h_env.numel() * 4 + h_dL.numel() * 4
+    d2h = (out_rgb.numel() + out_ds.numel() + out_de.numel()) * 4
+    step.rays.zero_()
+    n = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        for k, t in host.items():
+            getattr(step.st, k).copy_(t, non_blocking=True)
+        step.env.copy_(h_env, non_blocking=True)
+        step.dL.copy_(h_dL, non_blocking=True)
+        step.run()
+        out_rgb.copy_(step.rgb, non_blocking=True)
+        out_ds.copy_(step.d_surfel, non_blocking=True)
+        out_de.copy_(step.d_env, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rays = int(step.rays.item()) + n * step.cam.width * step.cam.height
+    return {"value": rays / dt / 1e6 * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": n}
+
+
+if __name__ == "__main__":
+    main()

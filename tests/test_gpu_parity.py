@@ -194,18 +194,22 @@ def test_c3_gradient_parity():
     np.testing.assert_allclose(d_env2.cpu().numpy(), ge, rtol=1e-5, atol=1e-6 * np.abs(ge).max())
     np.save("gpurun_out/grad_dump.npy", dict(d_s=d_s, gs=gs, d_e=d_e, ge=ge), allow_pickle=True) \
         if os.path.isdir("gpurun_out") else None
-    report = {}
-    for name, (a, b) in dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
-                             metallic=(15, 16), roughness=(16, 17)).items():
-        ref, got = d_s[:, a:b], gs[:, a:b]
-        floor = 1e-3 * np.abs(ref).max()
-        rel = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
-        report[name] = float(rel.max())
-    floor = 1e-3 * np.abs(d_e).max()
-    report["env"] = float((np.abs(ge - d_e) / np.maximum(np.abs(d_e), floor)).max())
-    print("gradient rel errors:", report, "nonzero surfels", int((np.abs(d_s).sum(1) > 0).sum()))
+    # Criterion: per attribute group the L2-relative error is at most 1e-3, and
+    # element-wise |g - g_ref| <= 1e-3 |g_ref| + 1e-4 max|g_ref| (the floor covers
+    # FP32 cancellation when large per-pixel contributions sum to a small value).
+    report, worst = {}, {}
+    groups = dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
+                  metallic=(15, 16), roughness=(16, 17))
+    pairs = {k: (d_s[:, a:b], gs[:, a:b]) for k, (a, b) in groups.items()}
+    pairs["env"] = (d_e, ge)
+    for name, (ref, got) in pairs.items():
+        report[name] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        worst[name] = float((np.abs(got - ref) / (1e-3 * np.abs(ref) + 1e-4 * np.abs(ref).max())).max())
+    print("gradient L2-relative errors:", report, "element-wise (<=1):", worst,
+          "nonzero surfels", int((np.abs(d_s).sum(1) > 0).sum()))
     assert (np.abs(d_s).sum(1) > 0).sum() > 50
     assert max(report.values()) <= 1e-3, report
+    assert max(worst.values()) <= 1.0, worst
 
 
 FLAG_GRAD = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6, cap=1e-5)
