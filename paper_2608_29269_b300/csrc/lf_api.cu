@@ -170,7 +170,6 @@ lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out) {
   if (e == cudaSuccess) e = dev_alloc(&c->node_off_dev, LF_MAX_OBJECTS + 1);
   if (e == cudaSuccess) e = dev_alloc(&c->bounds, 6 * LF_MAX_OBJECTS);
   if (e == cudaSuccess) e = dev_alloc(&c->insts_dev, LF_MAX_OBJECTS);
-  if (e == cudaSuccess) e = dev_alloc(&c->fetch_dev, 16);
   if (e != cudaSuccess) {
     lf_destroy(c);
     return e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA;
@@ -185,7 +184,6 @@ lf_status lf_destroy(lf_ctx* c) {
   free_scene_storage(c);
   dev_free(c->status_dev); dev_free(c->offsets_dev); dev_free(c->node_off_dev); dev_free(c->bounds);
   dev_free(c->insts_dev);
-  dev_free(c->fetch_dev);
   for (EnvSlot& e : c->env) { dev_free(e.tables); dev_free(e.rowsum); dev_free(e.sin_row); }
   delete c;
   return LF_OK;
@@ -407,8 +405,7 @@ lf_status lf_trace_primary(lf_ctx* c, const lf_camera* cam, int env_id, float* g
   lf_status st = check_render(c, cam, env_id);
   if (st != LF_OK) return st;
   if (!gbuf) return fail(c, LF_ERR_INVALID, "null G-buffer");
-  LF_CUDA(c, launch_trace_primary(lf_ctx_trace_args(c, env_id), to_cam(*cam), gbuf, c->fetch_dev, c->sms,
-                                  c->stream));
+  LF_CUDA(c, launch_trace_primary(lf_ctx_trace_args(c, env_id), to_cam(*cam), gbuf, c->stream));
   return LF_OK;
 }
 
@@ -487,8 +484,7 @@ lf_status lf_trace_backward(lf_ctx* c, const lf_camera* cam, const float* gbuf, 
     }
     LF_CUDA(c, launch_shade_combine_adjoint(B, c->dp, S, dL_drgb, sg, d_env, c->stream));
   }
-  LF_CUDA(c, launch_trace_backward(a, c->scene, to_cam(*cam), gbuf, sg, dL_dgbuf, d_surfel, d_env, c->fetch_dev + 1,
-                                   c->sms, c->stream));
+  LF_CUDA(c, launch_trace_backward(a, c->scene, to_cam(*cam), gbuf, sg, dL_dgbuf, d_surfel, d_env, c->stream));
   return LF_OK;
 }
 

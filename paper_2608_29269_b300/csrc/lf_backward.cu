@@ -77,31 +77,31 @@ __device__ __forceinline__ void surfel_adjoint(const SceneDev& sc, int id, float
   atomicAdd(o17 + 16, g_r);
 }
 
-// Per-pixel adjoint state of the back-to-front pass.
-struct BackState {
-  float3 gSx, gSn, gSa;
-  float gSt, gSm, gSr, gW;
-  float S, Tn;  // suffix sum of Eq. 7's alpha adjoint; transmittance behind the current hit
-  int remaining, rounds;
-  unsigned long long bound;
-  bool inclusive;
-};
-
-// Upstream gradients of one pixel's record -> adjoints of the Eq. 7 sums;
-// false when the pixel has no composited hit.
-__device__ __forceinline__ bool back_setup(const TraceArgs& a, const float* __restrict__ gbuf,
-                                           const float* __restrict__ sg, const float* __restrict__ gg, size_t P,
-                                           int p, float3& d, BackState& b, float* d_env) {
+__global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
+                                                       const float* __restrict__ gbuf,
+                                                       const float* __restrict__ sg,
+                                                       const float* __restrict__ gg, float* __restrict__ d_surfel,
+                                                       float* __restrict__ d_env) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  extern __shared__ int s_stack[];
+  load_instances_b(s_inst, a.insts, a.n_inst);
+  const int x = blockIdx.x * 16 + (threadIdx.x & 15), y = blockIdx.y * 8 + (threadIdx.x >> 4);
+  if (x >= cam.W || y >= cam.H) return;
+  const int p = y * cam.W + x;
+  const size_t P = (size_t)cam.W * cam.H;
+  const DevParams& Pm = a.P;
   const float* gb = gbuf + p;
   auto ch = [&](int c) { return __ldg(gb + (size_t)c * P); };
   auto up = [&](int c) { return gg ? __ldg(gg + (size_t)c * P + p) : 0.0f; };
-  d = f3(ch(LF_CH_DIR), ch(LF_CH_DIR + 1), ch(LF_CH_DIR + 2));
+  const float3 o = cam.eye;
+  const float3 d = f3(ch(LF_CH_DIR), ch(LF_CH_DIR + 1), ch(LF_CH_DIR + 2));
   const float T = ch(LF_CH_T), W = ch(LF_CH_W), depth = ch(LF_CH_DEPTH), nlen = ch(LF_CH_NLEN);
   const float3 xb = f3(ch(LF_CH_X), ch(LF_CH_X + 1), ch(LF_CH_X + 2));
   const float3 nb = f3(ch(LF_CH_N), ch(LF_CH_N + 1), ch(LF_CH_N + 2));
   const float3 ab = f3(ch(LF_CH_A), ch(LF_CH_A + 1), ch(LF_CH_A + 2));
   const float mb = ch(LF_CH_M), rb = ch(LF_CH_R);
   const int hits = (int)ch(LF_CH_HITS);
+  // upstream gradients on the record
   float3 g_n = f3(up(LF_CH_N), up(LF_CH_N + 1), up(LF_CH_N + 2));
   float3 g_a = f3(up(LF_CH_A), up(LF_CH_A + 1), up(LF_CH_A + 2));
   float g_m = up(LF_CH_M), g_r = up(LF_CH_R), g_T = up(LF_CH_T);
@@ -115,89 +115,42 @@ __device__ __forceinline__ bool back_setup(const TraceArgs& a, const float* __re
     g_r += __ldg(sg + 7 * P + p);
     g_T += __ldg(sg + 8 * P + p);
   }
-  if (gg) {  // rho = sum w a + T E(d)
+  // rho = sum w a + T E(d)
+  if (gg) {
     const float3 Ed = env_lookup(a.env, d);
     g_T += dot3(g_rho, Ed);
     env_scatter_p(a.env, d_env, d, g_rho * T);
   }
-  if (hits <= 0) return false;
-  const float inv = 1.0f / (W + a.P.eps_w);
-  b.gSx = g_x * inv;
-  b.gSa = g_a * inv + g_rho;
-  b.gSt = g_depth * inv;
-  b.gSm = g_m * inv;
-  b.gSr = g_r * inv;
+  if (hits <= 0) return;
+  const float inv = 1.0f / (W + Pm.eps_w);
+  const float3 gSx = g_x * inv, gSa = g_a * inv + g_rho;
+  const float gSt = g_depth * inv, gSm = g_m * inv, gSr = g_r * inv;
   float3 gmv = f3(0.f, 0.f, 0.f), mv = f3(0.f, 0.f, 0.f);
   if (nlen >= 1e-12f) {
     gmv = (g_n - nb * dot3(nb, g_n)) * (1.0f / nlen);
     mv = nb * nlen;
   }
-  b.gSn = gmv * inv;
-  b.gW = g_W - inv * (dot3(g_x, xb) + g_depth * depth + dot3(g_a, ab) + g_m * mb + g_r * rb + dot3(gmv, mv));
-  b.S = g_T * T;
-  b.Tn = T;
-  b.remaining = hits;
-  b.rounds = 0;
-  b.bound = ((unsigned long long)__float_as_uint(ch(LF_CH_TSTOP)) << 32) |
-            (unsigned long long)__float_as_uint(ch(LF_CH_STOPKEY_LO));
-  b.inclusive = true;
-  return true;
-}
-
-// Persistent: lanes take pixels in 16 x 8 tile order; per pixel, rounds of
-// "the K farthest hits at or below the bound" are processed back to front.
-__global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
-                                                       const float* __restrict__ gbuf,
-                                                       const float* __restrict__ sg,
-                                                       const float* __restrict__ gg, float* __restrict__ d_surfel,
-                                                       float* __restrict__ d_env, int* fetch) {
-  __shared__ Inst s_inst[LF_MAX_OBJECTS];
-  extern __shared__ int s_stack[];
-  load_instances_b(s_inst, a.insts, a.n_inst);
-  int* stack = s_stack + threadIdx.x;
-  const int tiles_x = (cam.W + 15) / 16, tiles_y = (cam.H + 7) / 8;
-  const int n = tiles_x * tiles_y * 128;
-  const size_t P = (size_t)cam.W * cam.H;
-  const DevParams& Pm = a.P;
-  const float3 o = cam.eye;
-  Counters cnt;
-  bool live = false, exhausted = false;
-  float3 d = f3(0.f, 0.f, 1.f);
-  Ray ray;
+  const float3 gSn = gmv * inv;
+  const float gW = g_W - inv * (dot3(g_x, xb) + g_depth * depth + dot3(g_a, ab) + g_m * mb + g_r * rb + dot3(gmv, mv));
+  float S = g_T * T;
+  float Tn = T;
+  int remaining = hits;
+  unsigned long long bound = ((unsigned long long)__float_as_uint(ch(LF_CH_TSTOP)) << 32) |
+                             (unsigned long long)__float_as_uint(ch(LF_CH_STOPKEY_LO));
+  bool inclusive = true;
   FarK kb;
+  kb.o = o;
+  kb.d = d;
   kb.P = Pm;
-  BackState b;
-  Trav tr;
-  while (true) {
-    const int k = warp_fetch(fetch, n, !live, exhausted);
-    if (!live && k < n) {
-      const int tile = k >> 7, w = k & 127;
-      const int x = (tile % tiles_x) * 16 + (w & 15), y = (tile / tiles_x) * 8 + (w >> 4);
-      if (x < cam.W && y < cam.H && back_setup(a, gbuf, sg, gg, P, y * cam.W + x, d, b, d_env)) {
-        ray = make_ray(o, d);
-        kb.o = o;
-        kb.d = d;
-        kb.reset(b.bound, b.inclusive);
-        tr.start(s_inst, a.n_inst, ray, kb.tlo(), kb.thi(), stack, TB);
-        live = true;
-      }
-    }
-    if (!__any_sync(0xffffffffu, live) && exhausted) break;
-    if (!live) continue;
-    const int leaf = tr.next_leaf(s_inst, ray, kb.tlo(), kb.thi(), stack, TB, cnt);
-    if (leaf >= 0) {
-      kb.leaf(leaf >> 25, leaf & 0xffffff, s_inst[leaf >> 25]);
-      continue;
-    }
-    if (tr.overflow) {
-      report(a.status, LF_ERR_STACK);
-      live = false;
-      continue;
-    }
-    const int nk = kb.cnt;
+  const Ray ray = make_ray(o, d);
+  Counters cnt;
+  for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
+    kb.reset(bound, inclusive);
+    traverse(s_inst, a.n_inst, ray, kb, s_stack + threadIdx.x, TB, a.status, cnt);
+    const int n = kb.cnt;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      if (j < nk && b.remaining > 0) {
+      if (j < n && remaining > 0) {
         const int code = kb.bc[j];
         const Inst& I = s_inst[code >> 24];
         const int l = code & 0xffffff;
@@ -207,43 +160,34 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
         hit_precise(rc, o, d, Pm, t, tl, alpha);
         const float3 nj = record_normal(rc, d);
         const float3 xj = o + d * t;
-        const float Tj = b.Tn / (1.0f - alpha);
-        const float wgt = Tj * alpha;
-        const float gw = b.gW + dot3(b.gSx, xj) + b.gSt * t + dot3(b.gSn, nj) + b.gSa.x * mt.x +
-                         b.gSa.y * mt.y + b.gSa.z * mt.z + b.gSm * mt.w + b.gSr * rc.g2.w;
-        const float g_alpha = Tj * gw - b.S / (1.0f - alpha);
-        b.S += gw * wgt;
-        b.Tn = Tj;
-        surfel_adjoint(sc, __float_as_int(rc.g1.w), o, d, Pm, g_alpha, b.gSx * wgt, b.gSt * wgt, b.gSn * wgt,
-                       b.gSa * wgt, b.gSm * wgt, b.gSr * wgt, d_surfel);
-        --b.remaining;
+        const float Tj = Tn / (1.0f - alpha);
+        const float w = Tj * alpha;
+        const float gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y +
+                         gSa.z * mt.z + gSm * mt.w + gSr * rc.g2.w;
+        const float g_alpha = Tj * gw - S / (1.0f - alpha);
+        S += gw * w;
+        Tn = Tj;
+        surfel_adjoint(sc, __float_as_int(rc.g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
+                       gSr * w, d_surfel);
+        --remaining;
       }
     }
-    if (b.remaining > 0 && nk == K && ++b.rounds < Pm.max_rounds) {
-      b.bound = kb.bk[K - 1];
-      b.inclusive = false;
-      kb.reset(b.bound, false);
-      tr.start(s_inst, a.n_inst, ray, kb.tlo(), kb.thi(), stack, TB);
-      continue;
+    if (remaining > 0) {
+      if (n < K) {  // the forward composited more hits than the re-traversal finds
+        report(a.status, LF_ERR_ROUND_LIMIT);
+        break;
+      }
+      bound = kb.bk[K - 1];
+      inclusive = false;
     }
-    // finished; hits left over mean the re-traversal found fewer hits than
-    // the forward composited
-    if (b.remaining > 0) report(a.status, LF_ERR_ROUND_LIMIT);
-    live = false;
   }
 }
 
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
                                   const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
-                                  int* fetch, int sms, cudaStream_t st) {
-  static int per_sm = 0;
-  if (!per_sm && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_backward, TB, STACK_SMEM) !=
-                      cudaSuccess || per_sm < 1))
-    per_sm = 1;
-  cudaError_t e = cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  k_trace_backward<<<per_sm * sms, TB, STACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env,
-                                                         fetch);
+                                  cudaStream_t st) {
+  dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
+  k_trace_backward<<<grid, TB, STACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env);
   return cudaGetLastError();
 }
 

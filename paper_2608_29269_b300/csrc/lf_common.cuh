@@ -484,40 +484,38 @@ __device__ __forceinline__ int entry_of(int ii, int child) {
   return child >= 0 ? ((ii << 25) | child) : ((ii << 25) | LEAF_BIT | ~child);
 }
 
-// Resumable depth-first traversal of the BLASes of every instance whose box
-// the ray enters, on one shared-memory stack.  next_leaf() descends internal
-// nodes until it reaches a leaf ("while-while", Aila and Laine 2009) and
-// returns it (or -1 when the ray's traversal is complete), so a persistent
-// kernel can interleave leaf work, per-ray events and fetching new rays.
-// `stack` points at this thread's first entry; entries are `stride` ints
-// apart.  A tree of n leaves has n - 1 internal nodes and a depth-first walk
-// visits each once: the visit budget only guards against a malformed tree.
-struct Trav {
-  int e, sp, budget;
-  bool overflow;
-
-  __device__ __forceinline__ void start(const Inst* insts, int n_inst, const Ray& ray, float tlo, float thi,
-                                        int* stack, int stride) {
-    sp = 0;
-    budget = 8;
-    overflow = false;
-    for (int ii = 0; ii < n_inst; ++ii) {  // instance 0 (background) is pushed first, popped last
-      const Inst& I = insts[ii];
-      if (I.root == INT_MIN) continue;
-      float tn;
-      if (!slab(I.lo[0], I.lo[1], I.lo[2], I.hi[0], I.hi[1], I.hi[2], ray, tlo, thi, tn)) continue;
-      if (sp >= STACK) { overflow = true; break; }
-      stack[(sp++) * stride] = entry_of(ii, I.root);
-      budget += 2 * I.n_leaves + 2;
+// Depth-first traversal of the BLASes of every instance whose box the ray
+// enters, on one shared-memory stack, organised "while-while" (Aila and Laine
+// 2009): each lane descends internal nodes until it holds a leaf, then the
+// lanes of the warp process their leaves together.  The visitor supplies the
+// culling interval [tlo(), thi()], consumes leaves and may end the ray early.
+// `stack` points at this thread's first entry; entries are `stride` ints apart.
+template <class V>
+__device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
+                                         int stride, int* status, Counters& cnt) {
+  int sp = 0;
+  // A tree of n leaves has n - 1 internal nodes; a depth-first walk visits
+  // each node at most once.  The budget only guards against a malformed tree.
+  int budget = 8;
+  for (int ii = 0; ii < n_inst; ++ii) {  // instance 0 (background) is pushed first, popped last
+    const Inst& I = insts[ii];
+    if (I.root == INT_MIN) continue;
+    float tn;
+    if (!slab(I.lo[0], I.lo[1], I.lo[2], I.hi[0], I.hi[1], I.hi[2], ray, vis.tlo(), vis.thi(), tn)) continue;
+    if (sp >= STACK) {
+      report(status, LF_ERR_STACK);
+      vis.abort();
+      return;
     }
-    e = sp > 0 ? stack[(--sp) * stride] : -1;
+    stack[(sp++) * stride] = entry_of(ii, I.root);
+    budget += 2 * I.n_leaves + 2;
   }
-
-  __device__ __forceinline__ int next_leaf(const Inst* insts, const Ray& ray, float lo, float hi, int* stack,
-                                           int stride, Counters& cnt) {
+  int e = sp > 0 ? stack[(--sp) * stride] : -1;
+  bool ok = true;
+  while (e >= 0) {
     while (e >= 0 && !(e & LEAF_BIT)) {
       if (--budget < 0 || sp >= STACK) {
-        overflow = true;
+        ok = false;
         e = -1;
         break;
       }
@@ -525,6 +523,7 @@ struct Trav {
       const int ii = e >> 25;
       const float4* N = insts[ii].nodes + 4 * (e & 0xffffff);
       const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), f = __ldg(N + 3);
+      const float lo = vis.tlo(), hi = vis.thi();
       float tl, tr;
       const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
       const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
@@ -541,27 +540,18 @@ struct Trav {
         e = sp > 0 ? stack[(--sp) * stride] : -1;
       }
     }
-    const int leaf = e;
     if (e >= 0) {
       ++cnt.tests;
+      const int ii = e >> 25;
+      vis.leaf(ii, e & 0xffffff, insts[ii]);
+      if (vis.done()) return;
       e = sp > 0 ? stack[(--sp) * stride] : -1;
     }
-    return leaf;
   }
-};
-
-// Warp-cooperative fetch of work items [0, n) from a global counter: lanes
-// with need == true get consecutive indices (>= n when the work is gone).
-// Called by all 32 lanes together; `exhausted` (warp-uniform) stops fetching.
-__device__ __forceinline__ int warp_fetch(int* counter, int n, bool need, bool& exhausted) {
-  const unsigned m = __ballot_sync(0xffffffffu, need && !exhausted);
-  if (m == 0u) return n;
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(counter, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (base + __popc(m) >= n) exhausted = true;
-  return need ? base + __popc(m & ((1u << lane) - 1u)) : n;
+  if (!ok) {
+    report(status, LF_ERR_STACK);
+    vis.abort();
+  }
 }
 
 // Collects the K smallest hit keys strictly greater than the last round's.
@@ -670,6 +660,21 @@ struct ShadowV {
   }
 };
 
+__device__ __forceinline__ float trace_shadow(const Inst* insts, int n_inst, float3 o, float3 d,
+                                              const DevParams& P, int* stack, int stride, int* status,
+                                              Counters& cnt) {
+  ShadowV v;
+  v.V = 1.0f;
+  v.stop = false;
+  v.o = o;
+  v.d = d;
+  v.P = P;
+  Ray ray = make_ray(o, d);
+  traverse(insts, n_inst, ray, v, stack, stride, status, cnt);
+  return v.V;
+}
+
+// Composited surface record of one ray (Eq. 7).
 struct Surface {
   float T, W, depth, m, r, nlen;
   float3 x, n, a;
@@ -678,27 +683,24 @@ struct Surface {
   unsigned long long stop_key;  // key of the last composited hit (0: none)
 };
 
-// Front-to-back compositing (Eq. 7) across k-buffer rounds, stopping after
-// the hit whose transmittance falls below T_min.
-struct Compositor {
-  float T, W, St, Sm, Sr;
-  float3 Sx, Sn, Sa;
-  int hits, rounds;
-  unsigned long long stop_key, last;
-
-  __device__ __forceinline__ void init() {
-    T = 1.0f;
-    W = St = Sm = Sr = 0.0f;
-    Sx = Sn = Sa = f3(0.f, 0.f, 0.f);
-    hits = rounds = 0;
-    stop_key = last = 0ull;
-  }
-
-  // Composite one round's buffer; true when the ray is finished.
-  __device__ __forceinline__ bool round(const NearK& kb, const Inst* insts, float3 o, float3 d, const DevParams& P,
-                                        int* status) {
+// Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop).
+__device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, float3 o, float3 d,
+                                                const DevParams& P, int* stack, int stride, int* status,
+                                                Counters& cnt, Surface& s, unsigned& composited) {
+  NearK kb;
+  kb.o = o;
+  kb.d = d;
+  kb.P = P;
+  Ray ray = make_ray(o, d);
+  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
+  float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
+  int hits = 0;
+  unsigned long long stop_key = 0ull, last = 0ull;
+  bool done = false;
+  for (int round = 0; round < P.max_rounds && !done; ++round) {
+    kb.reset(last);
+    traverse(insts, n_inst, ray, kb, stack, stride, status, cnt);
     const int n = kb.cnt;
-    bool done = false;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       if (j < n && !done) {
@@ -727,30 +729,24 @@ struct Compositor {
     if (!done && n < K) done = true;
     if (!done) {
       last = kb.bk[K - 1];
-      if (++rounds >= P.max_rounds) {
-        report(status, LF_ERR_ROUND_LIMIT);
-        done = true;
-      }
+      if (round == P.max_rounds - 1) report(status, LF_ERR_ROUND_LIMIT);
     }
-    return done;
   }
-
-  __device__ __forceinline__ void surface(float3 d, const DevParams& P, Surface& s) const {
-    const float inv = 1.0f / (W + P.eps_w);
-    s.T = T;
-    s.W = W;
-    s.x = Sx * inv;
-    s.depth = St * inv;
-    s.a = Sa * inv;
-    s.Sa = Sa;
-    s.m = Sm * inv;
-    s.r = Sr * inv;
-    const float3 mv = Sn * inv;
-    s.nlen = sqrtf(dot3(mv, mv));
-    s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
-    s.hits = hits;
-    s.stop_key = stop_key;
-  }
-};
+  composited += (unsigned)hits;
+  const float inv = 1.0f / (W + P.eps_w);
+  s.T = T;
+  s.W = W;
+  s.x = Sx * inv;
+  s.depth = St * inv;
+  s.a = Sa * inv;
+  s.Sa = Sa;
+  s.m = Sm * inv;
+  s.r = Sr * inv;
+  const float3 mv = Sn * inv;
+  s.nlen = sqrtf(dot3(mv, mv));
+  s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
+  s.hits = hits;
+  s.stop_key = stop_key;
+}
 
 }  // namespace lf

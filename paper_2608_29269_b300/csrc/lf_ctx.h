@@ -26,7 +26,6 @@ struct lf_ctx {
   int device = 0;
   int sms = 148;
   int* status_dev = nullptr;
-  int* fetch_dev = nullptr;  // work counters of persistent launches
   unsigned long long* counters = nullptr;
   std::string err;
   // scene (caller-owned arrays) and its object layout

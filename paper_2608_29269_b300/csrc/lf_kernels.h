@@ -59,13 +59,12 @@ struct TraceArgs {
   unsigned long long* counters;  // nullable: [nodes, tests, composited, rays]
 };
 
-cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, int* fetch, int sms,
-                                 cudaStream_t st);
+cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, cudaStream_t st);
 
 // Adjoint (lf_backward.cu)
 constexpr int SHADE_GRAD_CH = 9;  // per pixel: g_n (3), g_a (3), g_m, g_r, g_T
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
                                   const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
-                                  int* fetch, int sms, cudaStream_t st);
+                                  cudaStream_t st);
 
 }  // namespace lf

@@ -153,61 +153,49 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
 }
 
 // ---------------------------------------------------------------- shadow rays
-// Persistent: every lane keeps one ray in flight and fetches the next queue
-// entry as soon as its ray ends (warp-aggregated fetch), so a warp never waits
-// idle for its longest ray.
 // which = 0: NEE rays of queue A (origin from the G-buffer, direction we)
 // which = 1: secondary NEE rays of queue C (entry = item * 2 + q)
 __global__ void __launch_bounds__(WB) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S, int which, int* status,
                                                   unsigned long long* counters) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  __shared__ int s_job;
   extern __shared__ int s_stack[];
-  int* stack = s_stack + threadIdx.x;
   const int* q = which == 0 ? S.qA : S.qC;
   const int n = which == 0 ? S.counts[0] : S.counts[2];
-  int* fetch = S.counts + (which == 0 ? 3 : 5);
   Counters cnt;
-  bool live = false, exhausted = false;
-  int e = 0;
-  long long item = 0;
-  const Inst* insts = nullptr;
-  Ray ray;
-  ShadowV vis;
-  vis.P = P;
-  Trav tr;
-  while (true) {
-    const int k = warp_fetch(fetch, n, !live, exhausted);
-    if (!live && k < n) {
-      e = q[k];
-      item = which == 0 ? (long long)e : (long long)(e >> 1);
-      const ShadeJob& J = B.jobs[job_of_item(B, item)];
-      insts = J.insts;
+  // Jobs of a batch may have different scenes: blocks reload the instance
+  // table when the job of their first entry changes.
+  int loaded = -1;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int e = k < n ? q[k] : q[base];
+    const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+    const int j = job_of_item(B, item);
+    __syncthreads();
+    if (threadIdx.x == 0) s_job = j;
+    __syncthreads();
+    const int bj = s_job;
+    if (bj != loaded) {
+      load_insts(s_inst, B.jobs[bj].insts, B.jobs[bj].n_inst);
+      loaded = bj;
+    }
+    __syncthreads();
+    if (k < n) {
+      const ShadeJob& J = B.jobs[j];
+      const Inst* insts = (j == bj) ? s_inst : J.insts;
       float3 o, d;
       if (which == 0) {
-        o = pix_origin(J, (int)((item - J.item0) / J.spp), P.ray_offset);
+        const long long loc = item - J.item0;
+        o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
         d = ld3(S.we, item);
       } else {
         o = ld3(S.xs2, item);
         d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
       }
-      ray = make_ray(o, d);
-      vis.o = o;
-      vis.d = d;
-      vis.V = 1.0f;
-      vis.stop = false;
-      tr.start(insts, J.n_inst, ray, vis.tlo(), vis.thi(), stack, WB);
-      live = true;
-    }
-    if (!__any_sync(0xffffffffu, live) && exhausted) break;
-    if (live) {
-      const int leaf = tr.next_leaf(insts, ray, vis.tlo(), vis.thi(), stack, WB, cnt);
-      if (leaf >= 0) vis.leaf(leaf >> 25, leaf & 0xffffff, insts[leaf >> 25]);
-      if (leaf < 0 || vis.done()) {
-        if (tr.overflow) report(status, LF_ERR_STACK);
-        if (which == 0) S.Ve[item] = vis.V;
-        else if (e & 1) S.Vq1[item] = vis.V;
-        else S.Vq0[item] = vis.V;
-        live = false;
-      }
+      const float V = trace_shadow(insts, J.n_inst, o, d, P, s_stack + threadIdx.x, WB, status, cnt);
+      if (which == 0) S.Ve[item] = V;
+      else if (e & 1) S.Vq1[item] = V;
+      else S.Vq0[item] = V;
     }
   }
   if (counters) {
@@ -219,81 +207,60 @@ __global__ void __launch_bounds__(WB) k_wf_shadow(ShadeBatch B, DevParams P, Sam
 // ---------------------------------------------------------------- continuation rays
 __global__ void __launch_bounds__(WB) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S, int* status,
                                                     unsigned long long* counters) {
+  __shared__ Inst s_inst[LF_MAX_OBJECTS];
+  __shared__ int s_job;
   extern __shared__ int s_stack[];
-  int* stack = s_stack + threadIdx.x;
   const int n = S.counts[1];
   Counters cnt;
   unsigned comp = 0;
-  bool live = false, exhausted = false;
-  long long item = 0;
-  int job = 0;
-  const Inst* insts = nullptr;
-  Ray ray;
-  NearK kb;
-  kb.P = P;
-  Compositor cp;
-  Trav tr;
-  while (true) {
-    const int k = warp_fetch(S.counts + 4, n, !live, exhausted);
-    if (!live && k < n) {
-      item = (long long)S.qB[k];
-      job = job_of_item(B, item);
-      const ShadeJob& J = B.jobs[job];
-      insts = J.insts;
-      const float3 o = pix_origin(J, (int)((item - J.item0) / J.spp), P.ray_offset);
-      const float3 d = ld3(S.wi, item);
-      ray = make_ray(o, d);
-      kb.o = o;
-      kb.d = d;
-      kb.reset(0ull);
-      cp.init();
-      tr.start(insts, J.n_inst, ray, kb.tlo(), kb.thi(), stack, WB);
-      live = true;
+  int loaded = -1;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    const long long item = (long long)(k < n ? S.qB[k] : S.qB[base]);
+    const int j = job_of_item(B, item);
+    __syncthreads();
+    if (threadIdx.x == 0) s_job = j;
+    __syncthreads();
+    const int bj = s_job;
+    if (bj != loaded) {
+      load_insts(s_inst, B.jobs[bj].insts, B.jobs[bj].n_inst);
+      loaded = bj;
     }
-    if (!__any_sync(0xffffffffu, live) && exhausted) break;
-    if (!live) continue;
-    const int leaf = tr.next_leaf(insts, ray, kb.tlo(), kb.thi(), stack, WB, cnt);
-    if (leaf >= 0) {
-      kb.leaf(leaf >> 25, leaf & 0xffffff, insts[leaf >> 25]);
-      continue;
-    }
-    // end of a k-buffer round
-    bool fin = tr.overflow;
-    if (fin) report(status, LF_ERR_STACK);
-    else fin = cp.round(kb, insts, kb.o, kb.d, P, status);
-    if (!fin) {
-      kb.reset(cp.last);
-      tr.start(insts, B.jobs[job].n_inst, ray, kb.tlo(), kb.thi(), stack, WB);
-      continue;
-    }
-    live = false;
-    comp += (unsigned)cp.hits;
-    Surface s2;
-    cp.surface(kb.d, P, s2);
-    S.T2[item] = s2.T;
-    if (s2.hits == 0) continue;
-    const ShadeJob& J = B.jobs[job];
-    const long long loc = item - J.item0;
-    const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
-    const float3 n2 = s2.n, wo2 = -kb.d;
-    const float co2 = dot3(n2, wo2);
-    st3(S.xs2, item, s2.x + n2 * P.ray_offset);
-    const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
-    const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
-    const float uq[4] = {unit24(gb.y), unit24(gb.z), unit24(gb.w), unit24(gc.x)};
+    __syncthreads();
+    bool push0 = false, push1 = false;
+    if (k < n) {
+      const ShadeJob& J = B.jobs[j];
+      const Inst* insts = (j == bj) ? s_inst : J.insts;
+      const long long loc = item - J.item0;
+      const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+      const float3 xs = pix_origin(J, p, P.ray_offset);
+      const float3 wi = ld3(S.wi, item);
+      Surface s2;
+      trace_composite(insts, J.n_inst, xs, wi, P, s_stack + threadIdx.x, WB, status, cnt, s2, comp);
+      S.T2[item] = s2.T;
+      if (s2.hits > 0) {
+        const float3 n2 = s2.n, wo2 = -wi;
+        const float co2 = dot3(n2, wo2);
+        st3(S.xs2, item, s2.x + n2 * P.ray_offset);
+        const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
+        const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
+        const float uq[4] = {unit24(gb.y), unit24(gb.z), unit24(gb.w), unit24(gc.x)};
 #pragma unroll
-    for (int qq = 0; qq < 2; ++qq) {
-      float3 wq;
-      float pq;
-      env_sample(J.env, uq[2 * qq], uq[2 * qq + 1], wq, pq);
-      const float cq = dot3(n2, wq);
-      const bool ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
-      float3 fk = f3(0.f, 0.f, 0.f);
-      if (ok) fk = brdf_eval(n2, wo2, wq, s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f / pq);
-      st3(qq == 0 ? S.wq0 : S.wq1, item, wq);
-      st3(qq == 0 ? S.fk0 : S.fk1, item, fk);
-      if (ok) S.qC[atomicAdd(S.counts + 2, 1)] = (int)(item * 2 + qq);
+        for (int qq = 0; qq < 2; ++qq) {
+          float3 wq;
+          float pq;
+          env_sample(J.env, uq[2 * qq], uq[2 * qq + 1], wq, pq);
+          const float cq = dot3(n2, wq);
+          const bool ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
+          float3 fk = f3(0.f, 0.f, 0.f);
+          if (ok) fk = brdf_eval(n2, wo2, wq, s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f / pq);
+          if (qq == 0) { st3(S.wq0, item, wq); st3(S.fk0, item, fk); push0 = ok; }
+          else { st3(S.wq1, item, wq); st3(S.fk1, item, fk); push1 = ok; }
+        }
+      }
     }
+    queue_push(S.qC, S.counts + 2, (int)(item * 2), push0);
+    queue_push(S.qC, S.counts + 2, (int)(item * 2 + 1), push1);
   }
   if (counters) {
     atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
@@ -453,7 +420,7 @@ __global__ void k_wf_count(const int* counts, unsigned long long* ray_count) {
 // ---------------------------------------------------------------- host side
 size_t sample_buf_bytes(long long n_items) {
   const size_t ns = (size_t)n_items;
-  return sizeof(float) * SAMPLE_PLANES * ns + sizeof(int) * 4 * ns + 256;  // + 8 counters
+  return sizeof(float) * SAMPLE_PLANES * ns + sizeof(int) * 4 * ns + 256;
 }
 
 SampleBuf sample_buf(void* base, long long n_items) {
@@ -489,26 +456,18 @@ static int wf_grid(long long n, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sms * 16));
 }
 
-static int persistent_grid(const void* kernel, int smem, int sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WB, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  return per_sm * sms;
-}
-
 cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, int* status,
                                    unsigned long long* ray_count, unsigned long long* counters, int sms,
                                    cudaStream_t st) {
   if (B.n_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(S.counts, 0, 8 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(S.counts, 0, 4 * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  static int g_shadow = 0, g_continue = 0;  // persistent grid sizes (per process: one device model)
-  if (!g_shadow) g_shadow = persistent_grid((const void*)k_wf_shadow, WSTACK_SMEM, sms);
-  if (!g_continue) g_continue = persistent_grid((const void*)k_wf_continue, WSTACK_SMEM, sms);
   k_wf_gen<<<wf_grid(B.n_items, sms), WB, 0, st>>>(B, P, S);
-  k_wf_shadow<<<g_shadow, WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
-  k_wf_continue<<<g_continue, WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
-  k_wf_shadow<<<g_shadow, WB, WSTACK_SMEM, st>>>(B, P, S, 1, status, counters);
+  // queue lengths are known only on the device: the trace kernels size
+  // their loops from the counters (grids cover the worst case).
+  k_wf_shadow<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
+  k_wf_continue<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
+  k_wf_shadow<<<wf_grid(2 * B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 1, status, counters);
   k_wf_count<<<1, 32, 0, st>>>(S.counts, ray_count);
   return cudaGetLastError();
 }

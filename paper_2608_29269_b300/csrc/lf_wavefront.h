@@ -50,7 +50,7 @@ struct SampleBuf {
   int* qA;
   int* qB;
   int* qC;
-  int* counts;  // queue lengths A, B, C; fetch positions A, B, C
+  int* counts;  // queue lengths A, B, C
 };
 
 size_t sample_buf_bytes(long long n_items);
