@@ -208,6 +208,29 @@ lf_status lf_shade_bounce(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_d
                           uint64_t seed, float* rgb_dev, unsigned long long* ray_count_dev, void* samples_dev,
                           size_t samples_bytes);
 
+/*
+ * Allocation-free variant of lf_shade_bounce.  The paper has no counterpart:
+ * this is a convenience of the library.  It is for callers that cannot
+ * allocate device memory (a host whose device memory is owned by another
+ * allocator, a plugin that may not call cudaMalloc, a loop that must not
+ * allocate after start-up): instead of a caller buffer, the per-sample
+ * scratch is a fixed array of LF_STATIC_SCRATCH_BYTES inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Same arguments and results as lf_shade_bounce without the sample buffer.
+ *   - width * height * spp must be at most (LF_STATIC_SCRATCH_BYTES - 256) /
+ *     128 = 524286 samples; larger requests return LF_ERR_INVALID with a
+ *     message and enqueue nothing.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; each
+ *     call clears the counters that must start at zero.  Calls whose work
+ *     overlaps on the GPU (other streams, contexts or threads) race on it.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define LF_STATIC_SCRATCH_BYTES (64u << 20)
+lf_status lf_shade_bounce_static(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
+                                 uint64_t seed, float* rgb_dev, unsigned long long* ray_count_dev);
+
 /* Scratch bytes lf_trace_backward needs for a width x height image at spp
  * samples when it has to replay the shading (fwd_samples == NULL); with the
  * forward's sample buffer it needs 9 * width * height floats (+256 B). */
