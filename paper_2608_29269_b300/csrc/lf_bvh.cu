@@ -261,13 +261,21 @@ __device__ __forceinline__ void write_child_box(float4* node, int side, float3 l
 // One thread per leaf of the selected objects: pack the surfel's records,
 // compute its box and propagate boxes to the root; the second child to
 // arrive at a node forms the union (atomic visit counter per node).
+//
+// Index bases: the leaves, node links and sorted ids are those of the build
+// (global numbering); a.leaf_base / a.node_base / a.id_base / a.inst_base are
+// subtracted when writing records, nodes, flags and the instance entry and
+// when reading the raw attributes, so the same kernel fits both the
+// context's own storage (bases 0) and an object-local copy (a served version).
 __global__ void k_pack_fit(SceneDev s, FitArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n_leaves) return;
   const int L = a.first_leaf + g;
   const int obj = object_of(a.leaf_off, a.n_obj, L);
   const int lb = a.leaf_off[obj], n = a.leaf_off[obj + 1] - lb, nb = a.node_off[obj];
-  const int i = (int)a.sorted_ids[L];
+  const int id = (int)a.sorted_ids[L];
+  const int i = id - a.id_base;  // raw attribute index
+  const int Lw = L - a.leaf_base, nbw = nb - a.node_base;
   // pack
   const float su = s.scale[2 * i], sv = s.scale[2 * i + 1];
   const float3 mu = f3(s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]);
@@ -277,14 +285,14 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
   const double cx = (double)tu.y * tv.z - (double)tu.z * tv.y, cy = (double)tu.z * tv.x - (double)tu.x * tv.z,
                cz = (double)tu.x * tv.y - (double)tu.y * tv.x;
   const double cl = sqrt(cx * cx + cy * cy + cz * cz);
-  a.geo[GEO * L + 0] = make_float4(mu.x, mu.y, mu.z, s.opacity[i]);
-  a.geo[GEO * L + 1] = make_float4(tu.x / su, tu.y / su, tu.z / su, __int_as_float(i));
-  a.geo[GEO * L + 2] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, s.roughness[i]);
-  a.geo[GEO * L + 3] = make_float4((float)(cx / cl), (float)(cy / cl), (float)(cz / cl), 0.0f);
-  a.mat[L] = make_float4(s.albedo[3 * i], s.albedo[3 * i + 1], s.albedo[3 * i + 2], s.metallic[i]);
+  a.geo[GEO * Lw + 0] = make_float4(mu.x, mu.y, mu.z, s.opacity[i]);
+  a.geo[GEO * Lw + 1] = make_float4(tu.x / su, tu.y / su, tu.z / su, __int_as_float(id));
+  a.geo[GEO * Lw + 2] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, s.roughness[i]);
+  a.geo[GEO * Lw + 3] = make_float4((float)(cx / cl), (float)(cy / cl), (float)(cz / cl), 0.0f);
+  a.mat[Lw] = make_float4(s.albedo[3 * i], s.albedo[3 * i + 1], s.albedo[3 * i + 2], s.metallic[i]);
   float3 lo, hi;
   surfel_box(s, i, a.R, lo, hi);
-  Inst* inst = a.insts + obj;
+  Inst* inst = a.insts + (obj - a.inst_base);
   if (n == 1) {
     inst->lo[0] = lo.x; inst->lo[1] = lo.y; inst->lo[2] = lo.z;
     inst->hi[0] = hi.x; inst->hi[1] = hi.y; inst->hi[2] = hi.z;
@@ -297,10 +305,10 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
       return;
     }
     const int p = link >> 1, side = link & 1;
-    float4* node = a.nodes + 4 * (nb + p);
+    float4* node = a.nodes + 4 * (nbw + p);
     write_child_box(node, side, lo, hi);
     __threadfence();
-    if (atomicAdd(a.flags + nb + p, 1) == 0) return;
+    if (atomicAdd(a.flags + nbw + p, 1) == 0) return;
     __threadfence();
     const float* f = reinterpret_cast<const float*>(node);
     lo = f3(fminf(__ldcg(f + 0), __ldcg(f + 6)), fminf(__ldcg(f + 1), __ldcg(f + 7)), fminf(__ldcg(f + 2), __ldcg(f + 8)));
@@ -381,6 +389,15 @@ __global__ void k_env_marginal(const double* __restrict__ rowsum, int H, float* 
   }
 }
 
+// Instance table of one request: copy each object's current version entry.
+__global__ void k_gather_insts(InstPtrs src, Inst* __restrict__ dst, int n) {
+  const int k = blockIdx.x;
+  if (k >= n) return;
+  const float4* s = reinterpret_cast<const float4*>(src.p[k]);
+  float4* d = reinterpret_cast<float4*>(dst + k);
+  if (threadIdx.x < 4) d[threadIdx.x] = s[threadIdx.x];
+}
+
 __global__ void k_philox(const uint4* __restrict__ ctr, int n, uint32_t k0, uint32_t k1, uint4* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
@@ -452,6 +469,11 @@ cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, in
                               float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st) {
   k_env_rows<<<(H + 63) / 64, 64, 0, st>>>(rgb, sin_row, H, W, rowsum, pmf_col, cdf_col);
   k_env_marginal<<<1, 1, 0, st>>>(rowsum, H, pmf_row, cdf_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_insts(const InstPtrs& src, Inst* dst, int n, cudaStream_t st) {
+  if (n > 0) k_gather_insts<<<n, 32, 0, st>>>(src, dst, n);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,11 @@ struct FitArgs {
   Inst* insts;
   float R;  // support radius
   int* status;
+  int leaf_base = 0, node_base = 0, id_base = 0, inst_base = 0;  // object-local storage (served versions)
+};
+
+struct InstPtrs {
+  const Inst* p[LF_MAX_OBJECTS];
 };
 
 // BVH build / refit (lf_bvh.cu)
@@ -47,6 +52,7 @@ cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int
                             cudaStream_t st);
 cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, int W, double* rowsum, float* pmf_row,
                               float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st);
+cudaError_t launch_gather_insts(const InstPtrs& src, Inst* dst, int n, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st);
 
 // Rendering (lf_render.cu)
