@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--size", type=int, default=800)
     ap.add_argument("--spp", type=int, default=16)
+    ap.add_argument("--serve", action="store_true", help="served vs plain loop sweep only (C5-style)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the small served-vs-plain comparison")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rates", default="0.5,1,2")
+    ap.add_argument("--serve-scene", default="c4", choices=["c2", "c4"])
     return ap.parse_args()
 
 
@@ -240,8 +245,85 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def serving_compare(sc, envs, n_req, rate, resolutions, spps, seed, budget=40 << 30, max_slots=8, n_streams=4):
+    """Served loop vs the plain per-request rebuild-and-render loop on the same
+    request stream: p50 / p99 edit-to-frame latency (ms) and Mrays/s."""
+    import numpy as np
+    import torch
+    from paper_2608_29269_b300 import SceneTensors, Tracer
+    from paper_2608_29269_b300.serve import Server, run_plain, run_served
+    from synthetic.requests import request_stream
+    reqs = request_stream(n_req, rate, sc, n_envs=len(envs), resolutions=resolutions, spps=spps, seed=seed)
+    out = {}
+    tr = Tracer()
+    st = SceneTensors.from_numpy(sc)
+    tr.build(st)
+    env_t = [torch.as_tensor(e.rgb, device="cuda").contiguous() for e in envs]
+    for i, e in enumerate(env_t):
+        tr.set_env(i, e)
+    srv = Server(tr, budget_bytes=budget, max_slots=max_slots, n_streams=n_streams)
+    t0 = time.perf_counter()
+    served = run_served(srv, reqs)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r["latency"] for r in served if r["status"] == 0]) * 1e3
+    # rays per request: shading rays of its launch group are shared; estimate from the plain loop's counts below
+    out["served"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "completed": int(len(lat)), "wall_s": wall}
+    rays = torch.zeros(1, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    plain = run_plain_counted(tr, reqs, rays)
+    wall_p = time.perf_counter() - t0
+    latp = np.array([r["latency"] for r in plain]) * 1e3
+    total_rays = float(rays.item()) + sum(r.cam.width * r.cam.height for r in reqs)
+    out["plain"] = {"p50_ms": float(np.percentile(latp, 50)), "p99_ms": float(np.percentile(latp, 99)),
+                    "completed": int(len(latp)), "wall_s": wall_p, "mrays_s": total_rays / wall_p / 1e6}
+    out["served"]["mrays_s"] = total_rays / wall / 1e6
+    out["requests"] = n_req
+    out["rate_per_s"] = rate
+    tr.close()
+    return out
+
+
+def run_plain_counted(tracer, requests, rays):
+    """The plain loop (edit, full rebuild, render, frame to host, sync) counting shading rays."""
+    env_state = dict(env=0)
+    from paper_2608_29269_b300.serve import apply_edit
+    t0 = time.perf_counter()
+    out = []
+    for rq in requests:
+        arrival = t0 + rq.arrival
+        now = time.perf_counter()
+        if now < arrival:
+            time.sleep(arrival - now)
+        apply_edit(tracer, rq.edit, env_state)
+        tracer.build(tracer.scene)
+        g = tracer.trace_primary(rq.cam, env_state["env"])
+        rgb = tracer.shade(rq.cam, g, env_state["env"], rq.spp, rq.seed, ray_count=rays)
+        rgb.cpu()
+        tracer.sync()
+        out.append(dict(latency=time.perf_counter() - arrival))
+    return out
+
+
+def run_serve_sweep(args):
+    from synthetic import scenes as S
+    sc = S.scene_c4(0) if args.serve_scene == "c4" else S.scene_c2(0)
+    envs = [S.env_sky_sun(i) for i in range(3)]
+    res = {}
+    for rate in [float(x) for x in args.rates.split(",")]:
+        res[str(rate)] = serving_compare(sc, envs, args.requests, rate, (256, 512, 800, 1024), (4, 8, 16, 32), seed=5)
+    line = {"metric": "p50/p99 edit-to-frame ms, served vs plain loop", "unit": "ms", "higher_is_better": False,
+            "scene": f"{args.serve_scene}: {sc.n} surfels, {sc.n_objects} objects", "budget_gb": 40,
+            "requests_per_rate": args.requests, "rates": res, "data": "synthetic (seeded)"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.serve:
+        run_serve_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -307,13 +389,7 @@ def main():
     shade_rays = int(step.rays.item())
     rays = shade_rays + args.steps * cam.width * cam.height
     fwd_ms = sum(phase_ms["primary"]) + sum(phase_ms["shade"])
-    t = torch.tensor([total_ms, fwd_ms], dtype=torch.float64, device="cuda")
-    r = torch.tensor([rays], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(r, op=dist.ReduceOp.SUM)
-    total_ms, fwd_ms = float(t[0]), float(t[1])
-    rays_all = float(r[0])
+    total_ms, fwd_ms, rays_all = reduce_over_ranks(total_ms, fwd_ms, rays, "cuda")
     value = rays_all / (total_ms * 1e-3) / 1e6
     fwd_value = rays_all / (fwd_ms * 1e-3) / 1e6
 
@@ -355,6 +431,14 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps * sum(KERNELS_PER_STEP.values()),
     }
+    if not args.no_serving:
+        try:
+            from synthetic import scenes as S
+            line["serving"] = dict(serving_compare(sc, [env, S.env_sky_sun(1), S.env_sky_sun(2)], 24, 4.0,
+                                                   (256, 512), (4, 8), seed=11),
+                                   scene="200k-surfel room", resolutions=[256, 512], spp=[4, 8])
+        except Exception as exc:
+            line["serving"] = {"error": str(exc)}
     if not args.no_cpu_baseline:
         try:
             import oracle
@@ -371,6 +455,18 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def reduce_over_ranks(total_ms, fwd_ms, rays, device):
+    """Replicas: the job's time is the slowest rank's, its rays the sum of all ranks'."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, fwd_ms], dtype=torch.float64, device=device)
+    r = torch.tensor([float(rays)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(r[0])
 
 
 def read_traffic():

@@ -316,9 +316,16 @@ typedef struct {
 
 typedef struct lf_serve lf_serve;
 
-/* Create a server over the context's built scene and environments.
- * mem_budget_bytes bounds frame + version memory of in-flight requests. */
-lf_status lf_serve_create(lf_ctx* ctx, size_t mem_budget_bytes, int max_slots, int n_streams, lf_serve** out);
+/* Create a server over the context's built scene and environments (the
+ * context's scene must not be modified while the server runs).
+ * mem_budget_bytes bounds the device memory of in-flight requests (frame,
+ * G-buffer, per-sample buffer) and of live object versions; max_slots bounds
+ * the requests in flight; n_streams is the stream pool the launch groups
+ * rotate over; batch_window_us is how long the oldest pending request may
+ * wait for others to join its launch group while slots are free (0: admit
+ * at once).  Frames are at most 1024 x 1024. */
+lf_status lf_serve_create(lf_ctx* ctx, size_t mem_budget_bytes, int max_slots, int n_streams, int batch_window_us,
+                          lf_serve** out);
 /* Enqueue a request (host copy); returns its ticket.  Never blocks. */
 lf_status lf_serve_submit(lf_serve* srv, const lf_request* req, uint64_t* ticket);
 /* done = 1 when finished; then frame_host (width*height*3 floats, may be

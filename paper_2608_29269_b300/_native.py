@@ -82,7 +82,7 @@ SIGNATURES = [
     ("lf_env_tables", C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     ("lf_bvh_info", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("lf_bvh_copy_nodes", C.c_int, [_P, C.c_int, _P, C.c_size_t]),
-    ("lf_serve_create", C.c_int, [_P, C.c_size_t, C.c_int, C.c_int, C.POINTER(_P)]),
+    ("lf_serve_create", C.c_int, [_P, C.c_size_t, C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
     ("lf_serve_submit", C.c_int, [_P, C.POINTER(LfRequest), C.POINTER(C.c_uint64)]),
     ("lf_serve_poll", C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int), _P, C.c_size_t, C.POINTER(LfTiming)]),
     ("lf_serve_wait", C.c_int, [_P, C.c_uint64, C.c_int]),

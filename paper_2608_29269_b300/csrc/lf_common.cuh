@@ -554,75 +554,45 @@ __device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ra
   }
 }
 
-// Collects the K smallest hit keys strictly greater than the last round's,
-// with their alpha~.  It also tracks the transmittance of its sorted entries
-// from the round's starting transmittance T0: once it falls below T_min at
-// entry c, compositing will stop at c, so nothing behind c can matter; the
-// buffer is cut there and the culling window shrinks to c's depth (the
-// product is formed exactly like the compositor's, so both agree on c).
+// Collects the K smallest hit keys strictly greater than the last round's.
 struct NearK {
   unsigned long long bk[K];
   int bc[K];
-  float ba[K];
-  int cnt;                    // entries held
-  bool cut;                   // the transmittance fell below T_min inside the buffer
-  unsigned long long wkey;    // key of the last held entry once the buffer is full or cut
-  float T0;
+  int cnt;
   unsigned long long last;
   float3 o, d;
   DevParams P;
 
-  __device__ __forceinline__ void reset(unsigned long long lk, float t0) {
+  __device__ __forceinline__ void reset(unsigned long long lk) {
 #pragma unroll
-    for (int j = 0; j < K; ++j) { bk[j] = ~0ull; bc[j] = 0; ba[j] = 0.0f; }
+    for (int j = 0; j < K; ++j) { bk[j] = ~0ull; bc[j] = 0; }
     cnt = 0;
-    cut = false;
-    wkey = ~0ull;
-    T0 = t0;
     last = lk;
   }
-  __device__ __forceinline__ bool full() const { return cut || cnt >= K; }
   __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, key_t(last)); }
-  __device__ __forceinline__ float thi() const { return full() ? key_t(wkey) : BIG_F; }
+  __device__ __forceinline__ float thi() const { return cnt >= K ? key_t(bk[K - 1]) : BIG_F; }
   __device__ __forceinline__ bool done() const { return false; }
-  __device__ __forceinline__ void abort() { cnt = 0; cut = false; }
+  __device__ __forceinline__ void abort() { cnt = 0; }
   __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
     const Rec r = load_rec(I.geo, l);
     float t32;
     if (!hit_quick(r, o, d, P, t32)) return;
-    if (full() && t32 > thi() * 1.0001f + 1e-6f) return;  // beyond the window (FP32 depth, safe margin)
+    if (cnt >= K && t32 > thi() * 1.0001f + 1e-6f) return;  // beyond the window (FP32 depth, safe margin)
     float t, tl, alpha;
     if (!hit_precise(r, o, d, P, t, tl, alpha)) return;
     const unsigned long long key = hit_key(t, tl, __float_as_int(r.g1.w));
-    if (key <= last || (full() && key >= wkey)) return;
+    if (key <= last || (cnt >= K && key >= bk[K - 1])) return;
     int p = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) p += (j < cnt && bk[j] < key) ? 1 : 0;
+    for (int j = 0; j < K; ++j) p += bk[j] < key ? 1 : 0;
 #pragma unroll
     for (int j = K - 1; j > 0; --j)
-      if (j > p) { bk[j] = bk[j - 1]; bc[j] = bc[j - 1]; ba[j] = ba[j - 1]; }
+      if (j > p) { bk[j] = bk[j - 1]; bc[j] = bc[j - 1]; }
     const int code = (ii << 24) | l;
 #pragma unroll
     for (int j = 0; j < K; ++j)
-      if (j == p) { bk[j] = key; bc[j] = code; ba[j] = alpha; }
+      if (j == p) { bk[j] = key; bc[j] = code; }
     cnt = min(cnt + 1, K);
-    float T = T0;
-    int c = -1;
-    unsigned long long ck = ~0ull;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      if (j < cnt && c < 0) {
-        T = __fmul_rn(T, __fsub_rn(1.0f, ba[j]));
-        if (T < P.T_min) { c = j; ck = bk[j]; }
-      }
-    }
-    if (c >= 0) {
-      cnt = c + 1;
-      cut = true;
-      wkey = ck;
-    } else if (cnt >= K) {
-      wkey = bk[K - 1];
-    }
   }
 };
 
@@ -728,7 +698,7 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
   unsigned long long stop_key = 0ull, last = 0ull;
   bool done = false;
   for (int round = 0; round < P.max_rounds && !done; ++round) {
-    kb.reset(last, T);
+    kb.reset(last);
     traverse(insts, n_inst, ray, kb, stack, stride, status, cnt);
     const int n = kb.cnt;
 #pragma unroll
@@ -750,7 +720,7 @@ __device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, f
         add3(Sa, f3(mt.x, mt.y, mt.z) * w);
         Sm += w * mt.w;
         Sr += w * rc.g2.w;
-        T = __fmul_rn(T, __fsub_rn(1.0f, alpha));  // formed exactly as in NearK
+        T *= (1.0f - alpha);
         ++hits;
         stop_key = kb.bk[j];
         if (T < P.T_min) done = true;

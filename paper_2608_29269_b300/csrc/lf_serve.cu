@@ -102,6 +102,7 @@ struct lf_serve {
   lf_ctx* ctx = nullptr;
   size_t budget = 0, used = 0;
   int max_slots = 1, in_flight = 0;
+  double window_s = 0.0;  // how long a lone request waits for company
   std::vector<cudaStream_t> streams;
   int next_stream = 0;
   cudaStream_t edit_stream = nullptr;
@@ -364,6 +365,16 @@ void worker_main(lf_serve* s) {
       s->cv_done.notify_all();
     }
     if (s->stop && s->pending.empty() && s->groups.empty()) break;
+    // batching window: a request that arrived less than window_s ago waits
+    // for more company while slots are free
+    if (!s->pending.empty() && s->window_s > 0.0 && !s->stop &&
+        (int)s->pending.size() < std::min(MAX_JOBS, s->max_slots - s->in_flight)) {
+      const double age = now_s() - s->pending.front()->t_submit;
+      if (age < s->window_s) {
+        s->cv_work.wait_for(lock, std::chrono::duration<double>(std::min(s->window_s - age, 0.0005)));
+        continue;
+      }
+    }
     // admit a group in FIFO order
     Group* g = nullptr;
     while (!s->pending.empty() && s->in_flight < s->max_slots && !s->frame_pool.empty() &&
@@ -459,8 +470,9 @@ bool valid_request(const lf_serve* s, const lf_request* r) {
 
 extern "C" {
 
-lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams, lf_serve** out) {
-  if (!c || !out || max_slots < 1 || n_streams < 1 || budget == 0) return LF_ERR_INVALID;
+lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams, int batch_window_us,
+                          lf_serve** out) {
+  if (!c || !out || max_slots < 1 || n_streams < 1 || budget == 0 || batch_window_us < 0) return LF_ERR_INVALID;
   if (!c->built) return LF_ERR_NOT_BUILT;
   int env0 = -1;
   for (int i = 0; i < LF_MAX_ENVS; ++i)
@@ -470,6 +482,7 @@ lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams
   s->ctx = c;
   s->budget = budget;
   s->max_slots = max_slots;
+  s->window_s = 1e-6 * batch_window_us;
   s->env_id = env0;
   if (cudaStreamCreateWithFlags(&s->edit_stream, cudaStreamNonBlocking) != cudaSuccess) return LF_ERR_CUDA;
   if (cudaEventCreateWithFlags(&s->edit_event, cudaEventDisableTiming) != cudaSuccess) return LF_ERR_CUDA;

@@ -46,12 +46,13 @@ def request_struct(edit: Optional[dict], cam, spp: int, seed: int) -> N.LfReques
 class Server:
     """lf_serve: continuous batching over a device-resident scene."""
 
-    def __init__(self, tracer: Tracer, budget_bytes: int, max_slots: int = 8, n_streams: int = 4):
+    def __init__(self, tracer: Tracer, budget_bytes: int, max_slots: int = 8, n_streams: int = 4,
+                 batch_window_us: int = 0):
         self.tr = tracer
         self.lib = tracer.lib
         h = C.c_void_p()
         st = self.lib.lf_serve_create(tracer.ctx, C.c_size_t(int(budget_bytes)), int(max_slots), int(n_streams),
-                                      C.byref(h))
+                                      int(batch_window_us), C.byref(h))
         if st != N.LF_OK:
             raise N.LightFuseError(st, "lf_serve_create")
         self.h = h

@@ -31,7 +31,7 @@ def test_served_frames_equal_alone_and_plain_loop():
     from paper_2608_29269_b300.serve import Server, run_plain, run_served
     sc, tr, st = _setup()
     reqs = _requests(sc)
-    srv = Server(tr, budget_bytes=2 << 30, max_slots=8, n_streams=3)
+    srv = Server(tr, budget_bytes=2 << 30, max_slots=8, n_streams=3, batch_window_us=50_000)
     mix = run_served(srv, reqs, keep_frames=True)
     srv.close()
     srv1 = Server(tr, budget_bytes=2 << 30, max_slots=1, n_streams=1)

@@ -1,0 +1,66 @@
+"""Host-side logic without a GPU: multi-rank aggregation of the benchmark
+(world size 2 over gloo) and the seeded request streams of the served loop."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    total, fwd, rays = bench.reduce_over_ranks(100.0 + 50 * rank, 10.0 * (rank + 1), 1000 * (rank + 1), "cpu")
+    out[rank] = (total, fwd, rays)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_timing_is_max_and_rays_are_summed_over_ranks():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        assert out[r] == (150.0, 20.0, 3000.0)
+
+
+def test_single_process_aggregation_is_identity():
+    import bench
+    assert bench.reduce_over_ranks(12.5, 3.0, 77, "cpu") == (12.5, 3.0, 77.0)
+
+
+def test_request_stream_is_seeded_poisson_with_valid_edits():
+    from synthetic import scenes as S
+    from synthetic.requests import request_stream
+    sc = S.scene_c2(0, per_face=200, per_object=300)
+    a = request_stream(400, 5.0, sc, seed=1)
+    b = request_stream(400, 5.0, sc, seed=1)
+    assert [r.arrival for r in a] == [r.arrival for r in b]
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert abs(gaps.mean() - 0.2) < 0.03 and np.all(gaps > 0)
+    kinds = {r.edit["kind"] for r in a}
+    assert kinds == {"move", "material", "env"}
+    for r in a:
+        if r.edit["kind"] == "move":
+            R = r.edit["R"].astype(np.float64)
+            assert np.allclose(R @ R.T, np.eye(3), atol=1e-6) and abs(np.linalg.det(R) - 1) < 1e-6
+            assert 1 <= r.edit["object"] < sc.n_objects
+        assert r.cam.width in (256, 512, 800, 1024) and r.spp in (4, 8, 16, 32)
