@@ -354,23 +354,24 @@ def main():
         step.run()
     step.tr.sync()
 
-    # counted run (outside the timed region): traversal counters per phase
-    counters = {}
-    for ph in ["primary", "shade"]:
-        c = torch.zeros(4, dtype=torch.int64, device="cuda")
-        step.tr.set_counters(c)
-        if ph == "primary":
-            step.tr.trace_primary(cam, 0, out=step.gbuf)
-        else:
-            step.tr.shade(cam, step.gbuf, 0, args.spp, step.seed, out=step.rgb, samples=step.samples)
-        step.tr.sync()
-        counters[ph] = [int(v) for v in c.tolist()]
+    # counted run (outside the timed region): traversal counters per kernel slot
+    cnt16 = torch.zeros(16, dtype=torch.int64, device="cuda")
+    step.tr.set_counters(cnt16)
+    step.tr.trace_primary(cam, 0, out=step.gbuf)
+    step.tr.shade(cam, step.gbuf, 0, args.spp, step.seed, out=step.rgb, samples=step.samples)
+    step.tr.sync()
     step.tr.set_counters(None)
+    c = [int(v) for v in cnt16.tolist()]
+    counters = {name: c[4 * k:4 * k + 4] for k, name in
+                enumerate(["primary", "nee_shadow", "continuation", "secondary_shadow"])}
 
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
     step.rays.zero_()
     clocks = ClockSampler(local)
     per_step_ms, phase_ms = [], {n: [] for n in names}
+    kern_names = ["primary", "gen", "nee_shadow", "continuation", "secondary_shadow", "combine"]
+    kern_ms = {n: [] for n in kern_names}
+    step.tr.profile(True)  # CUDA events around the library's kernels, on its stream
     barrier()
     clocks.start()
     for k in range(args.steps):
@@ -382,8 +383,11 @@ def main():
         for n in names:
             phase_ms[n].append(events[n][0].elapsed_time(events[n][1]))
         per_step_ms.append(events["build"][0].elapsed_time(events["backward"][1]))
+        for n, v in zip(kern_names, step.tr.profile_read()):
+            kern_ms[n].append(v)
     barrier()
     clk = clocks.stop()
+    step.tr.profile(False)
     step.tr.sync()
     total_ms = sum(per_step_ms)
     shade_rays = int(step.rays.item())
@@ -401,18 +405,21 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    # ---------------------------------------------------------------- roofline of the dominant kernel group
+    # ---------------------------------------------------------------- roofline of the dominant kernel
     hbm, peak_kind = read_peaks()
     avg = {n: statistics.mean(v) for n, v in phase_ms.items()}
-    c = counters["shade"]
-    P = cam.width * cam.height
-    ns = P * args.spp
-    # algorithmic bytes of the shading pass: node visits (64 B), surfel tests (64 B packed record),
-    # composited hits (64 B record + 16 B material), per-sample buffer written and read once (28 floats + queues),
-    # G-buffer read (12 channels) and the image written.
-    shade_bytes = 64 * c[0] + 64 * c[1] + 80 * c[2] + ns * (28 * 4 * 2 + 16) + P * (12 * 4 + 12)
-    achieved = shade_bytes / (avg["shade"] * 1e-3) / 1e9
-    traffic = read_traffic()
+    kavg = {n: statistics.mean(v) for n, v in kern_ms.items()}
+    # algorithmic bytes per launch: node visits x 64 B, surfel tests x 64 B (packed record), composited
+    # hits x 80 B (record + material), plus each kernel's per-ray input and output
+    per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32}
+    kbytes = {n: 64 * counters[n][0] + 64 * counters[n][1] + 80 * counters[n][2] + per_ray_io[n] * counters[n][3]
+              for n in per_ray_io}
+    kernels = {n: {"ms": round(kavg[n], 3), "algorithmic_bytes": kbytes.get(n),
+                   "achieved_gbs": (kbytes[n] / (kavg[n] * 1e-3) / 1e9) if n in kbytes else None}
+               for n in kern_names}
+    dom = max(per_ray_io, key=lambda n: kavg[n])
+    achieved = kbytes[dom] / (kavg[dom] * 1e-3) / 1e9
+    traffic = read_traffic(KERNEL_NAMES[dom])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -421,12 +428,11 @@ def main():
         "fwd_mrays_s": fwd_value,
         "rays_per_step": rays_all / args.steps / world,
         "phase_ms": {n: round(v, 3) for n, v in avg.items()},
-        "roofline": {"bound": "hbm", "kernel": "shading wavefront (gen, shadow, continuation, combine)",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_kind": f"{peak_kind} HBM copy", "traffic": traffic,
-                     "algorithmic_bytes_per_launch": shade_bytes},
-        "counters": {"primary": counters["primary"], "shade": counters["shade"],
-                     "fields": ["node visits", "surfel tests", "composited hits", "rays"]},
+        "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy (burst)", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": kbytes[dom], "launch_ms": kavg[dom]},
+        "kernels": kernels,
+        "counters": dict(counters, fields=["node visits", "surfel tests", "composited hits", "rays"]),
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": args.steps * sum(KERNELS_PER_STEP.values()),
@@ -469,15 +475,20 @@ def reduce_over_ranks(total_ms, fwd_ms, rays, device):
     return float(t[0]), float(t[1]), float(r[0])
 
 
-def read_traffic():
-    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernels."""
+KERNEL_NAMES = {"primary": "k_trace_primary", "nee_shadow": "k_wf_shadow (NEE)",
+                "continuation": "k_wf_continue", "secondary_shadow": "k_wf_shadow (secondary)"}
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch of `kernel` at the bench workload, from the committed
+    ncu summary, when it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         if t.get("sources_sha") != sources_sha():
             return None
-        return t.get("shade_dram_bytes_per_launch")
+        return t.get("dram_bytes_per_launch", {}).get(kernel)
     except Exception:
         return None
 

@@ -261,11 +261,23 @@ lf_status lf_trace_backward(lf_ctx* ctx, const lf_camera* cam, const float* gbuf
                             size_t scratch_bytes);
 
 /*
- * Traversal counters for roofline accounting: when counters_dev (4 x uint64
- * on the device) is non-NULL, every trace kernel adds [node visits, surfel
- * tests, composited hits, rays] to it.  NULL turns counting off.
+ * Traversal counters for roofline accounting: when counters_dev (16 x uint64
+ * on the device) is non-NULL, the trace kernels ADD, per kernel slot k
+ * (0 primary rays, 1 NEE shadow rays, 2 continuation rays, 3 secondary
+ * shadow rays), [node visits, surfel tests, composited hits, rays] to
+ * counters_dev[4k .. 4k+3].  NULL turns counting off.
  */
 lf_status lf_set_counters(lf_ctx* ctx, unsigned long long* counters_dev);
+
+/*
+ * Per-kernel timing with CUDA events on the context's stream: while enabled,
+ * lf_trace_primary and lf_shade_bounce record events around their kernels;
+ * lf_profile_read waits for them and returns the milliseconds of the last
+ * calls' kernels: [primary, sample generation, NEE shadow rays, continuation
+ * rays, secondary shadow rays, combine].
+ */
+lf_status lf_profile(lf_ctx* ctx, int enable);
+lf_status lf_profile_read(lf_ctx* ctx, float* ms6);
 
 /* Philox4x32-10 of n counters (device n x 4 words) with key (k0, k1). */
 lf_status lf_philox(lf_ctx* ctx, const uint32_t* ctr_dev, int n, uint32_t k0, uint32_t k1, uint32_t* out_dev);

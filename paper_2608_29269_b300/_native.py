@@ -78,6 +78,8 @@ SIGNATURES = [
     ("lf_trace_backward", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P, _P, _P, _P,
                                     _P, C.c_size_t]),
     ("lf_set_counters", C.c_int, [_P, _P]),
+    ("lf_profile", C.c_int, [_P, C.c_int]),
+    ("lf_profile_read", C.c_int, [_P, C.POINTER(C.c_float)]),
     ("lf_philox", C.c_int, [_P, _P, C.c_int, C.c_uint32, C.c_uint32, _P]),
     ("lf_env_tables", C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     ("lf_bvh_info", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),

@@ -185,6 +185,8 @@ lf_status lf_destroy(lf_ctx* c) {
   dev_free(c->status_dev); dev_free(c->offsets_dev); dev_free(c->node_off_dev); dev_free(c->bounds);
   dev_free(c->insts_dev);
   for (EnvSlot& e : c->env) { dev_free(e.tables); dev_free(e.rowsum); dev_free(e.sin_row); }
+  for (cudaEvent_t& e : c->prof_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return LF_OK;
 }
@@ -207,6 +209,26 @@ lf_status lf_sync(lf_ctx* c) {
     return fail(c, (lf_status)st, st == LF_ERR_STACK ? "traversal stack overflow"
                                    : st == LF_ERR_ROUND_LIMIT ? "k-buffer round limit reached"
                                                               : "device error");
+  }
+  return LF_OK;
+}
+
+lf_status lf_profile(lf_ctx* c, int enable) {
+  if (!c) return LF_ERR_INVALID;
+  if (enable && !c->prof_ev[0])
+    for (cudaEvent_t& e : c->prof_ev) LF_CUDA(c, cudaEventCreate(&e));
+  c->profile = enable != 0;
+  return LF_OK;
+}
+
+lf_status lf_profile_read(lf_ctx* c, float* ms) {
+  if (!c || !ms) return LF_ERR_INVALID;
+  if (!c->prof_ev[0]) return fail(c, LF_ERR_NOT_BUILT, "profiling was never enabled");
+  // primary, gen, NEE shadow, continuation, secondary shadow, count + combine
+  const int a[6] = {0, 2, 3, 4, 5, 6}, b[6] = {1, 3, 4, 5, 6, 7};
+  for (int i = 0; i < 6; ++i) {
+    LF_CUDA(c, cudaEventSynchronize(c->prof_ev[b[i]]));
+    LF_CUDA(c, cudaEventElapsedTime(ms + i, c->prof_ev[a[i]], c->prof_ev[b[i]]));
   }
   return LF_OK;
 }
@@ -405,7 +427,9 @@ lf_status lf_trace_primary(lf_ctx* c, const lf_camera* cam, int env_id, float* g
   lf_status st = check_render(c, cam, env_id);
   if (st != LF_OK) return st;
   if (!gbuf) return fail(c, LF_ERR_INVALID, "null G-buffer");
+  if (c->profile) LF_CUDA(c, cudaEventRecord(c->prof_ev[0], c->stream));
   LF_CUDA(c, launch_trace_primary(lf_ctx_trace_args(c, env_id), to_cam(*cam), gbuf, c->stream));
+  if (c->profile) LF_CUDA(c, cudaEventRecord(c->prof_ev[1], c->stream));
   return LF_OK;
 }
 
@@ -448,8 +472,10 @@ lf_status lf_shade_bounce(lf_ctx* c, const lf_camera* cam, const float* gbuf, in
     return fail(c, LF_ERR_INVALID, "sample buffer too small");
   const ShadeBatch B = one_job(c, cam, gbuf, env_id, spp, seed, rgb);
   const SampleBuf S = sample_buf(samples, B.n_items);
-  LF_CUDA(c, launch_shade_wavefront(B, c->dp, S, c->status_dev, ray_count, c->counters, c->sms, c->stream));
+  LF_CUDA(c, launch_shade_wavefront(B, c->dp, S, c->status_dev, ray_count, c->counters, c->sms, c->stream,
+                                    c->profile ? c->prof_ev + 2 : nullptr));
   LF_CUDA(c, launch_shade_combine(B, c->dp, S, c->stream));
+  if (c->profile) LF_CUDA(c, cudaEventRecord(c->prof_ev[7], c->stream));
   return LF_OK;
 }
 

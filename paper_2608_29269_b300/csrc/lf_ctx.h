@@ -27,6 +27,8 @@ struct lf_ctx {
   int sms = 148;
   int* status_dev = nullptr;
   unsigned long long* counters = nullptr;
+  bool profile = false;
+  cudaEvent_t prof_ev[8] = {};  // primary | gen | NEE shadow | continuation | secondary shadow | combine
   std::string err;
   // scene (caller-owned arrays) and its object layout
   lf::SceneDev scene{};

@@ -13,6 +13,7 @@ __device__ __forceinline__ void load_instances(Inst* dst, const Inst* src, int n
   __syncthreads();
 }
 
+// Slot 0 of the per-kernel counters: primary rays.
 __device__ __forceinline__ void add_counters(unsigned long long* c, const Counters& k, unsigned comp, unsigned rays) {
   if (!c) return;
   atomicAdd(c + 0, (unsigned long long)k.nodes);

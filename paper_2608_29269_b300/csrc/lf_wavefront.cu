@@ -198,9 +198,11 @@ __global__ void __launch_bounds__(WB) k_wf_shadow(ShadeBatch B, DevParams P, Sam
       else S.Vq0[item] = V;
     }
   }
-  if (counters) {
-    atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
-    atomicAdd(counters + 1, (unsigned long long)cnt.tests);
+  if (counters) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
+    unsigned long long* c = counters + 4 * (which == 0 ? 1 : 3);
+    atomicAdd(c + 0, (unsigned long long)cnt.nodes);
+    atomicAdd(c + 1, (unsigned long long)cnt.tests);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(c + 3, (unsigned long long)n);
   }
 }
 
@@ -262,10 +264,11 @@ __global__ void __launch_bounds__(WB) k_wf_continue(ShadeBatch B, DevParams P, S
     queue_push(S.qC, S.counts + 2, (int)(item * 2), push0);
     queue_push(S.qC, S.counts + 2, (int)(item * 2 + 1), push1);
   }
-  if (counters) {
-    atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
-    atomicAdd(counters + 1, (unsigned long long)cnt.tests);
-    atomicAdd(counters + 2, (unsigned long long)comp);
+  if (counters) {  // slot 2: continuation rays
+    atomicAdd(counters + 8, (unsigned long long)cnt.nodes);
+    atomicAdd(counters + 9, (unsigned long long)cnt.tests);
+    atomicAdd(counters + 10, (unsigned long long)comp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(counters + 11, (unsigned long long)n);
   }
 }
 
@@ -458,16 +461,23 @@ static int wf_grid(long long n, int sms) {
 
 cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, int* status,
                                    unsigned long long* ray_count, unsigned long long* counters, int sms,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, cudaEvent_t* ev) {
   if (B.n_items <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(S.counts, 0, 4 * sizeof(int), st);
   if (e != cudaSuccess) return e;
+  // ev (nullable): 5 events bracketing gen | NEE shadow | continuation | secondary shadow
+  auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
+  mark(0);
   k_wf_gen<<<wf_grid(B.n_items, sms), WB, 0, st>>>(B, P, S);
+  mark(1);
   // queue lengths are known only on the device: the trace kernels size
   // their loops from the counters (grids cover the worst case).
   k_wf_shadow<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
+  mark(2);
   k_wf_continue<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
+  mark(3);
   k_wf_shadow<<<wf_grid(2 * B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 1, status, counters);
+  mark(4);
   k_wf_count<<<1, 32, 0, st>>>(S.counts, ray_count);
   return cudaGetLastError();
 }

@@ -57,7 +57,7 @@ size_t sample_buf_bytes(long long n_items);
 SampleBuf sample_buf(void* base, long long n_items);
 cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, int* status,
                                    unsigned long long* ray_count, unsigned long long* counters, int sms,
-                                   cudaStream_t st);
+                                   cudaStream_t st, cudaEvent_t* ev = nullptr);
 cudaError_t launch_shade_combine(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, cudaStream_t st);
 cudaError_t launch_shade_combine_adjoint(const ShadeBatch& B, const DevParams& P, const SampleBuf& S,
                                          const float* dL_drgb, float* sg, float* d_env, cudaStream_t st);

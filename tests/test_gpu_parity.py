@@ -213,3 +213,37 @@ def test_c3_gradient_parity():
 
 
 FLAG_GRAD = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6, cap=1e-5)
+
+
+def test_counters_and_kernel_timing_are_consistent():
+    """Per-kernel counter slots add up to the rays the shading reports, and
+    the per-kernel event timings are positive and inside the call's span."""
+    import torch
+    sc, cam, env = _c1_inputs()
+    tr, _ = gpu_tracer(sc, [env])
+    cnt = torch.zeros(16, dtype=torch.int64, device="cuda")
+    rays = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        tr.set_counters(torch.zeros(4, dtype=torch.int64, device="cuda"))
+    tr.set_counters(cnt)
+    tr.profile(True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tr.sync()
+    t0.record()
+    g = tr.trace_primary(cam, 0)
+    tr.shade(cam, g, 0, spp=4, seed=5, ray_count=rays)
+    tr.sync()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = tr.profile_read()
+    tr.profile(False)
+    tr.set_counters(None)
+    c = cnt.cpu().numpy().reshape(4, 4)
+    assert c[0, 3] == cam.width * cam.height
+    assert c[1, 3] + c[2, 3] + c[3, 3] == int(rays.item())
+    for k in range(4):
+        if c[k, 3] > 0:
+            assert c[k, 0] > 0 and c[k, 1] > 0
+    assert c[0, 2] > 0 and c[2, 2] >= 0 and c[1, 2] == 0 and c[3, 2] == 0
+    assert len(ms) == 6 and all(v > 0 for v in ms)
+    assert sum(ms) <= t0.elapsed_time(t1) * 1.05 + 0.05
