@@ -319,6 +319,11 @@ def run_serve_sweep(args):
     print(json.dumps(line))
 
 
+def stage(msg):
+    """Progress of the run on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def main():
     args = parse()
     if args.serve:
@@ -341,6 +346,7 @@ def main():
         build()
     if world > 1:
         dist.barrier()
+    stage("workload")
     sc, cam, env = make_workload(args.size, args.spp, 0)
     step = Step(sc, cam, env, args.spp, seed=1234 + rank)
     names = ["build", "primary", "shade", "backward"]
@@ -350,9 +356,11 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    stage("warm-up")
     for _ in range(args.warmup):
         step.run()
     step.tr.sync()
+    stage("counted run")
 
     # counted run (outside the timed region): traversal counters per kernel slot
     cnt16 = torch.zeros(16, dtype=torch.int64, device="cuda")
@@ -365,6 +373,7 @@ def main():
     counters = {name: c[4 * k:4 * k + 4] for k, name in
                 enumerate(["primary", "nee_shadow", "continuation", "secondary_shadow"])}
 
+    stage("timed steps")
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
     step.rays.zero_()
     clocks = ClockSampler(local)
@@ -398,6 +407,7 @@ def main():
     fwd_value = rays_all / (fwd_ms * 1e-3) / 1e6
 
     # ---------------------------------------------------------------- e2e through the public API
+    stage("end to end")
     e2e = e2e_run(step, sc, env, args, world)
 
     if rank != 0:
@@ -438,6 +448,7 @@ def main():
         "gpu_launches": args.steps * sum(KERNELS_PER_STEP.values()),
     }
     if not args.no_serving:
+        stage("serving comparison")
         try:
             from synthetic import scenes as S
             line["serving"] = dict(serving_compare(sc, [env, S.env_sky_sun(1), S.env_sky_sun(2)], 24, 4.0,
@@ -446,6 +457,7 @@ def main():
         except Exception as exc:
             line["serving"] = {"error": str(exc)}
     if not args.no_cpu_baseline:
+        stage("cpu baseline")
         try:
             import oracle
             oracle.build()

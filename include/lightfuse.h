@@ -335,7 +335,11 @@ typedef struct lf_serve lf_serve;
  * the requests in flight; n_streams is the stream pool the launch groups
  * rotate over; batch_window_us is how long the oldest pending request may
  * wait for others to join its launch group while slots are free (0: admit
- * at once).  Frames are at most 1024 x 1024. */
+ * at once).  Frames are at most 1024 x 1024.
+ * Each finished request keeps its pinned host frame until lf_serve_poll
+ * returns it; the server owns 2 * max_slots frames, so a client must poll
+ * finished requests for admission to go on (waiting on a later ticket while
+ * 2 * max_slots finished ones stay unpolled ends in LF_ERR_TIMEOUT). */
 lf_status lf_serve_create(lf_ctx* ctx, size_t mem_budget_bytes, int max_slots, int n_streams, int batch_window_us,
                           lf_serve** out);
 /* Enqueue a request (host copy); returns its ticket.  Never blocks. */

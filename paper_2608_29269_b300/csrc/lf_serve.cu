@@ -430,9 +430,16 @@ void worker_main(lf_serve* s) {
       }
       continue;
     }
-    // nothing to launch: wait for a submission or poll in-flight work
-    if (s->groups.empty()) s->cv_work.wait(lock, [&] { return s->stop || !s->pending.empty(); });
-    else s->cv_work.wait_for(lock, std::chrono::microseconds(50));
+    // nothing to launch: sleep until a request can be admitted (a submission,
+    // or a frame handed back by lf_serve_poll), or poll in-flight work.  The
+    // predicate must not hold while admission is blocked, or the loop would
+    // spin with the lock held and starve lf_serve_poll.
+    if (s->groups.empty())
+      s->cv_work.wait(lock, [&] {
+        return s->stop || (!s->pending.empty() && s->in_flight < s->max_slots && !s->frame_pool.empty());
+      });
+    else
+      s->cv_work.wait_for(lock, std::chrono::microseconds(50));
   }
 }
 

@@ -26,6 +26,16 @@ namespace lf {
 
 constexpr int WB = 128;  // threads per block of the wavefront kernels
 constexpr int WSTACK_SMEM = WB * STACK * (int)sizeof(int);
+// Minimum resident blocks per SM asked of the compiler (caps registers).
+#ifndef WF_MIN_BLOCKS_SHADOW
+#define WF_MIN_BLOCKS_SHADOW 1
+#endif
+#ifndef WF_MIN_BLOCKS_CONTINUE
+#define WF_MIN_BLOCKS_CONTINUE 4
+#endif
+// Slots of SampleBuf::counts: queue lengths A, B, C (0-2); fetch cursors of
+// the three trace kernels (4-6).
+constexpr int CURSOR_A = 4, CURSOR_B = 5, CURSOR_C = 6, N_COUNTS = 8;
 
 __device__ __forceinline__ int job_of_item(const ShadeBatch& B, long long item) {
   int lo = 0, hi = B.n_jobs - 1;
@@ -152,51 +162,47 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
   }
 }
 
+// ---------------------------------------------------------------- ray fetch
+// The trace kernels run a persistent grid (as many blocks as fit on the GPU)
+// and hand rays out to whole warps through a per-kernel cursor: a warp that
+// has finished its 32 rays takes the next 32 without waiting for the other
+// warps of its block.  No block barrier sits in the ray loop.
+__device__ __forceinline__ int warp_fetch(int* cursor) {
+  int base = 0;
+  if ((threadIdx.x & 31) == 0) base = atomicAdd(cursor, 32);
+  return __shfl_sync(0xffffffffu, base, 0);
+}
+
 // ---------------------------------------------------------------- shadow rays
 // which = 0: NEE rays of queue A (origin from the G-buffer, direction we)
 // which = 1: secondary NEE rays of queue C (entry = item * 2 + q)
-__global__ void __launch_bounds__(WB) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S, int which, int* status,
-                                                  unsigned long long* counters) {
-  __shared__ Inst s_inst[LF_MAX_OBJECTS];
-  __shared__ int s_job;
+__global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S,
+                                                                        int which, int* status,
+                                                                        unsigned long long* counters) {
   extern __shared__ int s_stack[];
   const int* q = which == 0 ? S.qA : S.qC;
   const int n = which == 0 ? S.counts[0] : S.counts[2];
+  int* cursor = S.counts + (which == 0 ? CURSOR_A : CURSOR_C);
   Counters cnt;
-  // Jobs of a batch may have different scenes: blocks reload the instance
-  // table when the job of their first entry changes.
-  int loaded = -1;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const int k = base + threadIdx.x;
-    const int e = k < n ? q[k] : q[base];
+  for (int base = warp_fetch(cursor); base < n; base = warp_fetch(cursor)) {
+    const int k = base + (threadIdx.x & 31);
+    if (k >= n) continue;
+    const int e = q[k];
     const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
-    const int j = job_of_item(B, item);
-    __syncthreads();
-    if (threadIdx.x == 0) s_job = j;
-    __syncthreads();
-    const int bj = s_job;
-    if (bj != loaded) {
-      load_insts(s_inst, B.jobs[bj].insts, B.jobs[bj].n_inst);
-      loaded = bj;
+    const ShadeJob& J = B.jobs[job_of_item(B, item)];
+    float3 o, d;
+    if (which == 0) {
+      const long long loc = item - J.item0;
+      o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+      d = ld3(S.we, item);
+    } else {
+      o = ld3(S.xs2, item);
+      d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
     }
-    __syncthreads();
-    if (k < n) {
-      const ShadeJob& J = B.jobs[j];
-      const Inst* insts = (j == bj) ? s_inst : J.insts;
-      float3 o, d;
-      if (which == 0) {
-        const long long loc = item - J.item0;
-        o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
-        d = ld3(S.we, item);
-      } else {
-        o = ld3(S.xs2, item);
-        d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
-      }
-      const float V = trace_shadow(insts, J.n_inst, o, d, P, s_stack + threadIdx.x, WB, status, cnt);
-      if (which == 0) S.Ve[item] = V;
-      else if (e & 1) S.Vq1[item] = V;
-      else S.Vq0[item] = V;
-    }
+    const float V = trace_shadow(J.insts, J.n_inst, o, d, P, s_stack + threadIdx.x, WB, status, cnt);
+    if (which == 0) S.Ve[item] = V;
+    else if (e & 1) S.Vq1[item] = V;
+    else S.Vq0[item] = V;
   }
   if (counters) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
     unsigned long long* c = counters + 4 * (which == 0 ? 1 : 3);
@@ -207,38 +213,25 @@ __global__ void __launch_bounds__(WB) k_wf_shadow(ShadeBatch B, DevParams P, Sam
 }
 
 // ---------------------------------------------------------------- continuation rays
-__global__ void __launch_bounds__(WB) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S, int* status,
-                                                    unsigned long long* counters) {
-  __shared__ Inst s_inst[LF_MAX_OBJECTS];
-  __shared__ int s_job;
+__global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S,
+                                                                            int* status,
+                                                                            unsigned long long* counters) {
   extern __shared__ int s_stack[];
   const int n = S.counts[1];
   Counters cnt;
   unsigned comp = 0;
-  int loaded = -1;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const int k = base + threadIdx.x;
-    const long long item = (long long)(k < n ? S.qB[k] : S.qB[base]);
-    const int j = job_of_item(B, item);
-    __syncthreads();
-    if (threadIdx.x == 0) s_job = j;
-    __syncthreads();
-    const int bj = s_job;
-    if (bj != loaded) {
-      load_insts(s_inst, B.jobs[bj].insts, B.jobs[bj].n_inst);
-      loaded = bj;
-    }
-    __syncthreads();
+  for (int base = warp_fetch(S.counts + CURSOR_B); base < n; base = warp_fetch(S.counts + CURSOR_B)) {
+    const int k = base + (threadIdx.x & 31);
+    const long long item = k < n ? (long long)S.qB[k] : 0;
     bool push0 = false, push1 = false;
     if (k < n) {
-      const ShadeJob& J = B.jobs[j];
-      const Inst* insts = (j == bj) ? s_inst : J.insts;
+      const ShadeJob& J = B.jobs[job_of_item(B, item)];
       const long long loc = item - J.item0;
       const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
       const float3 xs = pix_origin(J, p, P.ray_offset);
       const float3 wi = ld3(S.wi, item);
       Surface s2;
-      trace_composite(insts, J.n_inst, xs, wi, P, s_stack + threadIdx.x, WB, status, cnt, s2, comp);
+      trace_composite(J.insts, J.n_inst, xs, wi, P, s_stack + threadIdx.x, WB, status, cnt, s2, comp);
       S.T2[item] = s2.T;
       if (s2.hits > 0) {
         const float3 n2 = s2.n, wo2 = -wi;
@@ -459,11 +452,22 @@ static int wf_grid(long long n, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sms * 16));
 }
 
+// Persistent grid of a trace kernel: the blocks that fit on the GPU at once,
+// no more than the work needs.
+template <class K>
+static int resident_grid(K kernel, long long n, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WB, WSTACK_SMEM) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long blocks = (n + WB - 1) / WB;
+  return (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sms * per_sm));
+}
+
 cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, int* status,
                                    unsigned long long* ray_count, unsigned long long* counters, int sms,
                                    cudaStream_t st, cudaEvent_t* ev) {
   if (B.n_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(S.counts, 0, 4 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(S.counts, 0, N_COUNTS * sizeof(int), st);
   if (e != cudaSuccess) return e;
   // ev (nullable): 5 events bracketing gen | NEE shadow | continuation | secondary shadow
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
@@ -472,11 +476,12 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
   mark(1);
   // queue lengths are known only on the device: the trace kernels size
   // their loops from the counters (grids cover the worst case).
-  k_wf_shadow<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
+  k_wf_shadow<<<resident_grid(k_wf_shadow, B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
   mark(2);
-  k_wf_continue<<<wf_grid(B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
+  k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
   mark(3);
-  k_wf_shadow<<<wf_grid(2 * B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 1, status, counters);
+  k_wf_shadow<<<resident_grid(k_wf_shadow, 2 * B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 1, status,
+                                                                                          counters);
   mark(4);
   k_wf_count<<<1, 32, 0, st>>>(S.counts, ray_count);
   return cudaGetLastError();

@@ -91,8 +91,9 @@ class Server:
             pass
 
 
-def run_served(server: Server, requests, keep_frames: bool = False):
-    """Submit at the requests' arrival times; returns per-request records."""
+def run_served(server: Server, requests, keep_frames: bool = False, timeout_ms: int = 120_000):
+    """Submit at the requests' arrival times; returns per-request records
+    (status LF_ERR_TIMEOUT for a request not finished within timeout_ms)."""
     t0 = time.perf_counter()
     tickets: List[int] = [0] * len(requests)
 
@@ -108,7 +109,9 @@ def run_served(server: Server, requests, keep_frames: bool = False):
     th.join()
     out = []
     for i, rq in enumerate(requests):
-        server.wait(tickets[i])
+        if server.wait(tickets[i], timeout_ms) != N.LF_OK:
+            out.append(dict(status=N.LF_ERR_TIMEOUT, frame=None, latency=float("nan")))
+            continue
         st, frame, tm = server.result(tickets[i], rq.cam, want_frame=keep_frames)
         out.append(dict(status=st, frame=frame, latency=tm["t_done"] - tm["t_submit"], **tm))
     return out

@@ -77,3 +77,23 @@ def test_admission_budget_and_malformed_requests():
         stt, frame, tm = srv.result(k, cam)
         assert stt == N.LF_OK and frame is not None
     srv.close()
+
+
+def test_more_finished_requests_than_frames_keep_admission_going():
+    """Every request of a burst larger than the pinned frame pool (2 x
+    max_slots) completes when the client polls in order: the worker sleeps
+    while the pool is empty and wakes when a poll hands a frame back."""
+    import time
+    from paper_2608_29269_b300 import _native as N
+    from paper_2608_29269_b300.serve import Server
+    sc, tr, st = _setup()
+    cam = S.Camera((0.0, -0.5, 1.8), (0.0, -1.5, 0.0), (0.0, 1.0, 0.0), 60.0, 32, 32)
+    srv = Server(tr, budget_bytes=1 << 30, max_slots=2, n_streams=2)  # 4 frames
+    ts = [srv.submit(None, cam, 2, k) for k in range(11)]
+    t0 = time.perf_counter()
+    for k in ts:
+        assert srv.wait(k, 30_000) == N.LF_OK
+        stt, frame, _ = srv.result(k, cam)
+        assert stt == N.LF_OK and frame is not None and np.isfinite(frame).all()
+    assert time.perf_counter() - t0 < 30.0
+    srv.close()
