@@ -490,12 +490,22 @@ __device__ __forceinline__ int entry_of(int ii, int child) {
 // lanes of the warp process their leaves together.  The visitor supplies the
 // culling interval [tlo(), thi()], consumes leaves and may end the ray early.
 // `stack` points at this thread's first entry; entries are `stride` ints apart.
+//
+// The walk is resumable: trav_begin sets up a ray, each trav_step runs one
+// descent to a leaf plus that leaf's test, so a kernel can interleave rays of
+// different ages on the lanes of a warp (refilling lanes whose ray ended).
+struct TravState {
+  int sp;      // stack depth
+  int ent;     // entry to process next; < 0: none
+  int budget;  // node visits left (guards against a malformed tree)
+};
+
 template <class V>
-__device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
-                                         int stride, int* status, Counters& cnt) {
+__device__ __forceinline__ void trav_begin(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
+                                           int stride, int* status, TravState& st) {
   int sp = 0;
   // A tree of n leaves has n - 1 internal nodes; a depth-first walk visits
-  // each node at most once.  The budget only guards against a malformed tree.
+  // each node at most once.
   int budget = 8;
   for (int ii = 0; ii < n_inst; ++ii) {  // instance 0 (background) is pushed first, popped last
     const Inst& I = insts[ii];
@@ -505,52 +515,76 @@ __device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ra
     if (sp >= STACK) {
       report(status, LF_ERR_STACK);
       vis.abort();
+      st.sp = 0;
+      st.ent = -1;
+      st.budget = 0;
       return;
     }
     stack[(sp++) * stride] = entry_of(ii, I.root);
     budget += 2 * I.n_leaves + 2;
   }
-  int e = sp > 0 ? stack[(--sp) * stride] : -1;
-  bool ok = true;
-  while (e >= 0) {
-    while (e >= 0 && !(e & LEAF_BIT)) {
-      if (--budget < 0 || sp >= STACK) {
-        ok = false;
-        e = -1;
-        break;
-      }
-      ++cnt.nodes;
-      const int ii = e >> 25;
-      const float4* N = insts[ii].nodes + 4 * (e & 0xffffff);
-      const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), f = __ldg(N + 3);
-      const float lo = vis.tlo(), hi = vis.thi();
-      float tl, tr;
-      const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
-      const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
-      const int cl = entry_of(ii, __float_as_int(f.x)), cr = entry_of(ii, __float_as_int(f.y));
-      if (hl && hr) {
-        const bool lfirst = tl <= tr;
-        stack[(sp++) * stride] = lfirst ? cr : cl;
-        e = lfirst ? cl : cr;
-      } else if (hl) {
-        e = cl;
-      } else if (hr) {
-        e = cr;
-      } else {
-        e = sp > 0 ? stack[(--sp) * stride] : -1;
-      }
+  st.ent = sp > 0 ? stack[(--sp) * stride] : -1;
+  st.sp = sp;
+  st.budget = budget;
+}
+
+// One descent to the next leaf and its test.  Returns false once the ray has
+// nothing left to visit (or the visitor ended it, or the walk failed).
+template <class V>
+__device__ __forceinline__ bool trav_step(const Inst* insts, const Ray& ray, V& vis, int* stack, int stride,
+                                          int* status, Counters& cnt, TravState& st) {
+  int e = st.ent, sp = st.sp, budget = st.budget;
+  while (e >= 0 && !(e & LEAF_BIT)) {
+    if (--budget < 0 || sp >= STACK) {
+      report(status, LF_ERR_STACK);
+      vis.abort();
+      st.ent = -1;
+      return false;
     }
-    if (e >= 0) {
-      ++cnt.tests;
-      const int ii = e >> 25;
-      vis.leaf(ii, e & 0xffffff, insts[ii]);
-      if (vis.done()) return;
+    ++cnt.nodes;
+    const int ii = e >> 25;
+    const float4* N = insts[ii].nodes + 4 * (e & 0xffffff);
+    const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), f = __ldg(N + 3);
+    const float lo = vis.tlo(), hi = vis.thi();
+    float tl, tr;
+    const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
+    const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
+    const int cl = entry_of(ii, __float_as_int(f.x)), cr = entry_of(ii, __float_as_int(f.y));
+    if (hl && hr) {
+      const bool lfirst = tl <= tr;
+      stack[(sp++) * stride] = lfirst ? cr : cl;
+      e = lfirst ? cl : cr;
+    } else if (hl) {
+      e = cl;
+    } else if (hr) {
+      e = cr;
+    } else {
       e = sp > 0 ? stack[(--sp) * stride] : -1;
     }
   }
-  if (!ok) {
-    report(status, LF_ERR_STACK);
-    vis.abort();
+  if (e < 0) {
+    st.ent = -1;
+    return false;
+  }
+  ++cnt.tests;
+  const int ii = e >> 25;
+  vis.leaf(ii, e & 0xffffff, insts[ii]);
+  if (vis.done()) {
+    st.ent = -1;
+    return false;
+  }
+  st.ent = sp > 0 ? stack[(--sp) * stride] : -1;
+  st.sp = sp;
+  st.budget = budget;
+  return st.ent >= 0;
+}
+
+template <class V>
+__device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
+                                         int stride, int* status, Counters& cnt) {
+  TravState st;
+  trav_begin(insts, n_inst, ray, vis, stack, stride, status, st);
+  while (trav_step(insts, ray, vis, stack, stride, status, cnt, st)) {
   }
 }
 

@@ -176,33 +176,68 @@ __device__ __forceinline__ int warp_fetch(int* cursor) {
 // ---------------------------------------------------------------- shadow rays
 // which = 0: NEE rays of queue A (origin from the G-buffer, direction we)
 // which = 1: secondary NEE rays of queue C (entry = item * 2 + q)
+//
+// Rays of one warp differ widely in length, so a lane whose ray has ended
+// takes a new one: after each descent-and-leaf step the warp counts its idle
+// lanes and, once at least SHADOW_REFILL of them are idle, fetches that many
+// queue entries with one atomic and starts them.  A shadow ray's start and
+// end are cheap (two plane loads, one store), so refilling costs little.
+#ifndef SHADOW_REFILL
+#define SHADOW_REFILL 8
+#endif
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S,
                                                                         int which, int* status,
                                                                         unsigned long long* counters) {
   extern __shared__ int s_stack[];
+  int* stack = s_stack + threadIdx.x;
   const int* q = which == 0 ? S.qA : S.qC;
   const int n = which == 0 ? S.counts[0] : S.counts[2];
   int* cursor = S.counts + (which == 0 ? CURSOR_A : CURSOR_C);
+  const unsigned lane_lt = (1u << (threadIdx.x & 31)) - 1u;
   Counters cnt;
-  for (int base = warp_fetch(cursor); base < n; base = warp_fetch(cursor)) {
-    const int k = base + (threadIdx.x & 31);
-    if (k >= n) continue;
-    const int e = q[k];
-    const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
-    const ShadeJob& J = B.jobs[job_of_item(B, item)];
-    float3 o, d;
-    if (which == 0) {
-      const long long loc = item - J.item0;
-      o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
-      d = ld3(S.we, item);
-    } else {
-      o = ld3(S.xs2, item);
-      d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
+  bool live = false, drained = false;
+  int e = 0;
+  const Inst* insts = nullptr;
+  ShadowV v;
+  v.P = P;
+  Ray ray;
+  TravState ts;
+  while (true) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !live);
+    if (drained && idle == 0xffffffffu) break;
+    if (!drained && __popc(idle) >= SHADOW_REFILL) {
+      int base = 0;
+      if (lane_lt == 0u) base = atomicAdd(cursor, __popc(idle));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      drained = base + __popc(idle) >= n;
+      const int k = base + __popc(idle & lane_lt);
+      if (!live && k < n) {
+        e = q[k];
+        const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+        const ShadeJob& J = B.jobs[job_of_item(B, item)];
+        if (which == 0) {
+          const long long loc = item - J.item0;
+          v.o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+          v.d = ld3(S.we, item);
+        } else {
+          v.o = ld3(S.xs2, item);
+          v.d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
+        }
+        v.V = 1.0f;
+        v.stop = false;
+        ray = make_ray(v.o, v.d);
+        insts = J.insts;
+        trav_begin(insts, J.n_inst, ray, v, stack, WB, status, ts);
+        live = true;
+      }
     }
-    const float V = trace_shadow(J.insts, J.n_inst, o, d, P, s_stack + threadIdx.x, WB, status, cnt);
-    if (which == 0) S.Ve[item] = V;
-    else if (e & 1) S.Vq1[item] = V;
-    else S.Vq0[item] = V;
+    if (live && !trav_step(insts, ray, v, stack, WB, status, cnt, ts)) {
+      const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+      if (which == 0) S.Ve[item] = v.V;
+      else if (e & 1) S.Vq1[item] = v.V;
+      else S.Vq0[item] = v.V;
+      live = false;
+    }
   }
   if (counters) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
     unsigned long long* c = counters + 4 * (which == 0 ? 1 : 3);
