@@ -273,8 +273,13 @@ def serving_compare(sc, envs, n_req, rate, resolutions, spps, seed, budget=40 <<
     srv.close()
     lat = np.array([r["latency"] for r in served if r["status"] == 0]) * 1e3
     # rays per request: shading rays of its launch group are shared; estimate from the plain loop's counts below
+    ok = [r for r in served if r["status"] == 0]
+    phases = {name: [1e3 * (r[b] - r[a]) for r in ok] for name, a, b in
+              [("queue", "t_submit", "t_admit"), ("admit", "t_admit", "t_start"), ("gpu", "t_start", "t_done")]}
     out["served"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "completed": int(len(lat)), "failed": int(len(served) - len(lat)), "wall_s": wall}
+                     "completed": int(len(lat)), "failed": int(len(served) - len(lat)), "wall_s": wall,
+                     "mean_ms": {k: float(np.mean(v)) for k, v in phases.items()},
+                     "max_ms": {k: float(np.max(v)) for k, v in phases.items()}}
     rays = torch.zeros(1, dtype=torch.int64, device="cuda")
     run_plain(tr, warm)  # after the server is closed: the plain loop edits the context's own scene
     t0 = time.perf_counter()

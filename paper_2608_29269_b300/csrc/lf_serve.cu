@@ -107,6 +107,10 @@ struct lf_serve {
   int next_stream = 0;
   cudaStream_t edit_stream = nullptr;
   cudaEvent_t edit_event = nullptr;
+  // Stream-ordered allocations come from this server's own pool, which keeps
+  // up to the budget mapped between requests (the device's default pool
+  // would return its memory at every synchronisation).
+  cudaMemPool_t pool = nullptr;
   std::vector<Version*> current;               // current version per object
   std::vector<std::unique_ptr<Version>> versions;
   std::vector<float*> frame_pool;              // pinned host frames
@@ -127,8 +131,8 @@ struct lf_serve {
 
 namespace {
 
-cudaError_t alloc_async(char** p, size_t bytes, cudaStream_t st) {
-  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes ? bytes : 256, st);
+cudaError_t alloc_async(lf_serve* s, char** p, size_t bytes, cudaStream_t st) {
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes ? bytes : 256, s->pool, st);
 }
 
 size_t frame_bytes_of(const lf_camera& c, int spp) {
@@ -153,7 +157,7 @@ lf_status make_version(lf_serve* s, const lf_edit& e, Version** out) {
   v->n = cur->n;
   const int n = v->n;
   v->bytes = version_bytes(n);
-  if (alloc_async(&v->block, v->bytes, s->edit_stream) != cudaSuccess) return LF_ERR_OOM;
+  if (alloc_async(s, &v->block, v->bytes, s->edit_stream) != cudaSuccess) return LF_ERR_OOM;
   char* p = v->block;
   auto take = [&](size_t b) { char* r = p; p += (b + 255) / 256 * 256; return r; };
   v->raw = reinterpret_cast<float*>(take(sizeof(float) * RAW_FLOATS * n));
@@ -264,7 +268,7 @@ lf_status admit(lf_serve* s, Job* j) {
   const size_t b_insts = (sizeof(Inst) * LF_MAX_OBJECTS + 255) / 256 * 256;
   const size_t b_gbuf = (sizeof(float) * LF_GBUF_CHANNELS * P + 255) / 256 * 256;
   const size_t b_rgb = (sizeof(float) * 3 * P + 255) / 256 * 256;
-  if (alloc_async(&j->block, b_insts + b_gbuf + b_rgb, s->edit_stream) != cudaSuccess) return LF_ERR_OOM;
+  if (alloc_async(s, &j->block, b_insts + b_gbuf + b_rgb, s->edit_stream) != cudaSuccess) return LF_ERR_OOM;
   j->insts = reinterpret_cast<Inst*>(j->block);
   j->gbuf = reinterpret_cast<float*>(j->block + b_insts);
   j->rgb = reinterpret_cast<float*>(j->block + b_insts + b_gbuf);
@@ -310,7 +314,7 @@ lf_status launch_group(lf_serve* s, Group* g) {
     B.n_items += (long long)J.n_pix * J.spp;
     B.n_pix_total += J.n_pix;
   }
-  if (alloc_async(&g->samples, sample_buf_bytes(B.n_items) + 256, g->stream) != cudaSuccess) return LF_ERR_OOM;
+  if (alloc_async(s, &g->samples, sample_buf_bytes(B.n_items) + 256, g->stream) != cudaSuccess) return LF_ERR_OOM;
   g->rays_dev = reinterpret_cast<unsigned long long*>(g->samples + sample_buf_bytes(B.n_items));
   if (cudaMemsetAsync(g->rays_dev, 0, sizeof(unsigned long long), g->stream) != cudaSuccess) return LF_ERR_CUDA;
   const SampleBuf S = sample_buf(g->samples, B.n_items);
@@ -491,6 +495,16 @@ lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams
   s->max_slots = max_slots;
   s->window_s = 1e-6 * batch_window_us;
   s->env_id = env0;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = c->device;
+  if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) return LF_ERR_CUDA;
+  uint64_t keep = budget;
+  if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+    cudaMemPoolDestroy(s->pool);
+    return LF_ERR_CUDA;
+  }
   if (cudaStreamCreateWithFlags(&s->edit_stream, cudaStreamNonBlocking) != cudaSuccess) return LF_ERR_CUDA;
   if (cudaEventCreateWithFlags(&s->edit_event, cudaEventDisableTiming) != cudaSuccess) return LF_ERR_CUDA;
   for (int i = 0; i < n_streams; ++i) {
@@ -605,6 +619,7 @@ lf_status lf_serve_destroy(lf_serve* s) {
   cudaFreeHost(s->ray_slots);
   cudaEventDestroy(s->edit_event);
   cudaStreamDestroy(s->edit_stream);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
   return LF_OK;
 }

@@ -4,9 +4,10 @@ library (scheduler thread, edits, batched kernels)."""
 from __future__ import annotations
 
 import ctypes as C
+import queue
 import threading
 import time
-from typing import List, Optional
+from typing import Optional
 
 import numpy as np
 import torch
@@ -92,28 +93,38 @@ class Server:
 
 
 def run_served(server: Server, requests, keep_frames: bool = False, timeout_ms: int = 120_000):
-    """Submit at the requests' arrival times; returns per-request records
-    (status LF_ERR_TIMEOUT for a request not finished within timeout_ms)."""
+    """Submit at the requests' arrival times from one thread while this thread
+    collects results as they finish (a finished request holds one of the
+    server's pinned frames until it is collected).  Returns per-request
+    records; status LF_ERR_TIMEOUT for one not finished within timeout_ms."""
     t0 = time.perf_counter()
-    tickets: List[int] = [0] * len(requests)
+    submitted: "queue.Queue" = queue.Queue()
 
     def submitter():
         for i, rq in enumerate(requests):
             delay = t0 + rq.arrival - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets[i] = server.submit(rq.edit, rq.cam, rq.spp, rq.seed)
+            try:
+                submitted.put(server.submit(rq.edit, rq.cam, rq.spp, rq.seed))
+            except Exception as exc:  # hand the failure to the collector
+                submitted.put(exc)
 
     th = threading.Thread(target=submitter)
     th.start()
-    th.join()
     out = []
-    for i, rq in enumerate(requests):
-        if server.wait(tickets[i], timeout_ms) != N.LF_OK:
-            out.append(dict(status=N.LF_ERR_TIMEOUT, frame=None, latency=float("nan")))
-            continue
-        st, frame, tm = server.result(tickets[i], rq.cam, want_frame=keep_frames)
-        out.append(dict(status=st, frame=frame, latency=tm["t_done"] - tm["t_submit"], **tm))
+    try:
+        for rq in requests:
+            ticket = submitted.get()
+            if isinstance(ticket, Exception):
+                raise ticket
+            if server.wait(ticket, timeout_ms) != N.LF_OK:
+                out.append(dict(status=N.LF_ERR_TIMEOUT, frame=None, latency=float("nan")))
+                continue
+            st, frame, tm = server.result(ticket, rq.cam, want_frame=keep_frames)
+            out.append(dict(status=st, frame=frame, latency=tm["t_done"] - tm["t_submit"], **tm))
+    finally:
+        th.join()
     return out
 
 
