@@ -430,11 +430,14 @@ def main():
     hbm, peak_kind = read_peaks()
     avg = {n: statistics.mean(v) for n, v in phase_ms.items()}
     kavg = {n: statistics.mean(v) for n, v in kern_ms.items()}
-    # algorithmic bytes per launch: node visits x 64 B, surfel tests x 64 B (packed record), composited
-    # hits x 80 B (record + material), plus each kernel's per-ray input and output
+    # algorithmic bytes per launch: node visits x node bytes (binary node 64 B; wide node WIDE slots of
+    # 32 B), surfel tests x 64 B (packed record), composited hits x 80 B (record + material), plus each
+    # kernel's per-ray input and output
+    wide = step.tr.bvh_wide(0)[0].shape[1]
+    node_bytes = {"primary": 64, "nee_shadow": 32 * wide, "continuation": 64, "secondary_shadow": 32 * wide}
     per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32}
-    kbytes = {n: 64 * counters[n][0] + 64 * counters[n][1] + 80 * counters[n][2] + per_ray_io[n] * counters[n][3]
-              for n in per_ray_io}
+    kbytes = {n: node_bytes[n] * counters[n][0] + 64 * counters[n][1] + 80 * counters[n][2] +
+              per_ray_io[n] * counters[n][3] for n in per_ray_io}
     kernels = {n: {"ms": round(kavg[n], 3), "algorithmic_bytes": kbytes.get(n),
                    "achieved_gbs": (kbytes[n] / (kavg[n] * 1e-3) / 1e9) if n in kbytes else None}
                for n in kern_names}
@@ -454,7 +457,8 @@ def main():
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy (burst)", "traffic": traffic,
                      "algorithmic_bytes_per_launch": kbytes[dom], "launch_ms": kavg[dom]},
         "kernels": kernels,
-        "counters": dict(counters, fields=["node visits", "surfel tests", "composited hits", "rays"]),
+        "counters": dict(counters, fields=["node visits", "surfel tests", "composited hits", "rays"],
+                         node_bytes=node_bytes),
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": args.steps * sum(KERNELS_PER_STEP.values()),

@@ -83,6 +83,8 @@ SIGNATURES = [
     ("lf_philox", C.c_int, [_P, _P, C.c_int, C.c_uint32, C.c_uint32, _P]),
     ("lf_env_tables", C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     ("lf_bvh_info", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("lf_bvh_copy_wide", C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("lf_bvh_copy_nodes", C.c_int, [_P, C.c_int, _P, C.c_size_t]),
     ("lf_serve_create", C.c_int, [_P, C.c_size_t, C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
     ("lf_serve_submit", C.c_int, [_P, C.POINTER(LfRequest), C.POINTER(C.c_uint64)]),

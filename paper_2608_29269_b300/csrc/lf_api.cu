@@ -44,8 +44,9 @@ void dev_free(T*& p) {
 void free_scene_storage(lf_ctx* c) {
   dev_free(c->geo); dev_free(c->mat); dev_free(c->nodes); dev_free(c->leaf_parent); dev_free(c->node_parent);
   dev_free(c->flags); dev_free(c->keys); dev_free(c->vals); dev_free(c->keys_alt); dev_free(c->vals_alt);
-  dev_free(c->counts);
+  dev_free(c->counts); dev_free(c->node_range); dev_free(c->wnodes); dev_free(c->wsrc); dev_free(c->wqueue);
   c->cap_n = 0;
+  c->wcap = 0;
 }
 
 // Camera basis in FP64: f = normalize(target - eye), r = normalize(f x up),
@@ -108,7 +109,28 @@ lf_status lf_ctx_fit(lf_ctx* c, int first_obj, int last_obj) {
   a.R = std::sqrt(c->params.support_r2);
   a.status = c->status_dev;
   LF_CUDA(c, launch_pack_fit(c->scene, a, c->stream));
+  const int w0 = c->wnode_off_h[first_obj], w1 = c->wnode_off_h[last_obj + 1];
+  if (w1 > w0) {
+    WideArgs w = lf_ctx_wide_args(c);
+    w.first_slot = WIDE * w0;
+    LF_CUDA(c, launch_wide_boxes(w, WIDE * (w1 - w0), c->stream));
+  }
   return LF_OK;
+}
+
+WideArgs lf_ctx_wide_args(lf_ctx* c) {
+  WideArgs w;
+  w.n_obj_total = c->n_obj;
+  w.leaf_off = c->offsets_dev;
+  w.node_off = c->node_off_dev;
+  w.wnode_off = c->wnode_off_dev;
+  w.node_range = c->node_range;
+  w.nodes = c->nodes;
+  w.wnodes = c->wnodes;
+  w.wsrc = c->wsrc;
+  w.wqueue = c->wqueue;
+  w.status = c->status_dev;
+  return w;
 }
 
 TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id) {
@@ -168,6 +190,7 @@ lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->status_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = dev_alloc(&c->offsets_dev, LF_MAX_OBJECTS + 1);
   if (e == cudaSuccess) e = dev_alloc(&c->node_off_dev, LF_MAX_OBJECTS + 1);
+  if (e == cudaSuccess) e = dev_alloc(&c->wnode_off_dev, LF_MAX_OBJECTS + 1);
   if (e == cudaSuccess) e = dev_alloc(&c->bounds, 6 * LF_MAX_OBJECTS);
   if (e == cudaSuccess) e = dev_alloc(&c->insts_dev, LF_MAX_OBJECTS);
   if (e != cudaSuccess) {
@@ -182,7 +205,8 @@ lf_status lf_destroy(lf_ctx* c) {
   if (!c) return LF_ERR_INVALID;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   free_scene_storage(c);
-  dev_free(c->status_dev); dev_free(c->offsets_dev); dev_free(c->node_off_dev); dev_free(c->bounds);
+  dev_free(c->status_dev); dev_free(c->offsets_dev); dev_free(c->node_off_dev); dev_free(c->wnode_off_dev);
+  dev_free(c->bounds);
   dev_free(c->insts_dev);
   for (EnvSlot& e : c->env) { dev_free(e.tables); dev_free(e.rowsum); dev_free(e.sin_row); }
   for (cudaEvent_t& e : c->prof_ev)
@@ -272,6 +296,13 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     if (e == cudaSuccess) e = dev_alloc(&c->keys_alt, cap);
     if (e == cudaSuccess) e = dev_alloc(&c->vals_alt, cap);
     if (e == cudaSuccess) e = dev_alloc(&c->counts, 256 * tiles);
+    if (e == cudaSuccess) e = dev_alloc(&c->node_range, cap);
+    // wide nodes: sum over objects of wide_capacity(n_k) <= 2 cap / (WIDE - 1) + 2 LF_MAX_OBJECTS
+    const size_t wcap = 2 * cap / (WIDE - 1) + 2 * LF_MAX_OBJECTS;
+    if (e == cudaSuccess) e = dev_alloc(&c->wnodes, 2 * WIDE * wcap);
+    if (e == cudaSuccess) e = dev_alloc(&c->wsrc, WIDE * wcap);
+    if (e == cudaSuccess) e = dev_alloc(&c->wqueue, wcap);
+    c->wcap = wcap;
     if (e != cudaSuccess) {
       free_scene_storage(c);
       return fail(c, e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA, "BVH storage allocation failed");
@@ -287,9 +318,14 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
   for (int k = 0; k < n_obj; ++k)
     c->node_off_h[k + 1] = c->node_off_h[k] + std::max(0, c->offsets[k + 1] - c->offsets[k] - 1);
   c->n_nodes = c->node_off_h[n_obj];
+  c->wnode_off_h.assign(n_obj + 1, 0);
+  for (int k = 0; k < n_obj; ++k)
+    c->wnode_off_h[k + 1] = c->wnode_off_h[k] + wide_capacity(c->offsets[k + 1] - c->offsets[k]);
   LF_CUDA(c, cudaMemcpyAsync(c->offsets_dev, c->offsets.data(), sizeof(int) * (n_obj + 1), cudaMemcpyHostToDevice,
                              c->stream));
   LF_CUDA(c, cudaMemcpyAsync(c->node_off_dev, c->node_off_h.data(), sizeof(int) * (n_obj + 1),
+                             cudaMemcpyHostToDevice, c->stream));
+  LF_CUDA(c, cudaMemcpyAsync(c->wnode_off_dev, c->wnode_off_h.data(), sizeof(int) * (n_obj + 1),
                              cudaMemcpyHostToDevice, c->stream));
   // instance table (boxes are written by the fit)
   c->insts_h.assign(n_obj, Inst{});
@@ -304,6 +340,9 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     I.mat = c->mat + (size_t)c->offsets[k];
     I.id_base = c->offsets[k];
     I.pad = 0;
+    I.wnodes = c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k];
+    I.wroot = nk > WIDE ? 0 : (nk >= 1 ? ~0 : INT_MIN);
+    I.wroot_count = nk > WIDE ? 0 : nk;
   }
   LF_CUDA(c, cudaMemcpyAsync(c->insts_dev, c->insts_h.data(), sizeof(Inst) * n_obj, cudaMemcpyHostToDevice,
                              c->stream));
@@ -315,7 +354,15 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     LF_CUDA(c, cudaMemsetAsync(c->leaf_parent, 0xff, sizeof(int) * (size_t)n, c->stream));
     LF_CUDA(c, cudaMemsetAsync(c->node_parent, 0xff, sizeof(int) * (size_t)n, c->stream));
     LF_CUDA(c, launch_hierarchy(c->keys, c->offsets_dev, c->node_off_dev, n_obj, c->n_nodes, c->nodes,
-                                c->leaf_parent, c->node_parent, c->stream));
+                                c->leaf_parent, c->node_parent, c->node_range, c->stream));
+    const int n_wide = c->wnode_off_h[n_obj];
+    if (n_wide > 0) {
+      LF_CUDA(c, cudaMemsetAsync(c->wsrc, 0xff, sizeof(int) * WIDE * (size_t)n_wide, c->stream));
+      WideArgs w = lf_ctx_wide_args(c);
+      w.first_obj = 0;
+      w.n_objs = n_obj;
+      LF_CUDA(c, launch_collapse(w, c->stream));
+    }
     lf_status st = lf_ctx_fit(c, 0, n_obj - 1);
     if (st != LF_OK) return st;
   }
@@ -537,6 +584,25 @@ lf_status lf_bvh_copy_nodes(lf_ctx* c, int k, float* host_out, size_t bytes) {
   if (bytes < nn * 64) return fail(c, LF_ERR_INVALID, "buffer too small");
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   if (nn) LF_CUDA(c, cudaMemcpy(host_out, c->nodes + 4 * (size_t)c->node_off_h[k], nn * 64, cudaMemcpyDeviceToHost));
+  return LF_OK;
+}
+
+lf_status lf_bvh_copy_wide(lf_ctx* c, int k, float* host_out, size_t bytes, int* cap_nodes, int* root_code,
+                           int* root_count, int* wide) {
+  if (!c) return LF_ERR_INVALID;
+  if (!c->built) return fail(c, LF_ERR_NOT_BUILT, "no BVH");
+  if (k < 0 || k >= c->n_obj) return fail(c, LF_ERR_INVALID, "bad object id");
+  const size_t nn = (size_t)(c->wnode_off_h[k + 1] - c->wnode_off_h[k]);
+  if (cap_nodes) *cap_nodes = (int)nn;
+  if (root_code) *root_code = c->insts_h[k].wroot;
+  if (root_count) *root_count = c->insts_h[k].wroot_count;
+  if (wide) *wide = WIDE;
+  if (!host_out) return LF_OK;
+  const size_t need = nn * 2 * WIDE * sizeof(float4);
+  if (bytes < need) return fail(c, LF_ERR_INVALID, "buffer too small");
+  LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (nn)
+    LF_CUDA(c, cudaMemcpy(host_out, c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k], need, cudaMemcpyDeviceToHost));
   return LF_OK;
 }
 

@@ -16,7 +16,7 @@ constexpr int STACK_SMEM = TB * STACK * (int)sizeof(int);
 __device__ __forceinline__ void load_instances_b(Inst* dst, const Inst* src, int n) {
   const float4* s = reinterpret_cast<const float4*>(src);
   float4* d = reinterpret_cast<float4*>(dst);
-  for (int i = threadIdx.x; i < n * 4; i += blockDim.x) d[i] = s[i];
+  for (int i = threadIdx.x; i < n * (int)(sizeof(Inst) / sizeof(float4)); i += blockDim.x) d[i] = s[i];
   __syncthreads();
 }
 

@@ -219,7 +219,7 @@ __device__ __forceinline__ int delta(const unsigned* k, int n, int i, int j) {
 __global__ void k_hierarchy(const unsigned* __restrict__ skeys, const int* __restrict__ leaf_off,
                             const int* __restrict__ node_off, int n_obj, int n_nodes_total,
                             float4* __restrict__ nodes, int* __restrict__ leaf_parent,
-                            int* __restrict__ node_parent) {
+                            int* __restrict__ node_parent, int2* __restrict__ node_range) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_nodes_total) return;
   const int obj = object_of(node_off, n_obj, g);
@@ -245,6 +245,7 @@ __global__ void k_hierarchy(const unsigned* __restrict__ skeys, const int* __res
   const int left = (min(i, j) == gamma) ? ~gamma : gamma;
   const int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
   nodes[4 * (nb + i) + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
+  node_range[nb + i] = make_int2(min(i, j), abs(i - j) + 1);  // first leaf, leaf count
   if (left < 0) leaf_parent[lb + gamma] = (i << 1) | 0; else node_parent[nb + gamma] = (i << 1) | 0;
   if (right < 0) leaf_parent[lb + gamma + 1] = (i << 1) | 1; else node_parent[nb + gamma + 1] = (i << 1) | 1;
   if (i == 0) node_parent[nb] = -1;
@@ -323,6 +324,126 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
   report(a.status, LF_ERR_INVALID);
 }
 
+// ---------------------------------------------------------------- wide BVH
+// The binary BLAS of each object is collapsed into a WIDE-ary tree whose
+// nodes are traversed by WIDE lanes at once (one child slot per lane).  A wide
+// node starts from a binary node's two children and repeatedly replaces the
+// child with the most leaves by its own two children, while fewer than WIDE
+// children are held and that child has more than WIDE leaves.  A child with
+// at most WIDE leaves becomes a leaf slot (its surfels are consecutive in leaf
+// order); a larger one becomes a wide node of its own.  The rule depends on
+// leaf counts only, so the wide topology is fixed by the build and a refit
+// only copies boxes (k_wide_boxes).  A wide node that is not full holds only
+// leaf slots and covers more than WIDE surfels, which bounds the node count by
+// 2n / (WIDE - 1) + 2 per object.
+//
+// Topology: one block per object, level by level (breadth first); children
+// get consecutive indices in item order (block-wide scan), so the layout is
+// deterministic.  wsrc[slot] = binary parent (object-local) * 2 + side of the
+// slot's box; -1 for an empty slot.
+constexpr int COLLAPSE_THREADS = 128;
+
+__global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
+  __shared__ int s_scan[COLLAPSE_THREADS];
+  const int obj = a.first_obj + blockIdx.x;
+  const int n = a.leaf_off[obj + 1] - a.leaf_off[obj];
+  if (n <= WIDE) return;  // the root is a leaf slot held by the instance
+  const int nb = a.node_off[obj];                      // binary nodes, global numbering (ranges)
+  const int wb = a.wnode_off[obj];                     // wide nodes, global numbering
+  const int cap = a.wnode_off[obj + 1] - wb;
+  const float4* bnodes = a.nodes + 4 * (size_t)(nb - a.node_base);
+  float4* wn = a.wnodes + 2 * WIDE * (size_t)(wb - a.wnode_base);
+  int* wsrc = a.wsrc + WIDE * (size_t)(wb - a.wsrc_base);
+  int* queue = a.wqueue + (wb - a.wnode_base);
+  if (threadIdx.x == 0) queue[0] = 0;
+  __syncthreads();
+  int level_begin = 0, level_end = 1, total = 1;
+  bool overflow = false;
+  while (level_begin < level_end && !overflow) {
+    for (int chunk = level_begin; chunk < level_end; chunk += COLLAPSE_THREADS) {
+      const int item = chunk + threadIdx.x;
+      const bool valid = item < level_end;
+      int code[WIDE], cnt[WIDE], src[WIDE];
+      int nc = 0, n_int = 0;
+      if (valid) {
+        const int b = queue[item];
+        const float4 f = bnodes[4 * b + 3];
+        const int cl = __float_as_int(f.x), cr = __float_as_int(f.y);
+        code[0] = cl; src[0] = 2 * b + 0; cnt[0] = cl >= 0 ? a.node_range[nb + cl].y : 1;
+        code[1] = cr; src[1] = 2 * b + 1; cnt[1] = cr >= 0 ? a.node_range[nb + cr].y : 1;
+        nc = 2;
+        while (nc < WIDE) {
+          int best = -1;
+          for (int c = 0; c < nc; ++c)
+            if (code[c] >= 0 && cnt[c] > WIDE && (best < 0 || cnt[c] > cnt[best])) best = c;
+          if (best < 0) break;
+          const int e = code[best];
+          const float4 g = bnodes[4 * e + 3];
+          const int el = __float_as_int(g.x), er = __float_as_int(g.y);
+          code[best] = el; src[best] = 2 * e + 0; cnt[best] = el >= 0 ? a.node_range[nb + el].y : 1;
+          code[nc] = er; src[nc] = 2 * e + 1; cnt[nc] = er >= 0 ? a.node_range[nb + er].y : 1;
+          ++nc;
+        }
+        for (int c = 0; c < nc; ++c) n_int += (code[c] >= 0 && cnt[c] > WIDE) ? 1 : 0;
+      }
+      // exclusive scan of n_int over the chunk (item order)
+      s_scan[threadIdx.x] = n_int;
+      __syncthreads();
+      for (int off = 1; off < COLLAPSE_THREADS; off <<= 1) {
+        const int v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_scan[threadIdx.x] += v;
+        __syncthreads();
+      }
+      const int chunk_total = s_scan[COLLAPSE_THREADS - 1];
+      int next = total + s_scan[threadIdx.x] - n_int;
+      if (total + chunk_total > cap) {
+        overflow = true;  // uniform: every thread read the same scan total
+      } else if (valid) {
+        float4* node = wn + 2 * WIDE * (size_t)item;
+        for (int c = 0; c < WIDE; ++c) {
+          int cd = INT_MIN, ct = 0, sr = -1;
+          if (c < nc) {
+            sr = src[c];
+            if (code[c] >= 0 && cnt[c] > WIDE) {
+              cd = next;
+              queue[next++] = code[c];
+            } else {
+              cd = ~(code[c] >= 0 ? a.node_range[nb + code[c]].x : ~code[c]);
+              ct = cnt[c];
+            }
+          }
+          node[2 * c + 0] = make_float4(1.0f, 1.0f, 1.0f, __int_as_float(cd));
+          node[2 * c + 1] = make_float4(-1.0f, -1.0f, -1.0f, __int_as_float(ct));
+          wsrc[WIDE * item + c] = sr;
+        }
+      }
+      total += chunk_total;
+      __syncthreads();
+    }
+    level_begin = level_end;
+    level_end = total;
+  }
+  if (overflow && threadIdx.x == 0) report(a.status, LF_ERR_INVALID);
+}
+
+// Box of every wide slot from the binary node holding it (build and refit).
+__global__ void k_wide_boxes(WideArgs a, int n_slots) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_slots) return;
+  const int slot = a.first_slot + k;
+  const int sr = a.wsrc[slot - WIDE * a.wsrc_base];
+  if (sr < 0) return;
+  const int obj = object_of(a.wnode_off, a.n_obj_total, slot / WIDE);
+  const int nb = a.node_off[obj] - a.node_base;
+  const float* f = reinterpret_cast<const float*>(a.nodes + 4 * (size_t)(nb + (sr >> 1)));
+  const int o = (sr & 1) ? 6 : 0;
+  float4* w = a.wnodes + 2 * (size_t)(slot - WIDE * a.wnode_base);
+  const float4 p = w[0], q = w[1];
+  w[0] = make_float4(f[o + 0], f[o + 1], f[o + 2], p.w);
+  w[1] = make_float4(f[o + 3], f[o + 4], f[o + 5], q.w);
+}
+
 // ---------------------------------------------------------------- rigid transform
 __global__ void k_rigid(SceneDev s, int beg, int end, Mat34 T) {
   const int i = beg + blockIdx.x * blockDim.x + threadIdx.x;
@@ -395,7 +516,7 @@ __global__ void k_gather_insts(InstPtrs src, Inst* __restrict__ dst, int n) {
   if (k >= n) return;
   const float4* s = reinterpret_cast<const float4*>(src.p[k]);
   float4* d = reinterpret_cast<float4*>(dst + k);
-  if (threadIdx.x < 4) d[threadIdx.x] = s[threadIdx.x];
+  if (threadIdx.x < (int)(sizeof(Inst) / sizeof(float4))) d[threadIdx.x] = s[threadIdx.x];
 }
 
 __global__ void k_philox(const uint4* __restrict__ ctr, int n, uint32_t k0, uint32_t k1, uint4* __restrict__ out) {
@@ -442,10 +563,21 @@ cudaError_t launch_radix_sort(unsigned* keys, unsigned* vals, unsigned* keys_alt
 }
 
 cudaError_t launch_hierarchy(const unsigned* skeys, const int* leaf_off, const int* node_off, int n_obj,
-                             int n_nodes_total, float4* nodes, int* leaf_parent, int* node_parent, cudaStream_t st) {
+                             int n_nodes_total, float4* nodes, int* leaf_parent, int* node_parent,
+                             int2* node_range, cudaStream_t st) {
   if (n_nodes_total > 0)
     k_hierarchy<<<(n_nodes_total + 127) / 128, 128, 0, st>>>(skeys, leaf_off, node_off, n_obj, n_nodes_total,
-                                                            nodes, leaf_parent, node_parent);
+                                                            nodes, leaf_parent, node_parent, node_range);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collapse(const WideArgs& a, cudaStream_t st) {
+  if (a.n_objs > 0) k_collapse<<<a.n_objs, COLLAPSE_THREADS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_boxes(const WideArgs& a, int n_slots, cudaStream_t st) {
+  if (n_slots > 0) k_wide_boxes<<<(n_slots + 255) / 256, 256, 0, st>>>(a, n_slots);
   return cudaGetLastError();
 }
 

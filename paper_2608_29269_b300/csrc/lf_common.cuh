@@ -10,6 +10,9 @@
 //   BVH2 node (64 B, child boxes stored in the parent):
 //     n0 = (L.lo.xyz, L.hi.x)  n1 = (L.hi.yz, R.lo.xy)  n2 = (R.lo.z, R.hi.xyz)
 //     n3 = (left code, right code, -, -) ; code >= 0 internal node, code < 0 leaf ~code
+//   Wide node (WIDE child slots of 32 B; slot c read by lane c of a ray's group):
+//     slot = (lo.xyz, code), (hi.xyz, count) ; code >= 0 wide node, code < 0 leaf
+//     of `count` consecutive surfels from ~code, INT_MIN empty (inverted box)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,6 +22,11 @@
 namespace lf {
 
 constexpr int K = LF_KBUF;
+// Children per wide BVH node = lanes per ray in the cooperative traversal.
+#ifndef LF_WIDE
+#define LF_WIDE 16
+#endif
+constexpr int WIDE = LF_WIDE;
 constexpr int STACK = LF_STACK_DEPTH;
 constexpr float PI_F = 3.14159265358979323846f;
 constexpr float INV_PI_F = 0.318309886183790671538f;
@@ -33,16 +41,19 @@ struct DevParams {
 // One TLAS entry: an object's BLAS in world space (Eq. 2 after its transform).
 struct __align__(16) Inst {
   float lo[3];
-  int root;  // child code of the BLAS root (>= 0 node, < 0 leaf ~code); INT_MIN: empty
+  int root;  // child code of the binary BLAS root (>= 0 node, < 0 leaf ~code); INT_MIN: empty
   float hi[3];
   int n_leaves;
-  const float4* nodes;
+  const float4* nodes;   // binary BLAS
   const float4* geo;
   const float4* mat;
   int id_base;  // surfel id of the object's first surfel
   int pad;
+  const float4* wnodes;  // wide BLAS (WIDE children per node)
+  int wroot;             // wide root: >= 0 node, < 0 leaf ~first; INT_MIN: empty
+  int wroot_count;       // surfels of a leaf root
 };
-static_assert(sizeof(Inst) == 64, "Inst is 64 bytes");
+static_assert(sizeof(Inst) == 80, "Inst is 80 bytes");
 
 struct EnvDev {
   const float* rgb;  // H x W x 3

@@ -34,14 +34,20 @@ struct lf_ctx {
   lf::SceneDev scene{};
   bool built = false;
   int n = 0, n_obj = 0, n_nodes = 0;
-  std::vector<int> offsets, node_off_h;
+  std::vector<int> offsets, node_off_h, wnode_off_h;
   int* offsets_dev = nullptr;
   int* node_off_dev = nullptr;
+  int* wnode_off_dev = nullptr;
   int* bounds = nullptr;
   // library-owned BVH storage
   float4* geo = nullptr;
   float4* mat = nullptr;
   float4* nodes = nullptr;
+  int2* node_range = nullptr;  // per binary node: first leaf, leaf count
+  float4* wnodes = nullptr;    // wide BVH (WIDE slots of 2 float4 per node)
+  int* wsrc = nullptr;         // per wide slot: binary parent * 2 + side, -1 empty
+  int* wqueue = nullptr;       // collapse work queue
+  size_t wcap = 0;             // wide nodes allocated
   int* leaf_parent = nullptr;
   int* node_parent = nullptr;
   int* flags = nullptr;
@@ -59,4 +65,6 @@ struct lf_ctx {
 // Repack + refit objects [first_obj, last_obj] (lf_api.cu).
 lf_status lf_ctx_fit(lf_ctx* c, int first_obj, int last_obj);
 lf::TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id);
+// Wide-BVH arguments over the context's own storage (bases 0).
+lf::WideArgs lf_ctx_wide_args(lf_ctx* c);
 lf::CamDev lf_ctx_cam(const lf_camera& c);

@@ -32,6 +32,28 @@ struct FitArgs {
   int leaf_base = 0, node_base = 0, id_base = 0, inst_base = 0;  // object-local storage (served versions)
 };
 
+// Wide BVH collapse (topology) and box copy.  Index bases are subtracted
+// when addressing object-local storage (a served version); all bases are 0 for
+// the context's own arrays.
+struct WideArgs {
+  int first_obj = 0, n_objs = 0;  // objects handled by the launch
+  int n_obj_total = 0;            // objects in the offset tables
+  const int* leaf_off = nullptr;  // device, n_obj_total + 1
+  const int* node_off = nullptr;  // device, binary node offsets
+  const int* wnode_off = nullptr; // device, wide node offsets
+  const int2* node_range = nullptr;  // per binary node: first leaf, leaf count
+  const float4* nodes = nullptr;  // binary nodes (index - node_base)
+  float4* wnodes = nullptr;       // wide nodes (index - wnode_base)
+  int* wsrc = nullptr;            // per wide slot: binary parent * 2 + side, -1 empty (slot - WIDE * wsrc_base)
+  int* wqueue = nullptr;          // collapse queue (index - wnode_base)
+  int node_base = 0, wnode_base = 0, wsrc_base = 0;
+  int first_slot = 0;             // first global slot of a box copy
+  int* status = nullptr;
+};
+
+// Wide nodes an object of n surfels can need.
+inline int wide_capacity(int n) { return n > WIDE ? 2 * n / (WIDE - 1) + 2 : 0; }
+
 struct InstPtrs {
   const Inst* p[LF_MAX_OBJECTS];
 };
@@ -45,7 +67,10 @@ int radix_tiles(int n);
 cudaError_t launch_radix_sort(unsigned* keys, unsigned* vals, unsigned* keys_alt, unsigned* vals_alt, int n,
                               const int* offsets_dev, int n_obj, unsigned* counts, cudaStream_t st);
 cudaError_t launch_hierarchy(const unsigned* skeys, const int* leaf_off, const int* node_off, int n_obj,
-                             int n_nodes_total, float4* nodes, int* leaf_parent, int* node_parent, cudaStream_t st);
+                             int n_nodes_total, float4* nodes, int* leaf_parent, int* node_parent,
+                             int2* node_range, cudaStream_t st);
+cudaError_t launch_collapse(const WideArgs& a, cudaStream_t st);
+cudaError_t launch_wide_boxes(const WideArgs& a, int n_slots, cudaStream_t st);
 cudaError_t launch_pack_fit(const SceneDev& s, const FitArgs& a, cudaStream_t st);
 cudaError_t launch_rigid(const SceneDev& s, int beg, int end, const Mat34& T, cudaStream_t st);
 cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int set_rgb, float metal, float rough,

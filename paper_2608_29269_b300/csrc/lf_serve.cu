@@ -10,12 +10,16 @@
 //
 // Continuous batching: a scheduler thread admits pending requests in FIFO
 // order while a slot is free and their memory (frame, G-buffer, per-sample
-// buffer, new version) fits the budget; all requests admitted together form
-// a group whose shading runs as one batched wavefront (work items of every
-// request in the same launches) on one of several streams, so groups overlap
-// on the device; a group's finished frames are copied to pinned host memory.
+// buffer, new version) fits the budget; requests admitted together (up to a
+// work-item cap) form a group whose shading runs as one batched wavefront
+// (work items of every request in the same launches).  Groups launch on a
+// ladder of stream priorities: the oldest group in flight has precedence and
+// younger ones fill the SMs its kernels leave idle, so groups overlap on the
+// device without slowing the oldest; a group's finished frames are copied to
+// pinned host memory.
 // Completion is observed with events; memory of finished groups and of
 // versions no request references any more is released stream-ordered.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -39,6 +43,11 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// A launch group takes pending requests in FIFO order up to this many work
+// items (pixels x samples); a larger request forms a group of its own.
+// Small requests share launches; a large one does not hold small ones back.
+constexpr long long GROUP_MAX_SAMPLES = 1ll << 22;
+
 // Attribute layout of a version's raw copy (floats per surfel).
 constexpr int RAW_FLOATS = 17;
 
@@ -49,6 +58,7 @@ struct Version {
   float4* geo = nullptr;
   float4* mat = nullptr;
   float4* nodes = nullptr;
+  float4* wnodes = nullptr;   // wide BVH (topology of the build, boxes of this version)
   int* flags = nullptr;
   Inst* inst = nullptr;       // device entry (box written by the fit)
   char* block = nullptr;      // single allocation holding everything above
@@ -89,6 +99,7 @@ struct Job {
 
 struct Group {
   std::vector<Job*> jobs;
+  int level = 0;  // index into the server's streams (priority order)
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   char* samples = nullptr;
@@ -103,8 +114,10 @@ struct lf_serve {
   size_t budget = 0, used = 0;
   int max_slots = 1, in_flight = 0;
   double window_s = 0.0;  // how long a lone request waits for company
+  // streams[0] has the highest priority; a group launches on the stream one
+  // below the youngest group in flight (the last stream serialises), so
+  // older groups keep precedence and younger ones fill their tails.
   std::vector<cudaStream_t> streams;
-  int next_stream = 0;
   cudaStream_t edit_stream = nullptr;
   cudaEvent_t edit_event = nullptr;
   // Stream-ordered allocations come from this server's own pool, which keeps
@@ -143,7 +156,7 @@ size_t frame_bytes_of(const lf_camera& c, int spp) {
 
 size_t version_bytes(int n) {
   return sizeof(float) * RAW_FLOATS * (size_t)n + sizeof(float4) * (GEO + 1 + 4) * (size_t)n +
-         sizeof(int) * (size_t)n + sizeof(Inst) + 1024;
+         sizeof(float4) * 2 * WIDE * (size_t)wide_capacity(n) + sizeof(int) * (size_t)n + sizeof(Inst) + 1280;
 }
 
 // New version of object k: copy the current one, apply the edit, repack and
@@ -164,6 +177,8 @@ lf_status make_version(lf_serve* s, const lf_edit& e, Version** out) {
   v->geo = reinterpret_cast<float4*>(take(sizeof(float4) * GEO * n));
   v->mat = reinterpret_cast<float4*>(take(sizeof(float4) * n));
   v->nodes = reinterpret_cast<float4*>(take(sizeof(float4) * 4 * std::max(1, n - 1)));
+  const int nw = c->wnode_off_h[k + 1] - c->wnode_off_h[k];
+  v->wnodes = reinterpret_cast<float4*>(take(sizeof(float4) * 2 * WIDE * std::max(1, nw)));
   v->flags = reinterpret_cast<int*>(take(sizeof(int) * n));
   v->inst = reinterpret_cast<Inst*>(take(sizeof(Inst)));
   // copy attributes, nodes (child codes) and the instance entry
@@ -186,9 +201,13 @@ lf_status make_version(lf_serve* s, const lf_edit& e, Version** out) {
   if (n >= 2 && cudaMemcpyAsync(v->nodes, cur->nodes, sizeof(float4) * 4 * (n - 1), cudaMemcpyDeviceToDevice,
                                 s->edit_stream) != cudaSuccess)
     return LF_ERR_CUDA;
+  if (nw > 0 && cudaMemcpyAsync(v->wnodes, cur->wnodes, sizeof(float4) * 2 * WIDE * nw, cudaMemcpyDeviceToDevice,
+                                s->edit_stream) != cudaSuccess)
+    return LF_ERR_CUDA;
   // the instance entry points at the version's arrays (its box is written by the fit)
   Inst hinst = c->insts_h[k];
   hinst.nodes = v->nodes;
+  hinst.wnodes = v->wnodes;
   hinst.geo = v->geo;
   hinst.mat = v->mat;
   if (cudaMemcpyAsync(v->inst, &hinst, sizeof(Inst), cudaMemcpyHostToDevice, s->edit_stream) != cudaSuccess)
@@ -229,6 +248,15 @@ lf_status make_version(lf_serve* s, const lf_edit& e, Version** out) {
   a.id_base = c->offsets[k];
   a.inst_base = k;
   if (launch_pack_fit(dst, a, s->edit_stream) != cudaSuccess) return LF_ERR_CUDA;
+  if (nw > 0) {  // wide boxes from the version's refit binary nodes
+    WideArgs w = lf_ctx_wide_args(c);
+    w.nodes = v->nodes;
+    w.node_base = c->node_off_h[k];
+    w.wnodes = v->wnodes;
+    w.wnode_base = c->wnode_off_h[k];
+    w.first_slot = WIDE * c->wnode_off_h[k];
+    if (launch_wide_boxes(w, WIDE * nw, s->edit_stream) != cudaSuccess) return LF_ERR_CUDA;
+  }
   *out = v.get();
   s->versions.push_back(std::move(v));
   return LF_OK;
@@ -287,7 +315,8 @@ TraceArgs job_trace_args(lf_serve* s, Job* j) {
 
 lf_status launch_group(lf_serve* s, Group* g) {
   lf_ctx* c = s->ctx;
-  g->stream = s->streams[s->next_stream++ % s->streams.size()];
+  g->level = s->groups.empty() ? 0 : std::min(s->groups.back()->level + 1, (int)s->streams.size() - 1);
+  g->stream = s->streams[g->level];
   if (cudaEventRecord(s->edit_event, s->edit_stream) != cudaSuccess) return LF_ERR_CUDA;
   if (cudaStreamWaitEvent(g->stream, s->edit_event, 0) != cudaSuccess) return LF_ERR_CUDA;
   ShadeBatch B;
@@ -381,9 +410,12 @@ void worker_main(lf_serve* s) {
     }
     // admit a group in FIFO order
     Group* g = nullptr;
+    long long g_samples = 0;
     while (!s->pending.empty() && s->in_flight < s->max_slots && !s->frame_pool.empty() &&
            (!g || (int)g->jobs.size() < MAX_JOBS)) {
       Job* j = s->pending.front();
+      const long long j_samples = (long long)j->req.cam.width * j->req.cam.height * j->req.spp;
+      if (g && g_samples + j_samples > GROUP_MAX_SAMPLES) break;  // next group
       const size_t need = frame_bytes_of(j->req.cam, j->req.spp) +
                           ((j->req.edit.kind == LF_EDIT_MOVE || j->req.edit.kind == LF_EDIT_MATERIAL)
                                ? version_bytes(s->current[j->req.edit.object_id]->n) : 0);
@@ -421,6 +453,7 @@ void worker_main(lf_serve* s) {
       j->state = 1;
       if (!g) g = new Group();
       g->jobs.push_back(j);
+      g_samples += j_samples;
     }
     if (g) {
       const double t = now_s();
@@ -507,9 +540,12 @@ lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams
   }
   if (cudaStreamCreateWithFlags(&s->edit_stream, cudaStreamNonBlocking) != cudaSuccess) return LF_ERR_CUDA;
   if (cudaEventCreateWithFlags(&s->edit_event, cudaEventDisableTiming) != cudaSuccess) return LF_ERR_CUDA;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return LF_ERR_CUDA;
   for (int i = 0; i < n_streams; ++i) {
     cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LF_ERR_CUDA;
+    const int prio = std::min(greatest + i, least);  // numerically lower = higher priority
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess) return LF_ERR_CUDA;
     s->streams.push_back(st);
   }
   // base versions: the context's storage
@@ -520,6 +556,7 @@ lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams
     v->base = true;
     v->inst = c->insts_dev + k;
     v->nodes = c->nodes + 4 * (size_t)c->node_off_h[k];
+    v->wnodes = c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k];
     v->refs = 1;
     s->current.push_back(v.get());
     s->versions.push_back(std::move(v));

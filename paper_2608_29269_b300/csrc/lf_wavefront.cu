@@ -20,6 +20,7 @@
 // four kernels are replayed with the same seed first.
 #include <algorithm>
 
+#include "lf_coop.cuh"
 #include "lf_wavefront.h"
 
 namespace lf {
@@ -110,7 +111,7 @@ __device__ __forceinline__ void queue_push(int* q, int* counter, int value, bool
 __device__ __forceinline__ void load_insts(Inst* dst, const Inst* src, int n) {
   const float4* s = reinterpret_cast<const float4*>(src);
   float4* d = reinterpret_cast<float4*>(dst);
-  for (int i = threadIdx.x; i < n * 4; i += blockDim.x) d[i] = s[i];
+  for (int i = threadIdx.x; i < n * (int)(sizeof(Inst) / sizeof(float4)); i += blockDim.x) d[i] = s[i];
 }
 
 // ---------------------------------------------------------------- generation
@@ -176,70 +177,62 @@ __device__ __forceinline__ int warp_fetch(int* cursor) {
 // ---------------------------------------------------------------- shadow rays
 // which = 0: NEE rays of queue A (origin from the G-buffer, direction we)
 // which = 1: secondary NEE rays of queue C (entry = item * 2 + q)
-//
-// Rays of one warp differ widely in length, so a lane whose ray has ended
-// takes a new one: after each descent-and-leaf step the warp counts its idle
-// lanes and, once at least SHADOW_REFILL of them are idle, fetches that many
-// queue entries with one atomic and starts them.  A shadow ray's start and
-// end are cheap (two plane loads, one store), so refilling costs little.
-#ifndef SHADOW_REFILL
-#define SHADOW_REFILL 8
-#endif
+// WIDE lanes trace each ray through the wide BVH (lf_coop.cuh); a group takes
+// the next queue entry as soon as its ray has ended.
+constexpr int WGROUPS = WB / WIDE;  // rays per block in the cooperative kernels
+constexpr int CSTACK_SMEM = WGROUPS * CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float));
+
+__device__ __forceinline__ CStack group_stack(int* smem) {
+  const int gid = threadIdx.x / WIDE;
+  CStack st;
+  st.code = smem + gid * CSTACK;
+  st.cnt = smem + WGROUPS * CSTACK + gid * CSTACK;
+  st.t = reinterpret_cast<float*>(smem + 2 * WGROUPS * CSTACK) + gid * CSTACK;
+  return st;
+}
+
+// Next queue entry for the group (one atomic per ray).
+__device__ __forceinline__ int group_fetch(const Grp& g, int* cursor) {
+  int k = 0;
+  if (g.c == 0) k = atomicAdd(cursor, 1);
+  return gshfl(g, k, 0);
+}
+
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S,
                                                                         int which, int* status,
                                                                         unsigned long long* counters) {
-  extern __shared__ int s_stack[];
-  int* stack = s_stack + threadIdx.x;
+  extern __shared__ int s_cstack[];
+  const Grp g = make_grp();
+  const CStack st = group_stack(s_cstack);
   const int* q = which == 0 ? S.qA : S.qC;
   const int n = which == 0 ? S.counts[0] : S.counts[2];
   int* cursor = S.counts + (which == 0 ? CURSOR_A : CURSOR_C);
-  const unsigned lane_lt = (1u << (threadIdx.x & 31)) - 1u;
   Counters cnt;
-  bool live = false, drained = false;
-  int e = 0;
-  const Inst* insts = nullptr;
-  ShadowV v;
-  v.P = P;
-  Ray ray;
-  TravState ts;
-  while (true) {
-    const unsigned idle = __ballot_sync(0xffffffffu, !live);
-    if (drained && idle == 0xffffffffu) break;
-    if (!drained && __popc(idle) >= SHADOW_REFILL) {
-      int base = 0;
-      if (lane_lt == 0u) base = atomicAdd(cursor, __popc(idle));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      drained = base + __popc(idle) >= n;
-      const int k = base + __popc(idle & lane_lt);
-      if (!live && k < n) {
-        e = q[k];
-        const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
-        const ShadeJob& J = B.jobs[job_of_item(B, item)];
-        if (which == 0) {
-          const long long loc = item - J.item0;
-          v.o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
-          v.d = ld3(S.we, item);
-        } else {
-          v.o = ld3(S.xs2, item);
-          v.d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
-        }
-        v.V = 1.0f;
-        v.stop = false;
-        ray = make_ray(v.o, v.d);
-        insts = J.insts;
-        trav_begin(insts, J.n_inst, ray, v, stack, WB, status, ts);
-        live = true;
-      }
+  for (int k = group_fetch(g, cursor); k < n; k = group_fetch(g, cursor)) {
+    const int e = q[k];
+    const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+    const ShadeJob& J = B.jobs[job_of_item(B, item)];
+    ShadowCoop v;
+    v.P = P;
+    if (which == 0) {
+      const long long loc = item - J.item0;
+      v.o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+      v.d = ld3(S.we, item);
+    } else {
+      v.o = ld3(S.xs2, item);
+      v.d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
     }
-    if (live && !trav_step(insts, ray, v, stack, WB, status, cnt, ts)) {
-      const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+    v.V = 1.0f;
+    v.stop = false;
+    const Ray ray = make_ray(v.o, v.d);
+    coop_traverse(g, J.insts, J.n_inst, ray, v, st, status, cnt);
+    if (g.c == 0) {
       if (which == 0) S.Ve[item] = v.V;
       else if (e & 1) S.Vq1[item] = v.V;
       else S.Vq0[item] = v.V;
-      live = false;
     }
   }
-  if (counters) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
+  if (counters && g.c == 0) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
     unsigned long long* c = counters + 4 * (which == 0 ? 1 : 3);
     atomicAdd(c + 0, (unsigned long long)cnt.nodes);
     atomicAdd(c + 1, (unsigned long long)cnt.tests);
@@ -490,11 +483,11 @@ static int wf_grid(long long n, int sms) {
 // Persistent grid of a trace kernel: the blocks that fit on the GPU at once,
 // no more than the work needs.
 template <class K>
-static int resident_grid(K kernel, long long n, int sms) {
+static int resident_grid(K kernel, long long n, int sms, int smem, int rays_per_block) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WB, WSTACK_SMEM) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WB, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
-  const long long blocks = (n + WB - 1) / WB;
+  const long long blocks = (n + rays_per_block - 1) / rays_per_block;
   return (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sms * per_sm));
 }
 
@@ -511,12 +504,14 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
   mark(1);
   // queue lengths are known only on the device: the trace kernels size
   // their loops from the counters (grids cover the worst case).
-  k_wf_shadow<<<resident_grid(k_wf_shadow, B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 0, status, counters);
+  k_wf_shadow<<<resident_grid(k_wf_shadow, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
+      B, P, S, 0, status, counters);
   mark(2);
-  k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, status, counters);
+  k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms, WSTACK_SMEM, WB), WB, WSTACK_SMEM, st>>>(
+      B, P, S, status, counters);
   mark(3);
-  k_wf_shadow<<<resident_grid(k_wf_shadow, 2 * B.n_items, sms), WB, WSTACK_SMEM, st>>>(B, P, S, 1, status,
-                                                                                          counters);
+  k_wf_shadow<<<resident_grid(k_wf_shadow, 2 * B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
+      B, P, S, 1, status, counters);
   mark(4);
   k_wf_count<<<1, 32, 0, st>>>(S.counts, ray_count);
   return cudaGetLastError();

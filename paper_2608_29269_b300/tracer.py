@@ -230,6 +230,17 @@ class Tracer:
         self.check(self.lib.lf_philox(self.ctx, _ptr(ctr), ctr.shape[0], C.c_uint32(k0), C.c_uint32(k1), _ptr(out)))
         return out
 
+    def bvh_wide(self, object_id: int):
+        """(slots (cap, WIDE, 8) float32, root code, root count): the object's wide BVH storage."""
+        import numpy as np
+        cap, root, rcount, wide = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self.check(self.lib.lf_bvh_copy_wide(self.ctx, int(object_id), None, 0, C.byref(cap), C.byref(root),
+                                             C.byref(rcount), C.byref(wide)))
+        buf = np.zeros((max(1, cap.value), wide.value, 8), np.float32)
+        self.check(self.lib.lf_bvh_copy_wide(self.ctx, int(object_id), buf.ctypes.data_as(C.c_void_p), buf.nbytes,
+                                             C.byref(cap), C.byref(root), C.byref(rcount), C.byref(wide)))
+        return buf[: cap.value], root.value, rcount.value
+
     def bvh_nodes(self, object_id: int):
         n_int, root = C.c_int(), C.c_int()
         self.check(self.lib.lf_bvh_info(self.ctx, int(object_id), C.byref(n_int), C.byref(root)))

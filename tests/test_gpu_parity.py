@@ -159,6 +159,48 @@ def test_bvh_boxes_nest_and_cover_every_leaf():
         assert np.all(seen == 1)
 
 
+def test_wide_bvh_covers_every_leaf_once_and_nests():
+    """The wide BVH collapsed from the binary one: every surfel in exactly one
+    leaf slot, child slot boxes inside their parent slot's box, leaf slots of
+    at most WIDE surfels, node count within the per-object capacity."""
+    sc = S.scene_c2(0, per_face=2000, per_object=5000)
+    tr, _ = gpu_tracer(sc, [S.env_uniform(1.0, 8, 16)])
+    nodes_b = {}
+    for obj in range(sc.n_objects):
+        slots, root, rcount = tr.bvh_wide(obj)
+        n_leaves = sc.object_offsets[obj + 1] - sc.object_offsets[obj]
+        wide = slots.shape[1]
+        seen = np.zeros(n_leaves, int)
+        if root < 0:
+            assert n_leaves <= wide and rcount == n_leaves
+            continue
+        codes = slots[:, :, 3].copy().view(np.int32)
+        counts = slots[:, :, 7].copy().view(np.int32)
+        visited = set()
+        stack = [0]
+        while stack:
+            n = stack.pop()
+            assert n not in visited and n < len(slots)
+            visited.add(n)
+            for c in range(wide):
+                code = int(codes[n, c])
+                if code == np.iinfo(np.int32).min:
+                    continue
+                lo, hi = slots[n, c, 0:3], slots[n, c, 4:7]
+                assert np.all(lo <= hi)
+                if code >= 0:
+                    clive = codes[code] != np.iinfo(np.int32).min
+                    assert clive.sum() >= 2
+                    assert np.all(slots[code, clive, 0:3] >= lo) and np.all(slots[code, clive, 4:7] <= hi)
+                    stack.append(code)
+                else:
+                    first, cnt = ~code, int(counts[n, c])
+                    assert 1 <= cnt <= wide
+                    seen[first:first + cnt] += 1
+        assert np.all(seen == 1), obj
+        assert len(visited) <= len(slots)
+
+
 def test_c3_gradient_parity():
     """Adjoint vs the oracle's reverse-mode gradient (1e-3 relative), 512 surfels, 32x32, 4 spp."""
     import torch
