@@ -368,7 +368,9 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
   }
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   c->built = true;
-  return lf_sync(c);
+  const lf_status st = lf_sync(c);
+  if (st != LF_OK) c->built = false;  // a malformed hierarchy is never traced
+  return st;
 }
 
 lf_status lf_bvh_refit(lf_ctx* c, int k, const float R[9], const float t[3]) {
