@@ -434,7 +434,7 @@ def main():
     # 32 B), surfel tests x 64 B (packed record), composited hits x 80 B (record + material), plus each
     # kernel's per-ray input and output
     wide = step.tr.bvh_wide(0)[0].shape[1]
-    node_bytes = {"primary": 64, "nee_shadow": 32 * wide, "continuation": 64, "secondary_shadow": 32 * wide}
+    node_bytes = {"primary": 64, "nee_shadow": 32 * wide, "continuation": 32 * wide, "secondary_shadow": 32 * wide}
     per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32}
     kbytes = {n: node_bytes[n] * counters[n][0] + 64 * counters[n][1] + 80 * counters[n][2] +
               per_ray_io[n] * counters[n][3] for n in per_ray_io}

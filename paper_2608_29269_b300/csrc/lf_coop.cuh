@@ -178,4 +178,173 @@ struct ShadowCoop {
   }
 };
 
+// Cooperative k-buffer (K = WIDE): the K smallest hit keys strictly greater
+// than the last round's, sorted over the lanes (lane c holds entry c).  A
+// candidate is inserted by every lane at once: lanes below its rank keep their
+// entry, the lane at its rank takes it, the lanes above take their lower
+// neighbour's entry (the largest falls off a full buffer).
+struct NearKCoop {
+  unsigned long long bk;    // this lane's entry (~0: empty)
+  int bc;                   // its hit code: instance << 24 | leaf
+  int cnt;                  // entries held
+  unsigned long long last;  // keys must exceed this
+  unsigned long long kmax;  // largest held key once full
+  float kth;                // key_t(kmax) once full, else BIG_F
+  float3 o, d;
+  DevParams P;
+
+  __device__ __forceinline__ void reset(unsigned long long lk) {
+    bk = ~0ull;
+    bc = 0;
+    cnt = 0;
+    last = lk;
+    kmax = ~0ull;
+    kth = BIG_F;
+  }
+  __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, key_t(last)); }
+  __device__ __forceinline__ float thi() const { return kth; }
+  __device__ __forceinline__ bool done() const { return false; }
+  __device__ __forceinline__ void abort() { cnt = 0; }
+  __device__ __forceinline__ void leaf(const Grp& g, int ii, int first, int count, const Inst& I) {
+    bool valid = false;
+    unsigned long long key = 0ull;
+    int code = 0;
+    if (g.c < count) {
+      const int l = first + g.c;
+      const Rec r = load_rec(I.geo, l);
+      float t32;
+      if (hit_quick(r, o, d, P, t32) && !(cnt >= WIDE && t32 > kth * 1.0001f + 1e-6f)) {
+        float t, tl, alpha;
+        if (hit_precise(r, o, d, P, t, tl, alpha)) {
+          key = hit_key(t, tl, __float_as_int(r.g1.w));
+          valid = key > last && (cnt < WIDE || key < kmax);
+          code = (ii << 24) | l;
+        }
+      }
+    }
+    unsigned m = gballot(g, valid);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1u;
+      const unsigned long long k = gshfl(g, key, src);
+      const int cd = gshfl(g, code, src);
+      if (cnt >= WIDE && k >= kmax) continue;  // an earlier insertion lowered the bound
+      const unsigned long long pk = __shfl_up_sync(g.mask, bk, 1, WIDE);
+      const int pc = __shfl_up_sync(g.mask, bc, 1, WIDE);
+      if (bk > k) {
+        if (g.c == 0 || pk < k) {
+          bk = k;
+          bc = cd;
+        } else {
+          bk = pk;
+          bc = pc;
+        }
+      }
+      cnt = min(cnt + 1, WIDE);
+      if (cnt >= WIDE) {
+        kmax = gshfl(g, bk, WIDE - 1);
+        kth = key_t(kmax);
+      }
+    }
+  }
+};
+
+// Group sum (every lane receives the same bits).
+__device__ __forceinline__ float gsum(const Grp& g, float v) {
+#pragma unroll
+  for (int off = WIDE / 2; off > 0; off >>= 1) v += __shfl_xor_sync(g.mask, v, off, WIDE);
+  return v;
+}
+
+// Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop),
+// cooperative: each round collects the K nearest hits beyond the last
+// round's, then composites them front to back in parallel -- transmittance
+// in front of each hit by a prefix product over the lanes, the stop at the
+// first hit whose transmittance behind it falls below T_min, weighted sums by
+// butterflies.  Every lane ends with the same Surface.
+__device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, int n_inst, float3 o, float3 d,
+                                               const DevParams& P, const CStack& st, int* status, Counters& cnt,
+                                               Surface& s, unsigned& composited) {
+  NearKCoop kb;
+  kb.o = o;
+  kb.d = d;
+  kb.P = P;
+  const Ray ray = make_ray(o, d);
+  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
+  float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
+  int hits = 0;
+  unsigned long long stop_key = 0ull, last = 0ull;
+  bool done = false;
+  for (int round = 0; round < P.max_rounds && !done; ++round) {
+    kb.reset(last);
+    coop_traverse(g, insts, n_inst, ray, kb, st, status, cnt);
+    const int n = kb.cnt;
+    if (n == 0) break;
+    const bool have = g.c < n;
+    float alpha = 0.0f, t = 0.0f, mtl = 0.0f, rgh = 0.0f;
+    float3 nj = f3(0.f, 0.f, 0.f), alb = nj;
+    if (have) {
+      const Inst& I = insts[kb.bc >> 24];
+      const int l = kb.bc & 0xffffff;
+      const Rec rc = load_rec(I.geo, l);
+      const float4 mt = __ldg(I.mat + l);
+      float tl;
+      hit_precise(rc, o, d, P, t, tl, alpha);
+      nj = record_normal(rc, d);
+      alb = f3(mt.x, mt.y, mt.z);
+      mtl = mt.w;
+      rgh = rc.g2.w;
+    }
+    // inclusive prefix product of (1 - alpha) over the lanes
+    float q = have ? 1.0f - alpha : 1.0f;
+#pragma unroll
+    for (int off = 1; off < WIDE; off <<= 1) {
+      const float v = __shfl_up_sync(g.mask, q, off, WIDE);
+      if (g.c >= off) q *= v;
+    }
+    const float qb = __shfl_up_sync(g.mask, q, 1, WIDE);
+    const float Tb = g.c == 0 ? T : T * qb;  // transmittance in front of this hit
+    const float Ta = T * q;                  // behind it
+    const unsigned stopm = gballot(g, have && Ta < P.T_min);
+    const int lastc = stopm ? __ffs(stopm) - 1 : n - 1;
+    const float w = (have && g.c <= lastc) ? Tb * alpha : 0.0f;
+    W += gsum(g, w);
+    Sx.x += gsum(g, w * fmaf(d.x, t, o.x));
+    Sx.y += gsum(g, w * fmaf(d.y, t, o.y));
+    Sx.z += gsum(g, w * fmaf(d.z, t, o.z));
+    St += gsum(g, w * t);
+    Sn.x += gsum(g, w * nj.x);
+    Sn.y += gsum(g, w * nj.y);
+    Sn.z += gsum(g, w * nj.z);
+    Sa.x += gsum(g, w * alb.x);
+    Sa.y += gsum(g, w * alb.y);
+    Sa.z += gsum(g, w * alb.z);
+    Sm += gsum(g, w * mtl);
+    Sr += gsum(g, w * rgh);
+    T = gshfl(g, Ta, lastc);
+    hits += lastc + 1;
+    stop_key = gshfl(g, kb.bk, lastc);
+    done = stopm != 0u || n < WIDE;
+    if (!done) {
+      last = kb.kmax;
+      if (round == P.max_rounds - 1 && g.c == 0) report(status, LF_ERR_ROUND_LIMIT);
+    }
+  }
+  if (g.c == 0) composited += (unsigned)hits;
+  const float inv = 1.0f / (W + P.eps_w);
+  s.T = T;
+  s.W = W;
+  s.x = Sx * inv;
+  s.depth = St * inv;
+  s.a = Sa * inv;
+  s.Sa = Sa;
+  s.m = Sm * inv;
+  s.r = Sr * inv;
+  const float3 mv = Sn * inv;
+  s.nlen = sqrtf(dot3(mv, mv));
+  s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
+  s.hits = hits;
+  s.stop_key = stop_key;
+}
+
 }  // namespace lf

@@ -26,7 +26,6 @@
 namespace lf {
 
 constexpr int WB = 128;  // threads per block of the wavefront kernels
-constexpr int WSTACK_SMEM = WB * STACK * (int)sizeof(int);
 // Minimum resident blocks per SM asked of the compiler (caps registers).
 #ifndef WF_MIN_BLOCKS_SHADOW
 #define WF_MIN_BLOCKS_SHADOW 1
@@ -163,17 +162,6 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
   }
 }
 
-// ---------------------------------------------------------------- ray fetch
-// The trace kernels run a persistent grid (as many blocks as fit on the GPU)
-// and hand rays out to whole warps through a per-kernel cursor: a warp that
-// has finished its 32 rays takes the next 32 without waiting for the other
-// warps of its block.  No block barrier sits in the ray loop.
-__device__ __forceinline__ int warp_fetch(int* cursor) {
-  int base = 0;
-  if ((threadIdx.x & 31) == 0) base = atomicAdd(cursor, 32);
-  return __shfl_sync(0xffffffffu, base, 0);
-}
-
 // ---------------------------------------------------------------- shadow rays
 // which = 0: NEE rays of queue A (origin from the G-buffer, direction we)
 // which = 1: secondary NEE rays of queue C (entry = item * 2 + q)
@@ -241,51 +229,62 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
 }
 
 // ---------------------------------------------------------------- continuation rays
+// WIDE lanes per ray: cooperative k-buffer composite of the continuation ray
+// to the secondary record (lf_coop.cuh); lanes 0 and 1 then draw the two
+// environment NEE samples there and the group appends their shadow rays.
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S,
                                                                             int* status,
                                                                             unsigned long long* counters) {
-  extern __shared__ int s_stack[];
+  extern __shared__ int s_cstack[];
+  const Grp g = make_grp();
+  const CStack st = group_stack(s_cstack);
   const int n = S.counts[1];
   Counters cnt;
   unsigned comp = 0;
-  for (int base = warp_fetch(S.counts + CURSOR_B); base < n; base = warp_fetch(S.counts + CURSOR_B)) {
-    const int k = base + (threadIdx.x & 31);
-    const long long item = k < n ? (long long)S.qB[k] : 0;
-    bool push0 = false, push1 = false;
-    if (k < n) {
-      const ShadeJob& J = B.jobs[job_of_item(B, item)];
-      const long long loc = item - J.item0;
-      const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
-      const float3 xs = pix_origin(J, p, P.ray_offset);
-      const float3 wi = ld3(S.wi, item);
-      Surface s2;
-      trace_composite(J.insts, J.n_inst, xs, wi, P, s_stack + threadIdx.x, WB, status, cnt, s2, comp);
-      S.T2[item] = s2.T;
-      if (s2.hits > 0) {
+  for (int k = group_fetch(g, S.counts + CURSOR_B); k < n; k = group_fetch(g, S.counts + CURSOR_B)) {
+    const long long item = S.qB[k];
+    const ShadeJob& J = B.jobs[job_of_item(B, item)];
+    const long long loc = item - J.item0;
+    const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+    const float3 xs = pix_origin(J, p, P.ray_offset);
+    const float3 wi = ld3(S.wi, item);
+    Surface s2;
+    coop_composite(g, J.insts, J.n_inst, xs, wi, P, st, status, cnt, s2, comp);
+    if (g.c == 0) S.T2[item] = s2.T;
+    if (s2.hits > 0) {  // uniform over the group
+      bool ok = false;
+      if (g.c < 2) {
+        const int qq = g.c;
         const float3 n2 = s2.n, wo2 = -wi;
         const float co2 = dot3(n2, wo2);
-        st3(S.xs2, item, s2.x + n2 * P.ray_offset);
         const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
         const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
-        const float uq[4] = {unit24(gb.y), unit24(gb.z), unit24(gb.w), unit24(gc.x)};
-#pragma unroll
-        for (int qq = 0; qq < 2; ++qq) {
-          float3 wq;
-          float pq;
-          env_sample(J.env, uq[2 * qq], uq[2 * qq + 1], wq, pq);
-          const float cq = dot3(n2, wq);
-          const bool ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
-          float3 fk = f3(0.f, 0.f, 0.f);
-          if (ok) fk = brdf_eval(n2, wo2, wq, s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f / pq);
-          if (qq == 0) { st3(S.wq0, item, wq); st3(S.fk0, item, fk); push0 = ok; }
-          else { st3(S.wq1, item, wq); st3(S.fk1, item, fk); push1 = ok; }
+        const float u1 = qq == 0 ? unit24(gb.y) : unit24(gb.w);
+        const float u2 = qq == 0 ? unit24(gb.z) : unit24(gc.x);
+        float3 wq;
+        float pq;
+        env_sample(J.env, u1, u2, wq, pq);
+        const float cq = dot3(n2, wq);
+        ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
+        float3 fk = f3(0.f, 0.f, 0.f);
+        if (ok) fk = brdf_eval(n2, wo2, wq, s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f / pq);
+        if (qq == 0) {
+          st3(S.xs2, item, s2.x + n2 * P.ray_offset);
+          st3(S.wq0, item, wq);
+          st3(S.fk0, item, fk);
+        } else {
+          st3(S.wq1, item, wq);
+          st3(S.fk1, item, fk);
         }
       }
+      const unsigned m = gballot(g, ok);
+      int base = 0;
+      if (g.c == 0 && m) base = atomicAdd(S.counts + 2, __popc(m));
+      base = gshfl(g, base, 0);
+      if (ok) S.qC[base + __popc(m & ((1u << g.c) - 1u))] = (int)(item * 2 + g.c);
     }
-    queue_push(S.qC, S.counts + 2, (int)(item * 2), push0);
-    queue_push(S.qC, S.counts + 2, (int)(item * 2 + 1), push1);
   }
-  if (counters) {  // slot 2: continuation rays
+  if (counters && g.c == 0) {  // slot 2: continuation rays
     atomicAdd(counters + 8, (unsigned long long)cnt.nodes);
     atomicAdd(counters + 9, (unsigned long long)cnt.tests);
     atomicAdd(counters + 10, (unsigned long long)comp);
@@ -507,7 +506,7 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
   k_wf_shadow<<<resident_grid(k_wf_shadow, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
       B, P, S, 0, status, counters);
   mark(2);
-  k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms, WSTACK_SMEM, WB), WB, WSTACK_SMEM, st>>>(
+  k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
       B, P, S, status, counters);
   mark(3);
   k_wf_shadow<<<resident_grid(k_wf_shadow, 2 * B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
