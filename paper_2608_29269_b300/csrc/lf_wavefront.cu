@@ -28,10 +28,10 @@ namespace lf {
 constexpr int WB = 128;  // threads per block of the wavefront kernels
 // Minimum resident blocks per SM asked of the compiler (caps registers).
 #ifndef WF_MIN_BLOCKS_SHADOW
-#define WF_MIN_BLOCKS_SHADOW 1
+#define WF_MIN_BLOCKS_SHADOW 10
 #endif
 #ifndef WF_MIN_BLOCKS_CONTINUE
-#define WF_MIN_BLOCKS_CONTINUE 4
+#define WF_MIN_BLOCKS_CONTINUE 6
 #endif
 // Slots of SampleBuf::counts: queue lengths A, B, C (0-2); fetch cursors of
 // the three trace kernels (4-6).
