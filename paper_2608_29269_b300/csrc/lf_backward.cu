@@ -6,19 +6,16 @@
 // surfel parameters; its upstream gradients are those of the G-buffer
 // channels plus the shading adjoint's record gradients (normal, base colour,
 // metallic, roughness, final transmittance).
+#include "lf_coop.cuh"
 #include "lf_kernels.h"
 
 namespace lf {
 
 constexpr int TB = 128;
-constexpr int STACK_SMEM = TB * STACK * (int)sizeof(int);
-
-__device__ __forceinline__ void load_instances_b(Inst* dst, const Inst* src, int n) {
-  const float4* s = reinterpret_cast<const float4*>(src);
-  float4* d = reinterpret_cast<float4*>(dst);
-  for (int i = threadIdx.x; i < n * (int)(sizeof(Inst) / sizeof(float4)); i += blockDim.x) d[i] = s[i];
-  __syncthreads();
-}
+constexpr int BGROUPS = TB / WIDE;  // pixels per block (one per lane group)
+constexpr int BSTACK_SMEM = BGROUPS * CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float));
+constexpr int BTILE_W = BGROUPS >= 4 ? 4 : BGROUPS;
+constexpr int BTILE_H = BGROUPS / BTILE_W;
 
 // d_env += v at the four bilinear texels of direction w.
 __device__ __forceinline__ void env_scatter_p(const EnvDev& e, float* __restrict__ d_env, float3 w, float3 v) {
@@ -77,16 +74,25 @@ __device__ __forceinline__ void surfel_adjoint(const SceneDev& sc, int id, float
   atomicAdd(o17 + 16, g_r);
 }
 
+// WIDE lanes per pixel.  Each round collects the K hits just in front of the
+// bound (cooperative far k-buffer, descending over the lanes), then processes
+// them at once: with P_c = prod_{i <= c} (1 - alpha_i) over the lanes,
+// T_c = T_in / P_c, and the running sum S of the later hits' gw w is an
+// exclusive prefix sum; each lane scatters its own hit's adjoint.
 __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
                                                        const float* __restrict__ gbuf,
                                                        const float* __restrict__ sg,
                                                        const float* __restrict__ gg, float* __restrict__ d_surfel,
                                                        float* __restrict__ d_env) {
-  __shared__ Inst s_inst[LF_MAX_OBJECTS];
-  extern __shared__ int s_stack[];
-  load_instances_b(s_inst, a.insts, a.n_inst);
-  const int x = blockIdx.x * 16 + (threadIdx.x & 15), y = blockIdx.y * 8 + (threadIdx.x >> 4);
-  if (x >= cam.W || y >= cam.H) return;
+  extern __shared__ int s_cstack[];
+  const Grp g = make_grp();
+  const int gid = threadIdx.x / WIDE;
+  CStack st;
+  st.code = s_cstack + gid * CSTACK;
+  st.cnt = s_cstack + BGROUPS * CSTACK + gid * CSTACK;
+  st.t = reinterpret_cast<float*>(s_cstack + 2 * BGROUPS * CSTACK) + gid * CSTACK;
+  const int x = blockIdx.x * BTILE_W + gid % BTILE_W, y = blockIdx.y * BTILE_H + gid / BTILE_W;
+  if (x >= cam.W || y >= cam.H) return;  // uniform over the group
   const int p = y * cam.W + x;
   const size_t P = (size_t)cam.W * cam.H;
   const DevParams& Pm = a.P;
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   if (gg) {
     const float3 Ed = env_lookup(a.env, d);
     g_T += dot3(g_rho, Ed);
-    env_scatter_p(a.env, d_env, d, g_rho * T);
+    if (g.c == 0) env_scatter_p(a.env, d_env, d, g_rho * T);
   }
   if (hits <= 0) return;
   const float inv = 1.0f / (W + Pm.eps_w);
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   unsigned long long bound = ((unsigned long long)__float_as_uint(ch(LF_CH_TSTOP)) << 32) |
                              (unsigned long long)__float_as_uint(ch(LF_CH_STOPKEY_LO));
   bool inclusive = true;
-  FarK kb;
+  FarKCoop kb;
   kb.o = o;
   kb.d = d;
   kb.P = Pm;
@@ -146,38 +152,60 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
   Counters cnt;
   for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
     kb.reset(bound, inclusive);
-    traverse(s_inst, a.n_inst, ray, kb, s_stack + threadIdx.x, TB, a.status, cnt);
+    coop_traverse(g, a.insts, a.n_inst, ray, kb, st, a.status, cnt);
     const int n = kb.cnt;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      if (j < n && remaining > 0) {
-        const int code = kb.bc[j];
-        const Inst& I = s_inst[code >> 24];
-        const int l = code & 0xffffff;
-        const Rec rc = load_rec(I.geo, l);
-        const float4 mt = __ldg(I.mat + l);
-        float t, tl, alpha;
-        hit_precise(rc, o, d, Pm, t, tl, alpha);
-        const float3 nj = record_normal(rc, d);
-        const float3 xj = o + d * t;
-        const float Tj = Tn / (1.0f - alpha);
-        const float w = Tj * alpha;
-        const float gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y +
-                         gSa.z * mt.z + gSm * mt.w + gSr * rc.g2.w;
-        const float g_alpha = Tj * gw - S / (1.0f - alpha);
-        S += gw * w;
-        Tn = Tj;
-        surfel_adjoint(sc, __float_as_int(rc.g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
-                       gSr * w, d_surfel);
-        --remaining;
-      }
+    const int take = min(n, remaining);
+    const bool have = g.c < take;
+    float alpha = 0.0f, t = 0.0f, gw = 0.0f;
+    Rec rc;
+    float4 mt = make_float4(0.f, 0.f, 0.f, 0.f);
+    float3 nj = f3(0.f, 0.f, 0.f);
+    if (have) {
+      const Inst& I = a.insts[kb.bc >> 24];
+      const int l = kb.bc & 0xffffff;
+      rc = load_rec(I.geo, l);
+      mt = __ldg(I.mat + l);
+      float tl;
+      hit_precise(rc, o, d, Pm, t, tl, alpha);
+      nj = record_normal(rc, d);
+      const float3 xj = o + d * t;
+      gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y + gSa.z * mt.z +
+           gSm * mt.w + gSr * rc.g2.w;
     }
+    // P_c = prod_{i <= c} (1 - alpha_i): T_c = Tn / P_c
+    float q = have ? 1.0f - alpha : 1.0f;
+#pragma unroll
+    for (int off = 1; off < WIDE; off <<= 1) {
+      const float v = __shfl_up_sync(g.mask, q, off, WIDE);
+      if (g.c >= off) q *= v;
+    }
+    const float Tj = Tn / q;
+    const float w = have ? Tj * alpha : 0.0f;
+    // S before this hit: S_in + sum over the lanes in front (exclusive prefix sum of gw w)
+    float e = have ? gw * w : 0.0f;
+    float incl = e;
+#pragma unroll
+    for (int off = 1; off < WIDE; off <<= 1) {
+      const float v = __shfl_up_sync(g.mask, incl, off, WIDE);
+      if (g.c >= off) incl += v;
+    }
+    if (have) {
+      const float Sj = S + (incl - e);
+      const float g_alpha = Tj * gw - Sj / (1.0f - alpha);
+      surfel_adjoint(sc, __float_as_int(rc.g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
+                     gSr * w, d_surfel);
+    }
+    if (take > 0) {
+      S += gshfl(g, incl, take - 1);
+      Tn = gshfl(g, Tj, take - 1);
+    }
+    remaining -= take;
     if (remaining > 0) {
-      if (n < K) {  // the forward composited more hits than the re-traversal finds
-        report(a.status, LF_ERR_ROUND_LIMIT);
+      if (n < WIDE) {  // the forward composited more hits than the re-traversal finds
+        if (g.c == 0) report(a.status, LF_ERR_ROUND_LIMIT);
         break;
       }
-      bound = kb.bk[K - 1];
+      bound = kb.kmin;
       inclusive = false;
     }
   }
@@ -186,8 +214,8 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
                                   const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
                                   cudaStream_t st) {
-  dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
-  k_trace_backward<<<grid, TB, STACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env);
+  dim3 grid((cam.W + BTILE_W - 1) / BTILE_W, (cam.H + BTILE_H - 1) / BTILE_H);
+  k_trace_backward<<<grid, TB, BSTACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env);
   return cudaGetLastError();
 }
 

@@ -21,13 +21,9 @@
 
 namespace lf {
 
-constexpr int K = LF_KBUF;
-// Children per wide BVH node = lanes per ray in the cooperative traversal.
-#ifndef LF_WIDE
-#define LF_WIDE 16
-#endif
-constexpr int WIDE = LF_WIDE;
-constexpr int STACK = LF_STACK_DEPTH;
+// Children per wide BVH node = lanes per ray in the cooperative traversal =
+// hits per k-buffer round.
+constexpr int WIDE = LF_KBUF;
 constexpr float PI_F = 3.14159265358979323846f;
 constexpr float INV_PI_F = 0.318309886183790671538f;
 constexpr float INV_2PI_F = 0.159154943091895335769f;
@@ -489,235 +485,8 @@ struct Counters {
 };
 
 // Stack entries name (instance, node or leaf): instance << 25 | leaf flag
-// (bit 24) | index; -1 is "empty".
+// (bit 24) | index.
 constexpr int LEAF_BIT = 1 << 24;
-__device__ __forceinline__ int entry_of(int ii, int child) {
-  return child >= 0 ? ((ii << 25) | child) : ((ii << 25) | LEAF_BIT | ~child);
-}
-
-// Depth-first traversal of the BLASes of every instance whose box the ray
-// enters, on one shared-memory stack, organised "while-while" (Aila and Laine
-// 2009): each lane descends internal nodes until it holds a leaf, then the
-// lanes of the warp process their leaves together.  The visitor supplies the
-// culling interval [tlo(), thi()], consumes leaves and may end the ray early.
-// `stack` points at this thread's first entry; entries are `stride` ints apart.
-//
-// The walk is resumable: trav_begin sets up a ray, each trav_step runs one
-// descent to a leaf plus that leaf's test, so a kernel can interleave rays of
-// different ages on the lanes of a warp (refilling lanes whose ray ended).
-struct TravState {
-  int sp;      // stack depth
-  int ent;     // entry to process next; < 0: none
-  int budget;  // node visits left (guards against a malformed tree)
-};
-
-template <class V>
-__device__ __forceinline__ void trav_begin(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
-                                           int stride, int* status, TravState& st) {
-  int sp = 0;
-  // A tree of n leaves has n - 1 internal nodes; a depth-first walk visits
-  // each node at most once.
-  int budget = 8;
-  for (int ii = 0; ii < n_inst; ++ii) {  // instance 0 (background) is pushed first, popped last
-    const Inst& I = insts[ii];
-    if (I.root == INT_MIN) continue;
-    float tn;
-    if (!slab(I.lo[0], I.lo[1], I.lo[2], I.hi[0], I.hi[1], I.hi[2], ray, vis.tlo(), vis.thi(), tn)) continue;
-    if (sp >= STACK) {
-      report(status, LF_ERR_STACK);
-      vis.abort();
-      st.sp = 0;
-      st.ent = -1;
-      st.budget = 0;
-      return;
-    }
-    stack[(sp++) * stride] = entry_of(ii, I.root);
-    budget += 2 * I.n_leaves + 2;
-  }
-  st.ent = sp > 0 ? stack[(--sp) * stride] : -1;
-  st.sp = sp;
-  st.budget = budget;
-}
-
-// One descent to the next leaf and its test.  Returns false once the ray has
-// nothing left to visit (or the visitor ended it, or the walk failed).
-template <class V>
-__device__ __forceinline__ bool trav_step(const Inst* insts, const Ray& ray, V& vis, int* stack, int stride,
-                                          int* status, Counters& cnt, TravState& st) {
-  int e = st.ent, sp = st.sp, budget = st.budget;
-  while (e >= 0 && !(e & LEAF_BIT)) {
-    if (--budget < 0 || sp >= STACK) {
-      report(status, LF_ERR_STACK);
-      vis.abort();
-      st.ent = -1;
-      return false;
-    }
-    ++cnt.nodes;
-    const int ii = e >> 25;
-    const float4* N = insts[ii].nodes + 4 * (e & 0xffffff);
-    const float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), f = __ldg(N + 3);
-    const float lo = vis.tlo(), hi = vis.thi();
-    float tl, tr;
-    const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, ray, lo, hi, tl);
-    const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, ray, lo, hi, tr);
-    const int cl = entry_of(ii, __float_as_int(f.x)), cr = entry_of(ii, __float_as_int(f.y));
-    if (hl && hr) {
-      const bool lfirst = tl <= tr;
-      stack[(sp++) * stride] = lfirst ? cr : cl;
-      e = lfirst ? cl : cr;
-    } else if (hl) {
-      e = cl;
-    } else if (hr) {
-      e = cr;
-    } else {
-      e = sp > 0 ? stack[(--sp) * stride] : -1;
-    }
-  }
-  if (e < 0) {
-    st.ent = -1;
-    return false;
-  }
-  ++cnt.tests;
-  const int ii = e >> 25;
-  vis.leaf(ii, e & 0xffffff, insts[ii]);
-  if (vis.done()) {
-    st.ent = -1;
-    return false;
-  }
-  st.ent = sp > 0 ? stack[(--sp) * stride] : -1;
-  st.sp = sp;
-  st.budget = budget;
-  return st.ent >= 0;
-}
-
-template <class V>
-__device__ __forceinline__ void traverse(const Inst* insts, int n_inst, const Ray& ray, V& vis, int* stack,
-                                         int stride, int* status, Counters& cnt) {
-  TravState st;
-  trav_begin(insts, n_inst, ray, vis, stack, stride, status, st);
-  while (trav_step(insts, ray, vis, stack, stride, status, cnt, st)) {
-  }
-}
-
-// Collects the K smallest hit keys strictly greater than the last round's.
-struct NearK {
-  unsigned long long bk[K];
-  int bc[K];
-  int cnt;
-  unsigned long long last;
-  float3 o, d;
-  DevParams P;
-
-  __device__ __forceinline__ void reset(unsigned long long lk) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) { bk[j] = ~0ull; bc[j] = 0; }
-    cnt = 0;
-    last = lk;
-  }
-  __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, key_t(last)); }
-  __device__ __forceinline__ float thi() const { return cnt >= K ? key_t(bk[K - 1]) : BIG_F; }
-  __device__ __forceinline__ bool done() const { return false; }
-  __device__ __forceinline__ void abort() { cnt = 0; }
-  __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
-    const Rec r = load_rec(I.geo, l);
-    float t32;
-    if (!hit_quick(r, o, d, P, t32)) return;
-    if (cnt >= K && t32 > thi() * 1.0001f + 1e-6f) return;  // beyond the window (FP32 depth, safe margin)
-    float t, tl, alpha;
-    if (!hit_precise(r, o, d, P, t, tl, alpha)) return;
-    const unsigned long long key = hit_key(t, tl, __float_as_int(r.g1.w));
-    if (key <= last || (cnt >= K && key >= bk[K - 1])) return;
-    int p = 0;
-#pragma unroll
-    for (int j = 0; j < K; ++j) p += bk[j] < key ? 1 : 0;
-#pragma unroll
-    for (int j = K - 1; j > 0; --j)
-      if (j > p) { bk[j] = bk[j - 1]; bc[j] = bc[j - 1]; }
-    const int code = (ii << 24) | l;
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-      if (j == p) { bk[j] = key; bc[j] = code; }
-    cnt = min(cnt + 1, K);
-  }
-};
-
-// Collects the K largest hit keys below a bound (inclusive on the first round).
-struct FarK {
-  unsigned long long bk[K];
-  int bc[K];
-  int cnt;
-  unsigned long long bound;
-  bool inclusive;
-  float3 o, d;
-  DevParams P;
-
-  __device__ __forceinline__ void reset(unsigned long long b, bool incl) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) { bk[j] = 0ull; bc[j] = 0; }
-    cnt = 0;
-    bound = b;
-    inclusive = incl;
-  }
-  __device__ __forceinline__ float tlo() const { return cnt >= K ? fmaxf(P.t_min, key_t(bk[K - 1])) : P.t_min; }
-  __device__ __forceinline__ float thi() const { return key_t(bound); }
-  __device__ __forceinline__ bool done() const { return false; }
-  __device__ __forceinline__ void abort() { cnt = 0; }
-  __device__ __forceinline__ void leaf(int ii, int l, const Inst& I) {
-    const Rec r = load_rec(I.geo, l);
-    float t32;
-    if (!hit_quick(r, o, d, P, t32)) return;
-    if (t32 > thi() * 1.0001f + 1e-6f) return;
-    float t, tl, alpha;
-    if (!hit_precise(r, o, d, P, t, tl, alpha)) return;
-    const unsigned long long key = hit_key(t, tl, __float_as_int(r.g1.w));
-    if (key > bound || (key == bound && !inclusive)) return;
-    if (cnt >= K && key <= bk[K - 1]) return;
-    int p = 0;  // entries with a larger key come first
-#pragma unroll
-    for (int j = 0; j < K; ++j) p += bk[j] > key ? 1 : 0;
-#pragma unroll
-    for (int j = K - 1; j > 0; --j)
-      if (j > p) { bk[j] = bk[j - 1]; bc[j] = bc[j - 1]; }
-    const int code = (ii << 24) | l;
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-      if (j == p) { bk[j] = key; bc[j] = code; }
-    cnt = min(cnt + 1, K);
-  }
-};
-
-// Shadow ray: V = prod(1 - alpha~) over all accepted hits; 0 once below T_min.
-struct ShadowV {
-  float V;
-  bool stop;
-  float3 o, d;
-  DevParams P;
-  __device__ __forceinline__ float tlo() const { return P.t_min; }
-  __device__ __forceinline__ float thi() const { return BIG_F; }
-  __device__ __forceinline__ bool done() const { return stop; }
-  __device__ __forceinline__ void abort() { stop = true; }
-  __device__ __forceinline__ void leaf(int, int l, const Inst& I) {
-    const Rec r = load_rec(I.geo, l);
-    float t, tl, alpha;
-    if (!hit_surfel(r, o, d, P, t, tl, alpha)) return;
-    V *= (1.0f - alpha);
-    if (V < P.T_min) { V = 0.0f; stop = true; }
-  }
-};
-
-__device__ __forceinline__ float trace_shadow(const Inst* insts, int n_inst, float3 o, float3 d,
-                                              const DevParams& P, int* stack, int stride, int* status,
-                                              Counters& cnt) {
-  ShadowV v;
-  v.V = 1.0f;
-  v.stop = false;
-  v.o = o;
-  v.d = d;
-  v.P = P;
-  Ray ray = make_ray(o, d);
-  traverse(insts, n_inst, ray, v, stack, stride, status, cnt);
-  return v.V;
-}
 
 // Composited surface record of one ray (Eq. 7).
 struct Surface {
@@ -727,71 +496,5 @@ struct Surface {
   int hits;
   unsigned long long stop_key;  // key of the last composited hit (0: none)
 };
-
-// Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop).
-__device__ __forceinline__ void trace_composite(const Inst* insts, int n_inst, float3 o, float3 d,
-                                                const DevParams& P, int* stack, int stride, int* status,
-                                                Counters& cnt, Surface& s, unsigned& composited) {
-  NearK kb;
-  kb.o = o;
-  kb.d = d;
-  kb.P = P;
-  Ray ray = make_ray(o, d);
-  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
-  float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
-  int hits = 0;
-  unsigned long long stop_key = 0ull, last = 0ull;
-  bool done = false;
-  for (int round = 0; round < P.max_rounds && !done; ++round) {
-    kb.reset(last);
-    traverse(insts, n_inst, ray, kb, stack, stride, status, cnt);
-    const int n = kb.cnt;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      if (j < n && !done) {
-        const int code = kb.bc[j];
-        const Inst& I = insts[code >> 24];
-        const int l = code & 0xffffff;
-        const Rec rc = load_rec(I.geo, l);
-        const float4 mt = __ldg(I.mat + l);
-        float t, tl, alpha;
-        hit_precise(rc, o, d, P, t, tl, alpha);
-        const float3 nj = record_normal(rc, d);
-        const float w = T * alpha;
-        W += w;
-        add3(Sx, (o + d * t) * w);
-        St += w * t;
-        add3(Sn, nj * w);
-        add3(Sa, f3(mt.x, mt.y, mt.z) * w);
-        Sm += w * mt.w;
-        Sr += w * rc.g2.w;
-        T *= (1.0f - alpha);
-        ++hits;
-        stop_key = kb.bk[j];
-        if (T < P.T_min) done = true;
-      }
-    }
-    if (!done && n < K) done = true;
-    if (!done) {
-      last = kb.bk[K - 1];
-      if (round == P.max_rounds - 1) report(status, LF_ERR_ROUND_LIMIT);
-    }
-  }
-  composited += (unsigned)hits;
-  const float inv = 1.0f / (W + P.eps_w);
-  s.T = T;
-  s.W = W;
-  s.x = Sx * inv;
-  s.depth = St * inv;
-  s.a = Sa * inv;
-  s.Sa = Sa;
-  s.m = Sm * inv;
-  s.r = Sr * inv;
-  const float3 mv = Sn * inv;
-  s.nlen = sqrtf(dot3(mv, mv));
-  s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
-  s.hits = hits;
-  s.stop_key = stop_key;
-}
 
 }  // namespace lf

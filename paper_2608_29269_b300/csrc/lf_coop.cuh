@@ -13,7 +13,7 @@
 
 namespace lf {
 
-constexpr int CSTACK = 128;  // stack entries per ray (each node visit pushes at most WIDE - 1)
+constexpr int CSTACK = LF_STACK_DEPTH;  // stack entries per ray (a node visit pushes at most WIDE - 1)
 static_assert(WIDE == 8 || WIDE == 16 || WIDE == 32, "WIDE must be 8, 16 or 32");
 
 // The lanes of one ray.
@@ -244,6 +244,77 @@ struct NearKCoop {
       if (cnt >= WIDE) {
         kmax = gshfl(g, bk, WIDE - 1);
         kth = key_t(kmax);
+      }
+    }
+  }
+};
+
+// Cooperative far k-buffer for the back-to-front adjoint: the K largest hit
+// keys below a bound (inclusive on the first round), sorted descending over
+// the lanes (lane c holds entry c; 0 = empty).
+struct FarKCoop {
+  unsigned long long bk;
+  int bc;
+  int cnt;
+  unsigned long long bound;
+  bool inclusive;
+  unsigned long long kmin;  // smallest held key once full
+  float ktl;                // key_t(kmin) once full, else t_min
+  float3 o, d;
+  DevParams P;
+
+  __device__ __forceinline__ void reset(unsigned long long b, bool incl) {
+    bk = 0ull;
+    bc = 0;
+    cnt = 0;
+    bound = b;
+    inclusive = incl;
+    kmin = 0ull;
+    ktl = P.t_min;
+  }
+  __device__ __forceinline__ float tlo() const { return ktl; }
+  __device__ __forceinline__ float thi() const { return key_t(bound); }
+  __device__ __forceinline__ bool done() const { return false; }
+  __device__ __forceinline__ void abort() { cnt = 0; }
+  __device__ __forceinline__ void leaf(const Grp& g, int ii, int first, int count, const Inst& I) {
+    bool valid = false;
+    unsigned long long key = 0ull;
+    int code = 0;
+    if (g.c < count) {
+      const int l = first + g.c;
+      const Rec r = load_rec(I.geo, l);
+      float t32;
+      if (hit_quick(r, o, d, P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
+        float t, tl, alpha;
+        if (hit_precise(r, o, d, P, t, tl, alpha)) {
+          key = hit_key(t, tl, __float_as_int(r.g1.w));
+          valid = (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
+          code = (ii << 24) | l;
+        }
+      }
+    }
+    unsigned m = gballot(g, valid);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1u;
+      const unsigned long long k = gshfl(g, key, src);
+      const int cd = gshfl(g, code, src);
+      if (cnt >= WIDE && k <= kmin) continue;
+      const unsigned long long pk = __shfl_up_sync(g.mask, bk, 1, WIDE);
+      const int pc = __shfl_up_sync(g.mask, bc, 1, WIDE);
+      if (bk < k) {
+        if (g.c == 0 || pk > k) {
+          bk = k;
+          bc = cd;
+        } else {
+          bk = pk;
+          bc = pc;
+        }
+      }
+      cnt = min(cnt + 1, WIDE);
+      if (cnt >= WIDE) {
+        kmin = gshfl(g, bk, WIDE - 1);
+        ktl = fmaxf(P.t_min, key_t(kmin));
       }
     }
   }
