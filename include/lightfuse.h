@@ -38,7 +38,7 @@ extern "C" {
 
 #define LF_MAX_OBJECTS 64
 #define LF_MAX_ENVS 16     /* environment map slots                              */
-#define LF_KBUF 16         /* hits per k-buffer round = children per wide BVH node = lanes per ray */
+#define LF_KBUF 32         /* hits per k-buffer round = children per wide BVH node = lanes per ray */
 #define LF_STACK_DEPTH 128 /* traversal stack entries per ray (shared memory)                    */
 
 typedef enum {
