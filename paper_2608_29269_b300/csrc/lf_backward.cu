@@ -13,7 +13,7 @@ namespace lf {
 
 constexpr int TB = 128;
 constexpr int BGROUPS = TB / WIDE;  // pixels per block (one per lane group)
-constexpr int BSTACK_SMEM = BGROUPS * CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float));
+constexpr int BSTACK_SMEM = BGROUPS * CRAY_SMEM;
 constexpr int BTILE_W = BGROUPS >= 4 ? 4 : BGROUPS;
 constexpr int BTILE_H = BGROUPS / BTILE_W;
 
@@ -84,13 +84,10 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
                                                        const float* __restrict__ sg,
                                                        const float* __restrict__ gg, float* __restrict__ d_surfel,
                                                        float* __restrict__ d_env) {
-  extern __shared__ int s_cstack[];
+  extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const int gid = threadIdx.x / WIDE;
-  CStack st;
-  st.code = s_cstack + gid * CSTACK;
-  st.cnt = s_cstack + BGROUPS * CSTACK + gid * CSTACK;
-  st.t = reinterpret_cast<float*>(s_cstack + 2 * BGROUPS * CSTACK) + gid * CSTACK;
+  const CStack st = ray_smem(reinterpret_cast<unsigned char*>(s_cstack), BGROUPS, gid);
   const int x = blockIdx.x * BTILE_W + gid % BTILE_W, y = blockIdx.y * BTILE_H + gid / BTILE_W;
   if (x >= cam.W || y >= cam.H) return;  // uniform over the group
   const int p = y * cam.W + x;

@@ -41,12 +41,35 @@ __device__ __forceinline__ T gshfl(const Grp& g, T v, int src) {
   return __shfl_sync(g.mask, v, src, WIDE);
 }
 
-// Per-ray stack (three parallel arrays in shared memory).
+// Per-ray shared memory: the traversal stack (three parallel arrays) and
+// the k-buffer's merge scratch (WIDE entries).
 struct CStack {
   int* code;
   int* cnt;
   float* t;
+  unsigned long long* mk;
+  int* mc;
+  float* ma;
 };
+
+// Bytes of shared memory per ray.
+constexpr int CRAY_SMEM = CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float)) +
+                          WIDE * ((int)sizeof(unsigned long long) + (int)sizeof(int) + (int)sizeof(float));
+
+// Carves ray `gid`'s arrays out of a block's shared memory holding n_rays rays.
+__device__ __forceinline__ CStack ray_smem(unsigned char* smem, int n_rays, int gid) {
+  CStack st;
+  unsigned long long* mk = reinterpret_cast<unsigned long long*>(smem);
+  st.mk = mk + gid * WIDE;
+  int* ints = reinterpret_cast<int*>(mk + n_rays * WIDE);
+  st.code = ints + gid * CSTACK;
+  st.cnt = ints + n_rays * CSTACK + gid * CSTACK;
+  st.mc = ints + 2 * n_rays * CSTACK + gid * WIDE;
+  float* fl = reinterpret_cast<float*>(ints + 2 * n_rays * CSTACK + n_rays * WIDE);
+  st.t = fl + gid * CSTACK;
+  st.ma = fl + n_rays * CSTACK + gid * WIDE;
+  return st;
+}
 
 // Stack entries name (instance, wide node or leaf) as in the binary
 // traversal: instance << 25 | leaf flag (bit 24) | index; the leaf's surfel
@@ -179,42 +202,58 @@ struct ShadowCoop {
 };
 
 // Cooperative k-buffer (K = WIDE): the K smallest hit keys strictly greater
-// than the last round's, sorted over the lanes (lane c holds entry c).  A
-// candidate is inserted by every lane at once: lanes below its rank keep their
-// entry, the lane at its rank takes it, the lanes above take their lower
-// neighbour's entry (the largest falls off a full buffer).
+// than the last round's, sorted over the lanes (lane c holds entry c with its
+// opacity alpha~).  A leaf's accepted candidates are merged in one step: every
+// element's place in the merged order is its own index plus the number of
+// smaller elements of the other list (counted with one ballot per
+// candidate), elements are scattered to those places in shared memory and
+// read back; places beyond K fall off.
+//
+// Transmittance cut: with T the transmittance in front of the round, the
+// composite of the sorted buffer stops at the first entry s with
+// T prod_{i <= s} (1 - alpha_i) < T_min.  Hits found later can only enter
+// in front of s, which moves the stop forward, so nothing beyond entry s is
+// ever composited and the far bound of the traversal drops to its depth.
 struct NearKCoop {
   unsigned long long bk;    // this lane's entry (~0: empty)
   int bc;                   // its hit code: instance << 24 | leaf
+  float ba;                 // its alpha~
   int cnt;                  // entries held
   unsigned long long last;  // keys must exceed this
   unsigned long long kmax;  // largest held key once full
-  float kth;                // key_t(kmax) once full, else BIG_F
+  float Tin;                // transmittance in front of this round's hits
+  float tcut;               // far bound: the stop entry's depth, else kmax's once full, else BIG_F
   float3 o, d;
   DevParams P;
+  unsigned long long* mk;   // merge scratch in shared memory (WIDE entries per ray)
+  int* mc;
+  float* ma;
 
-  __device__ __forceinline__ void reset(unsigned long long lk) {
+  __device__ __forceinline__ void reset(unsigned long long lk, float T) {
     bk = ~0ull;
     bc = 0;
+    ba = 0.0f;
     cnt = 0;
     last = lk;
     kmax = ~0ull;
-    kth = BIG_F;
+    Tin = T;
+    tcut = BIG_F;
   }
   __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, key_t(last)); }
-  __device__ __forceinline__ float thi() const { return kth; }
+  __device__ __forceinline__ float thi() const { return tcut; }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
   __device__ __forceinline__ void leaf(const Grp& g, int ii, int first, int count, const Inst& I) {
     bool valid = false;
     unsigned long long key = 0ull;
     int code = 0;
+    float alpha = 0.0f;
     if (g.c < count) {
       const int l = first + g.c;
       const Rec r = load_rec(I.geo, l);
       float t32;
-      if (hit_quick(r, o, d, P, t32) && !(cnt >= WIDE && t32 > kth * 1.0001f + 1e-6f)) {
-        float t, tl, alpha;
+      if (hit_quick(r, o, d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f)) {
+        float t, tl;
         if (hit_precise(r, o, d, P, t, tl, alpha)) {
           key = hit_key(t, tl, __float_as_int(r.g1.w));
           valid = key > last && (cnt < WIDE || key < kmax);
@@ -222,30 +261,45 @@ struct NearKCoop {
         }
       }
     }
-    unsigned m = gballot(g, valid);
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1u;
-      const unsigned long long k = gshfl(g, key, src);
-      const int cd = gshfl(g, code, src);
-      if (cnt >= WIDE && k >= kmax) continue;  // an earlier insertion lowered the bound
-      const unsigned long long pk = __shfl_up_sync(g.mask, bk, 1, WIDE);
-      const int pc = __shfl_up_sync(g.mask, bc, 1, WIDE);
-      if (bk > k) {
-        if (g.c == 0 || pk < k) {
-          bk = k;
-          bc = cd;
-        } else {
-          bk = pk;
-          bc = pc;
-        }
-      }
-      cnt = min(cnt + 1, WIDE);
-      if (cnt >= WIDE) {
-        kmax = gshfl(g, bk, WIDE - 1);
-        kth = key_t(kmax);
-      }
+    const unsigned m = gballot(g, valid);
+    if (m == 0u) return;
+    int bshift = 0, cshift = 0, rb = 0;
+    for (unsigned mm = m; mm; mm &= mm - 1u) {
+      const int j = __ffs(mm) - 1;
+      const unsigned long long kj = gshfl(g, key, j);
+      const unsigned below = gballot(g, bk < kj);
+      if (g.c == j) rb = __popc(below);
+      bshift += bk > kj ? 1 : 0;
+      cshift += (valid && key > kj) ? 1 : 0;
     }
+    const int db = g.c + bshift, dc = rb + cshift;
+    if (db < WIDE) {
+      mk[db] = bk;
+      mc[db] = bc;
+      ma[db] = ba;
+    }
+    if (valid && dc < WIDE) {
+      mk[dc] = key;
+      mc[dc] = code;
+      ma[dc] = alpha;
+    }
+    __syncwarp(g.mask);
+    bk = mk[g.c];
+    bc = mc[g.c];
+    ba = ma[g.c];
+    __syncwarp(g.mask);
+    cnt = min(cnt + __popc(m), WIDE);
+    if (cnt >= WIDE) kmax = gshfl(g, bk, WIDE - 1);
+    // transmittance cut over the sorted buffer
+    float q = g.c < cnt ? 1.0f - ba : 1.0f;
+#pragma unroll
+    for (int off = 1; off < WIDE; off <<= 1) {
+      const float v = __shfl_up_sync(g.mask, q, off, WIDE);
+      if (g.c >= off) q *= v;
+    }
+    const unsigned stop = gballot(g, g.c < cnt && Tin * q < P.T_min);
+    if (stop) tcut = key_t(gshfl(g, bk, __ffs(stop) - 1));
+    else if (cnt >= WIDE) tcut = key_t(kmax);
   }
 };
 
@@ -340,6 +394,9 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   kb.o = o;
   kb.d = d;
   kb.P = P;
+  kb.mk = st.mk;
+  kb.mc = st.mc;
+  kb.ma = st.ma;
   const Ray ray = make_ray(o, d);
   float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
   float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
@@ -347,24 +404,26 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   unsigned long long stop_key = 0ull, last = 0ull;
   bool done = false;
   for (int round = 0; round < P.max_rounds && !done; ++round) {
-    kb.reset(last);
+    kb.reset(last, T);
     coop_traverse(g, insts, n_inst, ray, kb, st, status, cnt);
     const int n = kb.cnt;
     if (n == 0) break;
     const bool have = g.c < n;
-    float alpha = 0.0f, t = 0.0f, mtl = 0.0f, rgh = 0.0f;
+    // depth and alpha~ of each entry as the hit test computed them
+    const float alpha = have ? kb.ba : 0.0f, t = have ? key_t(kb.bk) : 0.0f;
+    float mtl = 0.0f, rgh = 0.0f;
     float3 nj = f3(0.f, 0.f, 0.f), alb = nj;
     if (have) {
       const Inst& I = insts[kb.bc >> 24];
       const int l = kb.bc & 0xffffff;
-      const Rec rc = load_rec(I.geo, l);
+      const float4* gr = I.geo + GEO * l;
+      const float4 g2 = __ldg(gr + 2), g3 = __ldg(gr + 3);
       const float4 mt = __ldg(I.mat + l);
-      float tl;
-      hit_precise(rc, o, d, P, t, tl, alpha);
-      nj = record_normal(rc, d);
+      const float3 nh = f3(g3.x, g3.y, g3.z);
+      nj = dot3(d, nh) < 0.0f ? nh : -nh;
       alb = f3(mt.x, mt.y, mt.z);
       mtl = mt.w;
-      rgh = rc.g2.w;
+      rgh = g2.w;
     }
     // inclusive prefix product of (1 - alpha) over the lanes
     float q = have ? 1.0f - alpha : 1.0f;

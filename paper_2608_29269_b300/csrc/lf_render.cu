@@ -6,20 +6,17 @@ namespace lf {
 
 constexpr int TB = 128;                      // threads per block
 constexpr int RGROUPS = TB / WIDE;           // pixels per block (one per lane group)
-constexpr int RSTACK_SMEM = RGROUPS * CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float));
+constexpr int RSTACK_SMEM = RGROUPS * CRAY_SMEM;
 constexpr int TILE_W = RGROUPS >= 4 ? 4 : RGROUPS;  // a block's pixels form a TILE_W x TILE_H tile
 constexpr int TILE_H = RGROUPS / TILE_W;
 
 // WIDE lanes per pixel: cooperative k-buffer composite of the primary ray
 // (lf_coop.cuh); lane 0 writes the G-buffer.
 __global__ void __launch_bounds__(TB) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
-  extern __shared__ int s_cstack[];
+  extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const int gid = threadIdx.x / WIDE;
-  CStack st;
-  st.code = s_cstack + gid * CSTACK;
-  st.cnt = s_cstack + RGROUPS * CSTACK + gid * CSTACK;
-  st.t = reinterpret_cast<float*>(s_cstack + 2 * RGROUPS * CSTACK) + gid * CSTACK;
+  const CStack st = ray_smem(reinterpret_cast<unsigned char*>(s_cstack), RGROUPS, gid);
   const int x = blockIdx.x * TILE_W + gid % TILE_W, y = blockIdx.y * TILE_H + gid / TILE_W;
   if (x >= cam.W || y >= cam.H) return;  // uniform over the group
   const int p = y * cam.W + x;

@@ -168,15 +168,10 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
 // WIDE lanes trace each ray through the wide BVH (lf_coop.cuh); a group takes
 // the next queue entry as soon as its ray has ended.
 constexpr int WGROUPS = WB / WIDE;  // rays per block in the cooperative kernels
-constexpr int CSTACK_SMEM = WGROUPS * CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float));
+constexpr int CSTACK_SMEM = WGROUPS * CRAY_SMEM;
 
 __device__ __forceinline__ CStack group_stack(int* smem) {
-  const int gid = threadIdx.x / WIDE;
-  CStack st;
-  st.code = smem + gid * CSTACK;
-  st.cnt = smem + WGROUPS * CSTACK + gid * CSTACK;
-  st.t = reinterpret_cast<float*>(smem + 2 * WGROUPS * CSTACK) + gid * CSTACK;
-  return st;
+  return ray_smem(reinterpret_cast<unsigned char*>(smem), WGROUPS, threadIdx.x / WIDE);
 }
 
 // Next queue entry for the group (one atomic per ray).
@@ -189,7 +184,7 @@ __device__ __forceinline__ int group_fetch(const Grp& g, int* cursor) {
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S,
                                                                         int which, int* status,
                                                                         unsigned long long* counters) {
-  extern __shared__ int s_cstack[];
+  extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const CStack st = group_stack(s_cstack);
   const int* q = which == 0 ? S.qA : S.qC;
@@ -235,7 +230,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S,
                                                                             int* status,
                                                                             unsigned long long* counters) {
-  extern __shared__ int s_cstack[];
+  extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const CStack st = group_stack(s_cstack);
   const int n = S.counts[1];
