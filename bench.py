@@ -444,6 +444,13 @@ def main():
     dom = max(per_ray_io, key=lambda n: kavg[n])
     achieved = kbytes[dom] / (kavg[dom] * 1e-3) / 1e9
     traffic = read_traffic(KERNEL_NAMES[dom])
+    # the working set sits in L2: L2 bytes of the same kernel (ncu) against the L2 read bandwidth measured here
+    l2_peak = step.tr.measure_l2_read()
+    l2_bytes = read_traffic(KERNEL_NAMES[dom], "l2_bytes_per_launch")
+    l2 = {"peak": l2_peak, "unit": "GB/s", "peak_kind": "measured in this run (ld.global.cg read loop over 32 MB)",
+          "bytes_per_launch": l2_bytes,
+          "achieved": l2_bytes / (kavg[dom] * 1e-3) / 1e9 if l2_bytes else None,
+          "frac": l2_bytes / (kavg[dom] * 1e-3) / 1e9 / l2_peak if l2_bytes else None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -455,7 +462,7 @@ def main():
         "phase_ms": {n: round(v, 3) for n, v in avg.items()},
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy (burst)", "traffic": traffic,
-                     "algorithmic_bytes_per_launch": kbytes[dom], "launch_ms": kavg[dom]},
+                     "algorithmic_bytes_per_launch": kbytes[dom], "launch_ms": kavg[dom], "l2": l2},
         "kernels": kernels,
         "counters": dict(counters, fields=["node visits", "surfel tests", "composited hits", "rays"],
                          node_bytes=node_bytes),
@@ -507,16 +514,16 @@ KERNEL_NAMES = {"primary": "k_trace_primary", "nee_shadow": "k_wf_shadow (NEE)",
                 "continuation": "k_wf_continue", "secondary_shadow": "k_wf_shadow (secondary)"}
 
 
-def read_traffic(kernel):
-    """DRAM bytes per launch of `kernel` at the bench workload, from the committed
-    ncu summary, when it was taken on the current kernel sources."""
+def read_traffic(kernel, field="dram_bytes_per_launch"):
+    """DRAM (or L2) bytes per launch of `kernel` at the bench workload, from the
+    committed ncu summary, when it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         if t.get("sources_sha") != sources_sha():
             return None
-        return t.get("dram_bytes_per_launch", {}).get(kernel)
+        return t.get(field, {}).get(kernel)
     except Exception:
         return None
 

@@ -279,6 +279,15 @@ lf_status lf_set_counters(lf_ctx* ctx, unsigned long long* counters_dev);
 lf_status lf_profile(lf_ctx* ctx, int enable);
 lf_status lf_profile_read(lf_ctx* ctx, float* ms6);
 
+/*
+ * Measurement helper (no counterpart in the paper): read bandwidth of the L2
+ * cache in GB/s, from `reps` passes of float4 loads cached at L2 only over a
+ * device buffer of `bytes` (at least 1 MiB; keep it well below the L2 size),
+ * after one warm-up pass.  Allocates and frees its own buffer; synchronises
+ * the context's stream.
+ */
+lf_status lf_measure_l2_read(lf_ctx* ctx, size_t bytes, int reps, float* gbs);
+
 /* Philox4x32-10 of n counters (device n x 4 words) with key (k0, k1). */
 lf_status lf_philox(lf_ctx* ctx, const uint32_t* ctr_dev, int n, uint32_t k0, uint32_t k1, uint32_t* out_dev);
 

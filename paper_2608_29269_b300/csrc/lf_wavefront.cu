@@ -31,7 +31,7 @@ constexpr int WB = 128;  // threads per block of the wavefront kernels
 #define WF_MIN_BLOCKS_SHADOW 10
 #endif
 #ifndef WF_MIN_BLOCKS_CONTINUE
-#define WF_MIN_BLOCKS_CONTINUE 6
+#define WF_MIN_BLOCKS_CONTINUE 8
 #endif
 // Slots of SampleBuf::counts: queue lengths A, B, C (0-2); fetch cursors of
 // the three trace kernels (4-6).

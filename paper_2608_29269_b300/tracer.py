@@ -225,6 +225,12 @@ class Tracer:
         self.check(self.lib.lf_profile_read(self.ctx, ms))
         return list(ms)
 
+    def measure_l2_read(self, nbytes: int = 32 << 20, reps: int = 40) -> float:
+        """L2 read bandwidth in GB/s (a measurement helper)."""
+        gbs = C.c_float()
+        self.check(self.lib.lf_measure_l2_read(self.ctx, C.c_size_t(int(nbytes)), int(reps), C.byref(gbs)))
+        return float(gbs.value)
+
     def philox(self, ctr: torch.Tensor, k0: int, k1: int) -> torch.Tensor:
         out = torch.empty_like(ctr)
         self.check(self.lib.lf_philox(self.ctx, _ptr(ctr), ctr.shape[0], C.c_uint32(k0), C.c_uint32(k1), _ptr(out)))
