@@ -142,8 +142,6 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
                              (unsigned long long)__float_as_uint(ch(LF_CH_STOPKEY_LO));
   bool inclusive = true;
   FarKCoop kb;
-  kb.o = o;
-  kb.d = d;
   kb.P = Pm;
   const Ray ray = make_ray(o, d);
   Counters cnt;

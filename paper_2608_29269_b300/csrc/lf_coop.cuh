@@ -80,7 +80,7 @@ __device__ __forceinline__ int wentry(int ii, int code) {
 
 // Visitor interface (all members group-uniform except inside leaf()):
 //   tlo(), thi()  culling interval of the ray
-//   leaf(g, ii, first, count, I)  lanes c < count handle surfel first + c
+//   leaf(g, ray, ii, first, count, I)  lanes c < count handle surfel first + c
 //   done(), abort()
 template <class V>
 __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, int n_inst, const Ray& ray, V& vis,
@@ -130,7 +130,7 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
       const Inst& I = insts[ii];
       if (e & LEAF_BIT) {
         if (g.c == 0) cnt.tests += ec;
-        vis.leaf(g, ii, e & 0xffffff, ec, I);
+        vis.leaf(g, ray, ii, e & 0xffffff, ec, I);
         if (vis.done()) return;
         break;
       }
@@ -178,18 +178,17 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
 struct ShadowCoop {
   float V;
   bool stop;
-  float3 o, d;
   DevParams P;
   __device__ __forceinline__ float tlo() const { return P.t_min; }
   __device__ __forceinline__ float thi() const { return BIG_F; }
   __device__ __forceinline__ bool done() const { return stop; }
   __device__ __forceinline__ void abort() { stop = true; }
-  __device__ __forceinline__ void leaf(const Grp& g, int, int first, int count, const Inst& I) {
+  __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int, int first, int count, const Inst& I) {
     float f = 1.0f;
     if (g.c < count) {
       const Rec r = load_rec(I.geo, first + g.c);
       float t, tl, alpha;
-      if (hit_surfel(r, o, d, P, t, tl, alpha)) f = 1.0f - alpha;
+      if (hit_surfel(r, ray.o, ray.d, P, t, tl, alpha)) f = 1.0f - alpha;
     }
 #pragma unroll
     for (int off = WIDE / 2; off > 0; off >>= 1) f *= __shfl_xor_sync(g.mask, f, off, WIDE);
@@ -223,7 +222,6 @@ struct NearKCoop {
   unsigned long long kmax;  // largest held key once full
   float Tin;                // transmittance in front of this round's hits
   float tcut;               // far bound: the stop entry's depth, else kmax's once full, else BIG_F
-  float3 o, d;
   DevParams P;
   unsigned long long* mk;   // merge scratch in shared memory (WIDE entries per ray)
   int* mc;
@@ -243,7 +241,7 @@ struct NearKCoop {
   __device__ __forceinline__ float thi() const { return tcut; }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
-  __device__ __forceinline__ void leaf(const Grp& g, int ii, int first, int count, const Inst& I) {
+  __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
     bool valid = false;
     unsigned long long key = 0ull;
     int code = 0;
@@ -252,9 +250,9 @@ struct NearKCoop {
       const int l = first + g.c;
       const Rec r = load_rec(I.geo, l);
       float t32;
-      if (hit_quick(r, o, d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f)) {
+      if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f)) {
         float t, tl;
-        if (hit_precise(r, o, d, P, t, tl, alpha)) {
+        if (hit_precise(r, ray.o, ray.d, P, t, tl, alpha)) {
           key = hit_key(t, tl, __float_as_int(r.g1.w));
           valid = key > last && (cnt < WIDE || key < kmax);
           code = (ii << 24) | l;
@@ -314,7 +312,6 @@ struct FarKCoop {
   bool inclusive;
   unsigned long long kmin;  // smallest held key once full
   float ktl;                // key_t(kmin) once full, else t_min
-  float3 o, d;
   DevParams P;
 
   __device__ __forceinline__ void reset(unsigned long long b, bool incl) {
@@ -330,7 +327,7 @@ struct FarKCoop {
   __device__ __forceinline__ float thi() const { return key_t(bound); }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
-  __device__ __forceinline__ void leaf(const Grp& g, int ii, int first, int count, const Inst& I) {
+  __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
     bool valid = false;
     unsigned long long key = 0ull;
     int code = 0;
@@ -338,9 +335,9 @@ struct FarKCoop {
       const int l = first + g.c;
       const Rec r = load_rec(I.geo, l);
       float t32;
-      if (hit_quick(r, o, d, P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
+      if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
         float t, tl, alpha;
-        if (hit_precise(r, o, d, P, t, tl, alpha)) {
+        if (hit_precise(r, ray.o, ray.d, P, t, tl, alpha)) {
           key = hit_key(t, tl, __float_as_int(r.g1.w));
           valid = (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
           code = (ii << 24) | l;
@@ -391,8 +388,6 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
                                                const DevParams& P, const CStack& st, int* status, Counters& cnt,
                                                Surface& s, unsigned& composited) {
   NearKCoop kb;
-  kb.o = o;
-  kb.d = d;
   kb.P = P;
   kb.mk = st.mk;
   kb.mc = st.mc;

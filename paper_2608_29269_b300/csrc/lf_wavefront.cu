@@ -197,17 +197,18 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     ShadowCoop v;
     v.P = P;
+    float3 o, d;
     if (which == 0) {
       const long long loc = item - J.item0;
-      v.o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
-      v.d = ld3(S.we, item);
+      o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+      d = ld3(S.we, item);
     } else {
-      v.o = ld3(S.xs2, item);
-      v.d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
+      o = ld3(S.xs2, item);
+      d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
     }
     v.V = 1.0f;
     v.stop = false;
-    const Ray ray = make_ray(v.o, v.d);
+    const Ray ray = make_ray(o, d);
     coop_traverse(g, J.insts, J.n_inst, ray, v, st, status, cnt);
     if (g.c == 0) {
       if (which == 0) S.Ve[item] = v.V;
