@@ -297,8 +297,8 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     if (e == cudaSuccess) e = dev_alloc(&c->vals_alt, cap);
     if (e == cudaSuccess) e = dev_alloc(&c->counts, 256 * tiles);
     if (e == cudaSuccess) e = dev_alloc(&c->node_range, cap);
-    // wide nodes: sum over objects of wide_capacity(n_k) <= 2 cap / (WIDE - 1) + 2 LF_MAX_OBJECTS
-    const size_t wcap = 2 * cap / (WIDE - 1) + 2 * LF_MAX_OBJECTS;
+    // wide nodes: the sum over objects of wide_capacity(n_k) is at most wide_capacity(cap) + 2 LF_MAX_OBJECTS
+    const size_t wcap = (size_t)wide_capacity((int)std::min<size_t>(cap, 1u << 30)) + 2 * LF_MAX_OBJECTS;
     if (e == cudaSuccess) e = dev_alloc(&c->wnodes, 2 * WIDE * wcap);
     if (e == cudaSuccess) e = dev_alloc(&c->wsrc, WIDE * wcap);
     if (e == cudaSuccess) e = dev_alloc(&c->wqueue, wcap);
@@ -341,8 +341,8 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     I.id_base = c->offsets[k];
     I.pad = 0;
     I.wnodes = c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k];
-    I.wroot = nk > WIDE ? 0 : (nk >= 1 ? ~0 : INT_MIN);
-    I.wroot_count = nk > WIDE ? 0 : nk;
+    I.wroot = nk > WLEAF ? 0 : (nk >= 1 ? ~0 : INT_MIN);
+    I.wroot_count = nk > WLEAF ? 0 : nk;
   }
   LF_CUDA(c, cudaMemcpyAsync(c->insts_dev, c->insts_h.data(), sizeof(Inst) * n_obj, cudaMemcpyHostToDevice,
                              c->stream));

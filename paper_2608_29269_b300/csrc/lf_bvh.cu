@@ -329,13 +329,14 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
 // nodes are traversed by WIDE lanes at once (one child slot per lane).  A wide
 // node starts from a binary node's two children and repeatedly replaces the
 // child with the most leaves by its own two children, while fewer than WIDE
-// children are held and that child has more than WIDE leaves.  A child with
-// at most WIDE leaves becomes a leaf slot (its surfels are consecutive in leaf
-// order); a larger one becomes a wide node of its own.  The rule depends on
-// leaf counts only, so the wide topology is fixed by the build and a refit
+// children are held and that child has more than WLEAF leaves.  A child with
+// at most WLEAF leaves becomes a leaf slot (its surfels are consecutive in
+// leaf order); a larger one becomes a wide node of its own.  The rule depends
+// on leaf counts only, so the wide topology is fixed by the build and a refit
 // only copies boxes (k_wide_boxes).  A wide node that is not full holds only
-// leaf slots and covers more than WIDE surfels, which bounds the node count by
-// 2n / (WIDE - 1) + 2 per object.
+// leaf slots and covers more than WLEAF surfels; with I nodes, at most
+// n / (WLEAF + 1) of them not full and n leaf slots, I (WIDE - 1) <= n +
+// (WIDE - 2) n / (WLEAF + 1), the capacity wide_capacity() allocates.
 //
 // Topology: one block per object, level by level (breadth first); children
 // get consecutive indices in item order (block-wide scan), so the layout is
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
   __shared__ int s_scan[COLLAPSE_THREADS];
   const int obj = a.first_obj + blockIdx.x;
   const int n = a.leaf_off[obj + 1] - a.leaf_off[obj];
-  if (n <= WIDE) return;  // the root is a leaf slot held by the instance
+  if (n <= WLEAF) return;  // the root is a leaf slot held by the instance
   const int nb = a.node_off[obj];                      // binary nodes, global numbering (ranges)
   const int wb = a.wnode_off[obj];                     // wide nodes, global numbering
   const int cap = a.wnode_off[obj + 1] - wb;
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
         while (nc < WIDE) {
           int best = -1;
           for (int c = 0; c < nc; ++c)
-            if (code[c] >= 0 && cnt[c] > WIDE && (best < 0 || cnt[c] > cnt[best])) best = c;
+            if (code[c] >= 0 && cnt[c] > WLEAF && (best < 0 || cnt[c] > cnt[best])) best = c;
           if (best < 0) break;
           const int e = code[best];
           const float4 g = bnodes[4 * e + 3];
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
           code[nc] = er; src[nc] = 2 * e + 1; cnt[nc] = er >= 0 ? a.node_range[nb + er].y : 1;
           ++nc;
         }
-        for (int c = 0; c < nc; ++c) n_int += (code[c] >= 0 && cnt[c] > WIDE) ? 1 : 0;
+        for (int c = 0; c < nc; ++c) n_int += (code[c] >= 0 && cnt[c] > WLEAF) ? 1 : 0;
       }
       // exclusive scan of n_int over the chunk (item order)
       s_scan[threadIdx.x] = n_int;
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
           int cd = INT_MIN, ct = 0, sr = -1;
           if (c < nc) {
             sr = src[c];
-            if (code[c] >= 0 && cnt[c] > WIDE) {
+            if (code[c] >= 0 && cnt[c] > WLEAF) {
               cd = next;
               queue[next++] = code[c];
             } else {

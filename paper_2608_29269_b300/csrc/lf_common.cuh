@@ -24,6 +24,12 @@ namespace lf {
 // Children per wide BVH node = lanes per ray in the cooperative traversal =
 // hits per k-buffer round.
 constexpr int WIDE = LF_KBUF;
+// Surfels at most in one leaf slot of the wide BVH.
+#ifndef LF_WIDE_LEAF
+#define LF_WIDE_LEAF LF_KBUF
+#endif
+constexpr int WLEAF = LF_WIDE_LEAF;
+static_assert(WLEAF >= 1 && WLEAF <= WIDE, "a leaf is tested by at most WIDE lanes");
 constexpr float PI_F = 3.14159265358979323846f;
 constexpr float INV_PI_F = 0.318309886183790671538f;
 constexpr float INV_2PI_F = 0.159154943091895335769f;

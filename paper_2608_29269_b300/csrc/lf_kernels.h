@@ -52,7 +52,11 @@ struct WideArgs {
 };
 
 // Wide nodes an object of n surfels can need.
-inline int wide_capacity(int n) { return n > WIDE ? 2 * n / (WIDE - 1) + 2 : 0; }
+inline int wide_capacity(int n) {
+  if (n <= WLEAF) return 0;
+  const long long nn = n;
+  return (int)((nn * (WLEAF + 1) + (long long)(WIDE - 2) * nn) / ((long long)(WIDE - 1) * (WLEAF + 1)) + 2);
+}
 
 struct InstPtrs {
   const Inst* p[LF_MAX_OBJECTS];
