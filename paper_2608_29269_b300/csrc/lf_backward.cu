@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
       nj = record_normal(rc, d);
       const float3 xj = o + d * t;
       gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y + gSa.z * mt.z +
-           gSm * mt.w + gSr * rc.g2.w;
+           gSm * mt.w + gSr * rec_rough(rc);
     }
     // P_c = prod_{i <= c} (1 - alpha_i): T_c = Tn / P_c
     float q = have ? 1.0f - alpha : 1.0f;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
     if (have) {
       const float Sj = S + (incl - e);
       const float g_alpha = Tj * gw - Sj / (1.0f - alpha);
-      surfel_adjoint(sc, __float_as_int(rc.g1.w), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
+      surfel_adjoint(sc, rec_id(rc), o, d, Pm, g_alpha, gSx * w, gSt * w, gSn * w, gSa * w, gSm * w,
                      gSr * w, d_surfel);
     }
     if (take > 0) {

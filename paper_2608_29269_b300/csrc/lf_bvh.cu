@@ -286,10 +286,12 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
   const double cx = (double)tu.y * tv.z - (double)tu.z * tv.y, cy = (double)tu.z * tv.x - (double)tu.x * tv.z,
                cz = (double)tu.x * tv.y - (double)tu.y * tv.x;
   const double cl = sqrt(cx * cx + cy * cy + cz * cz);
-  a.geo[GEO * Lw + 0] = make_float4(mu.x, mu.y, mu.z, s.opacity[i]);
-  a.geo[GEO * Lw + 1] = make_float4(tu.x / su, tu.y / su, tu.z / su, __int_as_float(id));
-  a.geo[GEO * Lw + 2] = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, s.roughness[i]);
-  a.geo[GEO * Lw + 3] = make_float4((float)(cx / cl), (float)(cy / cl), (float)(cz / cl), 0.0f);
+  const float3 nh = f3((float)(cx / cl), (float)(cy / cl), (float)(cz / cl));
+  const float3 ax = f3(tu.x / su, tu.y / su, tu.z / su), bx = f3(tv.x / sv, tv.y / sv, tv.z / sv);
+  a.geo[GEO * Lw + 0] = make_float4(mu.x, mu.y, mu.z, nh.x);
+  a.geo[GEO * Lw + 1] = make_float4(nh.y, nh.z, ax.x, ax.y);
+  a.geo[GEO * Lw + 2] = make_float4(ax.z, bx.x, bx.y, bx.z);
+  a.geo[GEO * Lw + 3] = make_float4(s.opacity[i], __int_as_float(id), s.roughness[i], 0.0f);
   a.mat[Lw] = make_float4(s.albedo[3 * i], s.albedo[3 * i + 1], s.albedo[3 * i + 2], s.metallic[i]);
   float3 lo, hi;
   surfel_box(s, i, a.R, lo, hi);

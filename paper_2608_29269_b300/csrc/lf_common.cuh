@@ -1,11 +1,10 @@
 // Device-side building blocks of the surfel ray tracer (sm_103a).
 //
 // Record layouts (library-owned, in BVH leaf order per object):
-//   geo[4*l+0] = (mu.xyz, opacity)
-//   geo[4*l+1] = (tu/s_u .xyz, surfel id as int bits)
-//   geo[4*l+2] = (tv/s_v .xyz, roughness)
-//   geo[4*l+3] = (n^.xyz, 0)  unit normal tu x tv, normalised in FP64 then rounded,
-//                so that exactly coplanar axis-aligned surfels get exactly equal t
+//   geo[4*l+0] = (mu.xyz, n^.x)        n^ = unit normal tu x tv, normalised in FP64
+//   geo[4*l+1] = (n^.yz, a.xy)         then rounded, so that exactly coplanar
+//   geo[4*l+2] = (a.z, b.xyz)          axis-aligned surfels get exactly equal t;
+//   geo[4*l+3] = (opacity, id bits, roughness, 0)   a = tu/s_u, b = tv/s_v
 //   mat[l]     = (albedo.rgb, metallic)
 //   BVH2 node (64 B, child boxes stored in the parent):
 //     n0 = (L.lo.xyz, L.hi.x)  n1 = (L.hi.yz, R.lo.xy)  n2 = (R.lo.z, R.hi.xyz)
@@ -136,12 +135,31 @@ __device__ __forceinline__ void sample_uniforms(uint32_t pixel, uint32_t s, uint
 // ------------------------------------------------------------------ Eq. 6
 constexpr int GEO = 4;  // float4 per packed surfel record
 
+// Packed record: the first three quads are what the quick plane test reads
+// (centre, normal, both scaled axes); the fourth (opacity, id, roughness) is
+// read only for candidates that pass it.
 struct Rec {
   float4 g0, g1, g2, g3;
 };
-__device__ __forceinline__ Rec load_rec(const float4* geo, int l) {
+__device__ __forceinline__ float3 rec_mu(const Rec& r) { return f3(r.g0.x, r.g0.y, r.g0.z); }
+__device__ __forceinline__ float3 rec_n(const Rec& r) { return f3(r.g0.w, r.g1.x, r.g1.y); }
+__device__ __forceinline__ float3 rec_a(const Rec& r) { return f3(r.g1.z, r.g1.w, r.g2.x); }
+__device__ __forceinline__ float3 rec_b(const Rec& r) { return f3(r.g2.y, r.g2.z, r.g2.w); }
+__device__ __forceinline__ float rec_opacity(const Rec& r) { return r.g3.x; }
+__device__ __forceinline__ int rec_id(const Rec& r) { return __float_as_int(r.g3.y); }
+__device__ __forceinline__ float rec_rough(const Rec& r) { return r.g3.z; }
+__device__ __forceinline__ void load_rec3(const float4* geo, int l, Rec& r) {
   const float4* g = geo + GEO * l;
-  return Rec{__ldg(g), __ldg(g + 1), __ldg(g + 2), __ldg(g + 3)};
+  r.g0 = __ldg(g);
+  r.g1 = __ldg(g + 1);
+  r.g2 = __ldg(g + 2);
+}
+__device__ __forceinline__ void load_rec_tail(const float4* geo, int l, Rec& r) { r.g3 = __ldg(geo + GEO * l + 3); }
+__device__ __forceinline__ Rec load_rec(const float4* geo, int l) {
+  Rec r;
+  load_rec3(geo, l, r);
+  load_rec_tail(geo, l, r);
+  return r;
 }
 
 // Error-free transformations: TwoSum (Knuth) and TwoProd via FMA.
@@ -187,7 +205,7 @@ __device__ __forceinline__ void dot2(float3 ah, float3 al, float3 b, float& hi, 
 // on FP32 rounding.
 __device__ __forceinline__ bool hit_quick(const Rec& r, const float3 o, const float3 d, const DevParams& P,
                                           float& t32) {
-  const float3 a = f3(r.g1.x, r.g1.y, r.g1.z), b = f3(r.g2.x, r.g2.y, r.g2.z), nh = f3(r.g3.x, r.g3.y, r.g3.z);
+  const float3 a = rec_a(r), b = rec_b(r), nh = rec_n(r);
   const float3 p = f3(r.g0.x - o.x, r.g0.y - o.y, r.g0.z - o.z);
   t32 = __fdividef(dot3(p, nh), dot3(d, nh));
   if (!(t32 > 0.5f * P.t_min) || !(t32 < BIG_F)) return false;
@@ -198,7 +216,7 @@ __device__ __forceinline__ bool hit_quick(const Rec& r, const float3 o, const fl
 
 __device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const float3 d, const DevParams& P,
                                             float& t, float& tl, float& alpha) {
-  const float3 a = f3(r.g1.x, r.g1.y, r.g1.z), b = f3(r.g2.x, r.g2.y, r.g2.z), nh = f3(r.g3.x, r.g3.y, r.g3.z);
+  const float3 a = rec_a(r), b = rec_b(r), nh = rec_n(r);
   float3 ph, pl;
   two_sum(r.g0.x, -o.x, ph.x, pl.x);
   two_sum(r.g0.y, -o.y, ph.y, pl.y);
@@ -218,14 +236,19 @@ __device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const 
   const float u = dot_rn(q, a), v = dot_rn(q, b);
   const float r2 = __fmaf_rn(u, u, __fmul_rn(v, v));
   if (!(r2 <= P.support_r2)) return false;
-  alpha = fminf(P.alpha_max, __fmul_rn(r.g0.w, expf(__fmul_rn(-0.5f, r2))));
+  alpha = fminf(P.alpha_max, __fmul_rn(rec_opacity(r), expf(__fmul_rn(-0.5f, r2))));
   return alpha >= P.alpha_min;
 }
 
-__device__ __forceinline__ bool hit_surfel(const Rec& r, const float3 o, const float3 d, const DevParams& P,
-                                           float& t, float& tl, float& alpha) {
-  float t32;
-  return hit_quick(r, o, d, P, t32) && hit_precise(r, o, d, P, t, tl, alpha);
+// Full test of record l: the quick test on its first three quads, then the
+// fourth quad and the precise test for a candidate that passes.
+__device__ __forceinline__ bool hit_surfel(const float4* geo, int l, const float3 o, const float3 d,
+                                           const DevParams& P, Rec& r, float& t32, float& t, float& tl,
+                                           float& alpha) {
+  load_rec3(geo, l, r);
+  if (!hit_quick(r, o, d, P, t32)) return false;
+  load_rec_tail(geo, l, r);
+  return hit_precise(r, o, d, P, t, tl, alpha);
 }
 
 // 64-bit sort key of a hit: FP32 depth bits | low depth part quantised to
@@ -241,7 +264,7 @@ __device__ __forceinline__ float key_t(unsigned long long k) { return __uint_as_
 
 // Normal of a packed record facing the ray (two-sided surfels).
 __device__ __forceinline__ float3 record_normal(const Rec& r, const float3 d) {
-  const float3 n = f3(r.g3.x, r.g3.y, r.g3.z);
+  const float3 n = rec_n(r);
   return dot3(d, n) < 0.0f ? n : -n;
 }
 

@@ -186,9 +186,9 @@ struct ShadowCoop {
   __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int, int first, int count, const Inst& I) {
     float f = 1.0f;
     if (g.c < count) {
-      const Rec r = load_rec(I.geo, first + g.c);
-      float t, tl, alpha;
-      if (hit_surfel(r, ray.o, ray.d, P, t, tl, alpha)) f = 1.0f - alpha;
+      Rec r;
+      float t32, t, tl, alpha;
+      if (hit_surfel(I.geo, first + g.c, ray.o, ray.d, P, r, t32, t, tl, alpha)) f = 1.0f - alpha;
     }
 #pragma unroll
     for (int off = WIDE / 2; off > 0; off >>= 1) f *= __shfl_xor_sync(g.mask, f, off, WIDE);
@@ -248,12 +248,14 @@ struct NearKCoop {
     float alpha = 0.0f;
     if (g.c < count) {
       const int l = first + g.c;
-      const Rec r = load_rec(I.geo, l);
+      Rec r;
+      load_rec3(I.geo, l, r);
       float t32;
       if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f)) {
         float t, tl;
+        load_rec_tail(I.geo, l, r);
         if (hit_precise(r, ray.o, ray.d, P, t, tl, alpha)) {
-          key = hit_key(t, tl, __float_as_int(r.g1.w));
+          key = hit_key(t, tl, rec_id(r));
           valid = key > last && (cnt < WIDE || key < kmax);
           code = (ii << 24) | l;
         }
@@ -333,12 +335,14 @@ struct FarKCoop {
     int code = 0;
     if (g.c < count) {
       const int l = first + g.c;
-      const Rec r = load_rec(I.geo, l);
+      Rec r;
+      load_rec3(I.geo, l, r);
       float t32;
       if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
         float t, tl, alpha;
+        load_rec_tail(I.geo, l, r);
         if (hit_precise(r, ray.o, ray.d, P, t, tl, alpha)) {
-          key = hit_key(t, tl, __float_as_int(r.g1.w));
+          key = hit_key(t, tl, rec_id(r));
           valid = (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
           code = (ii << 24) | l;
         }
@@ -412,13 +416,13 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
       const Inst& I = insts[kb.bc >> 24];
       const int l = kb.bc & 0xffffff;
       const float4* gr = I.geo + GEO * l;
-      const float4 g2 = __ldg(gr + 2), g3 = __ldg(gr + 3);
+      const float4 g0 = __ldg(gr), g1 = __ldg(gr + 1), g3 = __ldg(gr + 3);
       const float4 mt = __ldg(I.mat + l);
-      const float3 nh = f3(g3.x, g3.y, g3.z);
+      const float3 nh = f3(g0.w, g1.x, g1.y);
       nj = dot3(d, nh) < 0.0f ? nh : -nh;
       alb = f3(mt.x, mt.y, mt.z);
       mtl = mt.w;
-      rgh = g2.w;
+      rgh = g3.z;
     }
     // inclusive prefix product of (1 - alpha) over the lanes
     float q = have ? 1.0f - alpha : 1.0f;
