@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc,
     if (have) {
       const Inst& I = a.insts[kb.bc >> 24];
       const int l = kb.bc & 0xffffff;
-      rc = load_rec(I.geo, l);
+      rc = load_rec(I.geo, I.n_leaves, l);
       mt = __ldg(I.mat + l);
       float tl;
       hit_precise(rc, o, d, Pm, t, tl, alpha);

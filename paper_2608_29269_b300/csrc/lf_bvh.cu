@@ -288,10 +288,11 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
   const double cl = sqrt(cx * cx + cy * cy + cz * cz);
   const float3 nh = f3((float)(cx / cl), (float)(cy / cl), (float)(cz / cl));
   const float3 ax = f3(tu.x / su, tu.y / su, tu.z / su), bx = f3(tv.x / sv, tv.y / sv, tv.z / sv);
-  a.geo[GEO * Lw + 0] = make_float4(mu.x, mu.y, mu.z, nh.x);
-  a.geo[GEO * Lw + 1] = make_float4(nh.y, nh.z, ax.x, ax.y);
-  a.geo[GEO * Lw + 2] = make_float4(ax.z, bx.x, bx.y, bx.z);
-  a.geo[GEO * Lw + 3] = make_float4(s.opacity[i], __int_as_float(id), s.roughness[i], 0.0f);
+  float4* rec = a.geo + (size_t)GEO * (lb - a.leaf_base) + (L - lb);  // the object's planes of n quads
+  rec[0] = make_float4(mu.x, mu.y, mu.z, nh.x);
+  rec[(size_t)n] = make_float4(nh.y, nh.z, ax.x, ax.y);
+  rec[2 * (size_t)n] = make_float4(ax.z, bx.x, bx.y, bx.z);
+  rec[3 * (size_t)n] = make_float4(s.opacity[i], __int_as_float(id), s.roughness[i], 0.0f);
   a.mat[Lw] = make_float4(s.albedo[3 * i], s.albedo[3 * i + 1], s.albedo[3 * i + 2], s.metallic[i]);
   float3 lo, hi;
   surfel_box(s, i, a.R, lo, hi);
@@ -416,8 +417,8 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
               ct = cnt[c];
             }
           }
-          node[2 * c + 0] = make_float4(1.0f, 1.0f, 1.0f, __int_as_float(cd));
-          node[2 * c + 1] = make_float4(-1.0f, -1.0f, -1.0f, __int_as_float(ct));
+          node[c] = make_float4(1.0f, 1.0f, 1.0f, __int_as_float(cd));
+          node[WIDE + c] = make_float4(-1.0f, -1.0f, -1.0f, __int_as_float(ct));
           wsrc[WIDE * item + c] = sr;
         }
       }
@@ -441,10 +442,11 @@ __global__ void k_wide_boxes(WideArgs a, int n_slots) {
   const int nb = a.node_off[obj] - a.node_base;
   const float* f = reinterpret_cast<const float*>(a.nodes + 4 * (size_t)(nb + (sr >> 1)));
   const int o = (sr & 1) ? 6 : 0;
-  float4* w = a.wnodes + 2 * (size_t)(slot - WIDE * a.wnode_base);
-  const float4 p = w[0], q = w[1];
+  const int local = slot - WIDE * a.wnode_base;  // node * WIDE + c in the storage
+  float4* w = a.wnodes + 2 * (size_t)WIDE * (local / WIDE) + (local % WIDE);
+  const float4 p = w[0], q = w[WIDE];
   w[0] = make_float4(f[o + 0], f[o + 1], f[o + 2], p.w);
-  w[1] = make_float4(f[o + 3], f[o + 4], f[o + 5], q.w);
+  w[WIDE] = make_float4(f[o + 3], f[o + 4], f[o + 5], q.w);
 }
 
 // ---------------------------------------------------------------- rigid transform

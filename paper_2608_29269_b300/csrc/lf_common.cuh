@@ -1,17 +1,18 @@
 // Device-side building blocks of the surfel ray tracer (sm_103a).
 //
-// Record layouts (library-owned, in BVH leaf order per object):
-//   geo[4*l+0] = (mu.xyz, n^.x)        n^ = unit normal tu x tv, normalised in FP64
-//   geo[4*l+1] = (n^.yz, a.xy)         then rounded, so that exactly coplanar
-//   geo[4*l+2] = (a.z, b.xyz)          axis-aligned surfels get exactly equal t;
-//   geo[4*l+3] = (opacity, id bits, roughness, 0)   a = tu/s_u, b = tv/s_v
+// Record layouts (library-owned, in BVH leaf order per object, each quad in
+// its own plane of n quads per object):
+//   geo[0*n+l] = (mu.xyz, n^.x)        n^ = unit normal tu x tv, normalised in FP64
+//   geo[1*n+l] = (n^.yz, a.xy)         then rounded, so that exactly coplanar
+//   geo[2*n+l] = (a.z, b.xyz)          axis-aligned surfels get exactly equal t;
+//   geo[3*n+l] = (opacity, id bits, roughness, 0)   a = tu/s_u, b = tv/s_v
 //   mat[l]     = (albedo.rgb, metallic)
 //   BVH2 node (64 B, child boxes stored in the parent):
 //     n0 = (L.lo.xyz, L.hi.x)  n1 = (L.hi.yz, R.lo.xy)  n2 = (R.lo.z, R.hi.xyz)
 //     n3 = (left code, right code, -, -) ; code >= 0 internal node, code < 0 leaf ~code
-//   Wide node (WIDE child slots of 32 B; slot c read by lane c of a ray's group):
-//     slot = (lo.xyz, code), (hi.xyz, count) ; code >= 0 wide node, code < 0 leaf
-//     of `count` consecutive surfels from ~code, INT_MIN empty (inverted box)
+//   Wide node (WIDE child slots; lane c of a ray's warp reads slot c): WIDE
+//     quads (lo.xyz, code) then WIDE quads (hi.xyz, count); code >= 0 wide
+//     node, code < 0 leaf of `count` consecutive surfels from ~code, INT_MIN empty
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -148,17 +149,21 @@ __device__ __forceinline__ float3 rec_b(const Rec& r) { return f3(r.g2.y, r.g2.z
 __device__ __forceinline__ float rec_opacity(const Rec& r) { return r.g3.x; }
 __device__ __forceinline__ int rec_id(const Rec& r) { return __float_as_int(r.g3.y); }
 __device__ __forceinline__ float rec_rough(const Rec& r) { return r.g3.z; }
-__device__ __forceinline__ void load_rec3(const float4* geo, int l, Rec& r) {
-  const float4* g = geo + GEO * l;
-  r.g0 = __ldg(g);
-  r.g1 = __ldg(g + 1);
-  r.g2 = __ldg(g + 2);
+// An object's records are stored as GEO planes of n quads (quad k of record l
+// at geo[k * n + l]), so the lanes of a warp reading consecutive records
+// read consecutive 16-byte quads.
+__device__ __forceinline__ void load_rec3(const float4* geo, int n, int l, Rec& r) {
+  r.g0 = __ldg(geo + l);
+  r.g1 = __ldg(geo + n + l);
+  r.g2 = __ldg(geo + 2 * n + l);
 }
-__device__ __forceinline__ void load_rec_tail(const float4* geo, int l, Rec& r) { r.g3 = __ldg(geo + GEO * l + 3); }
-__device__ __forceinline__ Rec load_rec(const float4* geo, int l) {
+__device__ __forceinline__ void load_rec_tail(const float4* geo, int n, int l, Rec& r) {
+  r.g3 = __ldg(geo + 3 * n + l);
+}
+__device__ __forceinline__ Rec load_rec(const float4* geo, int n, int l) {
   Rec r;
-  load_rec3(geo, l, r);
-  load_rec_tail(geo, l, r);
+  load_rec3(geo, n, l, r);
+  load_rec_tail(geo, n, l, r);
   return r;
 }
 
@@ -242,12 +247,12 @@ __device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const 
 
 // Full test of record l: the quick test on its first three quads, then the
 // fourth quad and the precise test for a candidate that passes.
-__device__ __forceinline__ bool hit_surfel(const float4* geo, int l, const float3 o, const float3 d,
+__device__ __forceinline__ bool hit_surfel(const float4* geo, int n, int l, const float3 o, const float3 d,
                                            const DevParams& P, Rec& r, float& t32, float& t, float& tl,
                                            float& alpha) {
-  load_rec3(geo, l, r);
+  load_rec3(geo, n, l, r);
   if (!hit_quick(r, o, d, P, t32)) return false;
-  load_rec_tail(geo, l, r);
+  load_rec_tail(geo, n, l, r);
   return hit_precise(r, o, d, P, t, tl, alpha);
 }
 

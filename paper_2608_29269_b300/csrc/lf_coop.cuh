@@ -1,8 +1,8 @@
 // Cooperative traversal of the wide BVH: WIDE consecutive lanes of a warp
 // trace one ray together (sm_103a).
 //
-// At a wide node lane c tests child slot c (one 32-byte slot per lane, so a
-// node is one coalesced 16 * 32 B read), the group continues with the nearest
+// At a wide node lane c tests child slot c (the node's two quad planes make
+// each of its two loads one contiguous WIDE * 16 B read), the group continues with the nearest
 // child it enters and pushes the others on the ray's stack in shared memory;
 // at a leaf lane c tests surfel first + c.  Every branch below is uniform over
 // the group, so the lanes of a ray never diverge from one another and a warp
@@ -140,8 +140,8 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
         return;
       }
       if (g.c == 0) ++cnt.nodes;
-      const float4* slot = I.wnodes + 2 * ((size_t)(e & 0xffffff) * WIDE + g.c);
-      const float4 A = __ldg(slot), Bx = __ldg(slot + 1);
+      const float4* node = I.wnodes + 2 * WIDE * (size_t)(e & 0xffffff);
+      const float4 A = __ldg(node + g.c), Bx = __ldg(node + WIDE + g.c);
       const int code = __float_as_int(A.w), count = __float_as_int(Bx.w);
       float tn = 0.0f;
       const bool hit = code != INT_MIN && slab(A.x, A.y, A.z, Bx.x, Bx.y, Bx.z, ray, vis.tlo(), vis.thi(), tn);
@@ -188,7 +188,7 @@ struct ShadowCoop {
     if (g.c < count) {
       Rec r;
       float t32, t, tl, alpha;
-      if (hit_surfel(I.geo, first + g.c, ray.o, ray.d, P, r, t32, t, tl, alpha)) f = 1.0f - alpha;
+      if (hit_surfel(I.geo, I.n_leaves, first + g.c, ray.o, ray.d, P, r, t32, t, tl, alpha)) f = 1.0f - alpha;
     }
 #pragma unroll
     for (int off = WIDE / 2; off > 0; off >>= 1) f *= __shfl_xor_sync(g.mask, f, off, WIDE);
@@ -249,11 +249,11 @@ struct NearKCoop {
     if (g.c < count) {
       const int l = first + g.c;
       Rec r;
-      load_rec3(I.geo, l, r);
+      load_rec3(I.geo, I.n_leaves, l, r);
       float t32;
       if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f)) {
         float t, tl;
-        load_rec_tail(I.geo, l, r);
+        load_rec_tail(I.geo, I.n_leaves, l, r);
         if (hit_precise(r, ray.o, ray.d, P, t, tl, alpha)) {
           key = hit_key(t, tl, rec_id(r));
           valid = key > last && (cnt < WIDE || key < kmax);
@@ -336,11 +336,11 @@ struct FarKCoop {
     if (g.c < count) {
       const int l = first + g.c;
       Rec r;
-      load_rec3(I.geo, l, r);
+      load_rec3(I.geo, I.n_leaves, l, r);
       float t32;
       if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
         float t, tl, alpha;
-        load_rec_tail(I.geo, l, r);
+        load_rec_tail(I.geo, I.n_leaves, l, r);
         if (hit_precise(r, ray.o, ray.d, P, t, tl, alpha)) {
           key = hit_key(t, tl, rec_id(r));
           valid = (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
@@ -415,8 +415,8 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     if (have) {
       const Inst& I = insts[kb.bc >> 24];
       const int l = kb.bc & 0xffffff;
-      const float4* gr = I.geo + GEO * l;
-      const float4 g0 = __ldg(gr), g1 = __ldg(gr + 1), g3 = __ldg(gr + 3);
+      const int nl = I.n_leaves;
+      const float4 g0 = __ldg(I.geo + l), g1 = __ldg(I.geo + nl + l), g3 = __ldg(I.geo + 3 * nl + l);
       const float4 mt = __ldg(I.mat + l);
       const float3 nh = f3(g0.w, g1.x, g1.y);
       nj = dot3(d, nh) < 0.0f ? nh : -nh;

@@ -237,15 +237,17 @@ class Tracer:
         return out
 
     def bvh_wide(self, object_id: int):
-        """(slots (cap, WIDE, 8) float32, root code, root count): the object's wide BVH storage."""
+        """(slots (cap, WIDE, 8) float32: lo.xyz, code bits, hi.xyz, count bits; root code, root count):
+        the object's wide BVH storage."""
         import numpy as np
         cap, root, rcount, wide = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         self.check(self.lib.lf_bvh_copy_wide(self.ctx, int(object_id), None, 0, C.byref(cap), C.byref(root),
                                              C.byref(rcount), C.byref(wide)))
-        buf = np.zeros((max(1, cap.value), wide.value, 8), np.float32)
+        buf = np.zeros((max(1, cap.value), 2, wide.value, 4), np.float32)  # per node: lo quads, hi quads
         self.check(self.lib.lf_bvh_copy_wide(self.ctx, int(object_id), buf.ctypes.data_as(C.c_void_p), buf.nbytes,
                                              C.byref(cap), C.byref(root), C.byref(rcount), C.byref(wide)))
-        return buf[: cap.value], root.value, rcount.value
+        slots = np.ascontiguousarray(buf.transpose(0, 2, 1, 3)).reshape(-1, wide.value, 8)
+        return slots[: cap.value], root.value, rcount.value
 
     def bvh_nodes(self, object_id: int):
         n_int, root = C.c_int(), C.c_int()
