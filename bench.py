@@ -185,7 +185,7 @@ KERNELS_PER_STEP = {  # launches of this library's kernels in one step
     "env": 2,
     "refit": 2,
     "primary": 1,
-    "shade": 6,  # gen, shadow A, continue, shadow C, count, combine
+    "shade": 7,  # gen, shadow A, continue, secondary sampling, shadow C, count, combine
     "backward": 2,  # combine adjoint, trace backward
 }
 

@@ -79,7 +79,7 @@ __device__ __forceinline__ void surfel_adjoint(const SceneDev& sc, int id, float
 // them at once: with P_c = prod_{i <= c} (1 - alpha_i) over the lanes,
 // T_c = T_in / P_c, and the running sum S of the later hits' gw w is an
 // exclusive prefix sum; each lane scatters its own hit's adjoint.
-__global__ void __launch_bounds__(TB) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
+__global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
                                                        const float* __restrict__ gbuf,
                                                        const float* __restrict__ sg,
                                                        const float* __restrict__ gg, float* __restrict__ d_surfel,

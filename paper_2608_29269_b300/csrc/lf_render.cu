@@ -12,7 +12,7 @@ constexpr int TILE_H = RGROUPS / TILE_W;
 
 // WIDE lanes per pixel: cooperative k-buffer composite of the primary ray
 // (lf_coop.cuh); lane 0 writes the G-buffer.
-__global__ void __launch_bounds__(TB) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
+__global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
   extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const int gid = threadIdx.x / WIDE;

@@ -8,8 +8,9 @@
 //                 continuation rays to queue B.
 //   k_wf_shadow   queue A: visibility V_e of the NEE rays.
 //   k_wf_continue queue B: k-buffer composite of the continuation ray to the
-//                 secondary record; two environment NEE samples there
-//                 (factor f2 cos / pdf, ray origin), appended to queue C.
+//                 secondary record.
+//   k_wf_secondary queue B: two environment NEE samples at the secondary
+//                 record (factor f2 cos / pdf, ray origin), appended to queue C.
 //   k_wf_shadow   queue C: visibility V_q of the secondary NEE rays.
 //   k_wf_combine  per pixel: sum of the per-sample terms in sample order,
 //                 L = T E(d) + (1 - T) / S * sum.
@@ -225,9 +226,19 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
 }
 
 // ---------------------------------------------------------------- continuation rays
-// WIDE lanes per ray: cooperative k-buffer composite of the continuation ray
-// to the secondary record (lf_coop.cuh); lanes 0 and 1 then draw the two
-// environment NEE samples there and the group appends their shadow rays.
+// The secondary record between k_wf_continue and k_wf_secondary is held in
+// planes that are written for good only afterwards: normal in wq0, base
+// colour in fk0, metallic in Vq0, roughness in Vq1.
+__device__ __forceinline__ float* const* rec_n2(const SampleBuf& S) { return S.wq0; }
+__device__ __forceinline__ float* const* rec_a2(const SampleBuf& S) { return S.fk0; }
+__device__ __forceinline__ float* rec_m2(const SampleBuf& S) { return S.Vq0; }
+__device__ __forceinline__ float* rec_r2(const SampleBuf& S) { return S.Vq1; }
+
+// One warp per ray: cooperative k-buffer composite of the continuation ray
+// to the secondary record (lf_coop.cuh).  Lane 0 stores T2 and, when the ray
+// found a surface (then T2 < 1), the record for k_wf_secondary: the NEE
+// origin in xs2 and normal, base colour, metallic and roughness in planes
+// that k_wf_secondary and the secondary shadow rays overwrite afterwards.
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S,
                                                                             int* status,
                                                                             unsigned long long* counters) {
@@ -241,43 +252,19 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
     const long long item = S.qB[k];
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     const long long loc = item - J.item0;
-    const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
-    const float3 xs = pix_origin(J, p, P.ray_offset);
+    const float3 xs = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
     const float3 wi = ld3(S.wi, item);
     Surface s2;
     coop_composite(g, J.insts, J.n_inst, xs, wi, P, st, status, cnt, s2, comp);
-    if (g.c == 0) S.T2[item] = s2.T;
-    if (s2.hits > 0) {  // uniform over the group
-      bool ok = false;
-      if (g.c < 2) {
-        const int qq = g.c;
-        const float3 n2 = s2.n, wo2 = -wi;
-        const float co2 = dot3(n2, wo2);
-        const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
-        const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
-        const float u1 = qq == 0 ? unit24(gb.y) : unit24(gb.w);
-        const float u2 = qq == 0 ? unit24(gb.z) : unit24(gc.x);
-        float3 wq;
-        float pq;
-        env_sample(J.env, u1, u2, wq, pq);
-        const float cq = dot3(n2, wq);
-        ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
-        float3 fk = f3(0.f, 0.f, 0.f);
-        if (ok) fk = brdf_eval(n2, wo2, wq, s2.a, s2.m, s2.r, P.brdf_mode) * (cq * (1.0f - s2.T) * 0.5f / pq);
-        if (qq == 0) {
-          st3(S.xs2, item, s2.x + n2 * P.ray_offset);
-          st3(S.wq0, item, wq);
-          st3(S.fk0, item, fk);
-        } else {
-          st3(S.wq1, item, wq);
-          st3(S.fk1, item, fk);
-        }
+    if (g.c == 0) {
+      S.T2[item] = s2.T;
+      if (s2.hits > 0) {
+        st3(S.xs2, item, s2.x + s2.n * P.ray_offset);
+        st3(rec_n2(S), item, s2.n);
+        st3(rec_a2(S), item, s2.a);
+        rec_m2(S)[item] = s2.m;
+        rec_r2(S)[item] = s2.r;
       }
-      const unsigned m = gballot(g, ok);
-      int base = 0;
-      if (g.c == 0 && m) base = atomicAdd(S.counts + 2, __popc(m));
-      base = gshfl(g, base, 0);
-      if (ok) S.qC[base + __popc(m & ((1u << g.c) - 1u))] = (int)(item * 2 + g.c);
     }
   }
   if (counters && g.c == 0) {  // slot 2: continuation rays
@@ -285,6 +272,50 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
     atomicAdd(counters + 9, (unsigned long long)cnt.tests);
     atomicAdd(counters + 10, (unsigned long long)comp);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(counters + 11, (unsigned long long)n);
+  }
+}
+
+// ---------------------------------------------------------------- secondary NEE sampling
+// One thread per continuation ray that found a surface: the two environment
+// NEE samples at the secondary record (factor f2 cos (1 - T2) / 2 / p_env),
+// appended to queue C.  Kept out of the warp-per-ray continuation kernel,
+// where two lanes would run the CDF searches while thirty wait.
+__global__ void __launch_bounds__(WB) k_wf_secondary(ShadeBatch B, DevParams P, SampleBuf S) {
+  const int n = S.counts[1];
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    long long item = 0;
+    bool push0 = false, push1 = false;
+    if (k < n) {
+      item = S.qB[k];
+      const float T2 = S.T2[item];
+      if (T2 < 1.0f) {
+        const ShadeJob& J = B.jobs[job_of_item(B, item)];
+        const long long loc = item - J.item0;
+        const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+        const float3 n2 = ld3(rec_n2(S), item), a2 = ld3(rec_a2(S), item);
+        const float m2 = rec_m2(S)[item], r2 = rec_r2(S)[item];
+        const float3 wo2 = -ld3(S.wi, item);
+        const float co2 = dot3(n2, wo2);
+        const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
+        const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
+        const float uq[4] = {unit24(gb.y), unit24(gb.z), unit24(gb.w), unit24(gc.x)};
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+          float3 wq;
+          float pq;
+          env_sample(J.env, uq[2 * qq], uq[2 * qq + 1], wq, pq);
+          const float cq = dot3(n2, wq);
+          const bool ok = cq > 0.0f && co2 > 0.0f && pq > 0.0f;
+          float3 fk = f3(0.f, 0.f, 0.f);
+          if (ok) fk = brdf_eval(n2, wo2, wq, a2, m2, r2, P.brdf_mode) * (cq * (1.0f - T2) * 0.5f / pq);
+          if (qq == 0) { st3(S.wq0, item, wq); st3(S.fk0, item, fk); push0 = ok; }
+          else { st3(S.wq1, item, wq); st3(S.fk1, item, fk); push1 = ok; }
+        }
+      }
+    }
+    queue_push(S.qC, S.counts + 2, (int)(item * 2), push0);
+    queue_push(S.qC, S.counts + 2, (int)(item * 2 + 1), push1);
   }
 }
 
@@ -504,6 +535,7 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
   mark(2);
   k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
       B, P, S, status, counters);
+  k_wf_secondary<<<wf_grid(B.n_items, sms), WB, 0, st>>>(B, P, S);
   mark(3);
   k_wf_shadow<<<resident_grid(k_wf_shadow, 2 * B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
       B, P, S, 1, status, counters);
