@@ -229,9 +229,12 @@ __device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const 
   float nhi, nlo, dhi, dlo;
   dot2(ph, pl, nh, nhi, nlo);
   dot2(d, f3(0.f, 0.f, 0.f), nh, dhi, dlo);
-  const float t0 = __fdiv_rn(nhi, dhi);
+  // t0 need not be correctly rounded: the residual below is formed exactly
+  // (FMA) from whatever t0 is, and t1 = res / d is a correction ~2^-23 t,
+  // whose own relative error of 2 ulp is far below the double-float's.
+  const float t0 = __fdividef(nhi, dhi);
   const float res = __fadd_rn(__fmaf_rn(-t0, dhi, nhi), __fmaf_rn(-t0, dlo, nlo));
-  const float t1 = __fdiv_rn(res, dhi);
+  const float t1 = __fdividef(res, dhi);
   t = __fadd_rn(t0, t1);
   tl = __fsub_rn(t1, __fsub_rn(t, t0));
   if (!(t > P.t_min) || !(t < BIG_F)) return false;
