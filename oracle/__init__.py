@@ -189,6 +189,26 @@ def grad(scene, cam, env, pixels, spp, seed, dL_drgb=None, dL_dch=None, shade=Tr
     return d_s, d_e
 
 
+def rigid(scene, k, R, t):
+    """Eq. 2 on object k: a copy of `scene` with mu <- R mu + t, tu <- R tu,
+    tv <- R tv for the object's surfels (scales, opacity and materials are
+    unchanged).  The scene stores FP32 values, so each component is evaluated
+    in FP64 as ((R0 x0 + R1 x1) + R2 x2) (+ t) -- every product of two FP32
+    values is exact -- and rounded once to FP32."""
+    out = scene.copy()
+    lo, hi = int(scene.object_offsets[k]), int(scene.object_offsets[k + 1])
+    R = np.asarray(R, np.float32).astype(np.float64).reshape(3, 3)
+    t = np.asarray(t, np.float32).astype(np.float64).reshape(3)
+    for name, shift in (("mu", True), ("tu", False), ("tv", False)):
+        x = getattr(scene, name)[lo:hi].astype(np.float64)
+        y = np.empty_like(x)
+        for r in range(3):
+            acc = (R[r, 0] * x[:, 0] + R[r, 1] * x[:, 1]) + R[r, 2] * x[:, 2]
+            y[:, r] = acc + t[r] if shift else acc
+        getattr(out, name)[lo:hi] = y.astype(np.float32)
+    return out
+
+
 def trace_rays(scene, env, origins, dirs, params=None):
     """Eq. 6-7 composite of explicit rays.  Returns (ch (n,NCH), margins (n,8))."""
     L = lib()

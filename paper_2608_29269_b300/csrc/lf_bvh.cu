@@ -450,17 +450,23 @@ __global__ void k_wide_boxes(WideArgs a, int n_slots) {
 }
 
 // ---------------------------------------------------------------- rigid transform
+// Eq. 2 on one object's surfels: mu <- R mu + t, tu <- R tu, tv <- R tv.
+// Each component is ((R0 x0 + R1 x1) + R2 x2) (+ t) in FP64, where every
+// product of two FP32 values is exact, rounded once to FP32: the result does
+// not depend on FMA contraction, so any FP64 evaluation in this order gives
+// the same bits.
 __global__ void k_rigid(SceneDev s, int beg, int end, Mat34 T) {
   const int i = beg + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= end) return;
-  float m[3] = {s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]};
-  float u[3] = {s.tu[3 * i], s.tu[3 * i + 1], s.tu[3 * i + 2]};
-  float v[3] = {s.tv[3 * i], s.tv[3 * i + 1], s.tv[3 * i + 2]};
+  const double m[3] = {s.mu[3 * i], s.mu[3 * i + 1], s.mu[3 * i + 2]};
+  const double u[3] = {s.tu[3 * i], s.tu[3 * i + 1], s.tu[3 * i + 2]};
+  const double v[3] = {s.tv[3 * i], s.tv[3 * i + 1], s.tv[3 * i + 2]};
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    s.mu[3 * i + r] = T.R[3 * r] * m[0] + T.R[3 * r + 1] * m[1] + T.R[3 * r + 2] * m[2] + T.t[r];
-    s.tu[3 * i + r] = T.R[3 * r] * u[0] + T.R[3 * r + 1] * u[1] + T.R[3 * r + 2] * u[2];
-    s.tv[3 * i + r] = T.R[3 * r] * v[0] + T.R[3 * r + 1] * v[1] + T.R[3 * r + 2] * v[2];
+    const double R0 = T.R[3 * r], R1 = T.R[3 * r + 1], R2 = T.R[3 * r + 2];
+    s.mu[3 * i + r] = __double2float_rn(__dadd_rn(__dadd_rn(__dadd_rn(R0 * m[0], R1 * m[1]), R2 * m[2]), (double)T.t[r]));
+    s.tu[3 * i + r] = __double2float_rn(__dadd_rn(__dadd_rn(R0 * u[0], R1 * u[1]), R2 * u[2]));
+    s.tv[3 * i + r] = __double2float_rn(__dadd_rn(__dadd_rn(R0 * v[0], R1 * v[1]), R2 * v[2]));
   }
 }
 

@@ -410,3 +410,64 @@ def test_bsdf_sampler_density_is_consistent(p_spec, r):
     np.testing.assert_allclose(oracle.bsdf_pdf(n, wo, r, p_spec, wi), pdf, rtol=1e-12)
     if p_spec == 0.0:  # Malley: cos^2 of the sampled direction is uniform
         assert stats.kstest(c ** 2, "uniform").pvalue > 1e-4
+
+
+# ---------------------------------------------------------------- Eq. 2 (rigid object transform)
+
+
+def _rot_y(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]], np.float32)
+
+
+def test_rigid_identity_and_untouched_objects():
+    sc = scene_c1()
+    two = Scene(sc.mu, sc.tu, sc.tv, sc.scale, sc.opacity, sc.albedo, sc.metallic, sc.roughness,
+                np.array([0, 400, sc.n], np.int32))
+    same = oracle.rigid(two, 1, np.eye(3), np.zeros(3))
+    for k in ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic", "roughness"]:
+        np.testing.assert_array_equal(getattr(same, k), getattr(two, k))
+    moved = oracle.rigid(two, 1, _rot_y(0.7), np.array([0.3, -0.2, 0.1], np.float32))
+    np.testing.assert_array_equal(moved.mu[:400], two.mu[:400])  # object 0 untouched
+    assert not np.allclose(moved.mu[400:], two.mu[400:])
+
+
+def test_rigid_preserves_distances_and_frames():
+    sc = scene_c1()
+    R, t = _rot_y(1.1), np.array([0.5, 0.25, -0.75], np.float32)
+    mv = oracle.rigid(sc, 0, R, t)
+    i, j = np.random.default_rng(2).integers(0, sc.n, (2, 200))
+    d0 = np.linalg.norm(sc.mu[i].astype(np.float64) - sc.mu[j], axis=1)
+    d1 = np.linalg.norm(mv.mu[i].astype(np.float64) - mv.mu[j], axis=1)
+    np.testing.assert_allclose(d1, d0, rtol=1e-6, atol=1e-6)
+    for a, b in [("tu", "tu"), ("tv", "tv"), ("tu", "tv")]:
+        g0 = np.sum(getattr(sc, a).astype(np.float64) * getattr(sc, b), axis=1)
+        g1 = np.sum(getattr(mv, a).astype(np.float64) * getattr(mv, b), axis=1)
+        np.testing.assert_allclose(g1, g0, atol=1e-6)
+    # two moves equal one move by the composed transform (up to one extra FP32 rounding)
+    R2, t2 = _rot_y(-0.4), np.array([-0.1, 0.05, 0.2], np.float32)
+    twice = oracle.rigid(mv, 0, R2, t2)
+    R12 = (R2.astype(np.float64) @ R.astype(np.float64)).astype(np.float32)
+    t12 = (R2.astype(np.float64) @ t + t2).astype(np.float32)
+    once = oracle.rigid(sc, 0, R12, t12)
+    np.testing.assert_allclose(twice.mu, once.mu, atol=3e-6)
+    np.testing.assert_allclose(twice.tu, once.tu, atol=3e-6)
+
+
+def test_moving_scene_and_camera_together_leaves_the_image_unchanged():
+    """Under a uniform environment, a rigid move of every object together with
+    the camera is a change of frame: the rendered pixels stay the same."""
+    sc = scene_c1()
+    cam = Camera((0, 0, 3), (0, 0, 0), (0, 1, 0), 60.0, 24, 24)
+    env = env_uniform(0.8, 8, 16)
+    R, t = _rot_y(0.9), np.array([0.4, -0.3, 0.2], np.float32)
+    mv = oracle.rigid(sc, 0, R, t)
+    R64, t64 = R.astype(np.float64), t.astype(np.float64)
+    cam2 = Camera(tuple(R64 @ np.array(cam.eye, float) + t64), tuple(R64 @ np.array(cam.target, float) + t64),
+                  tuple(R64 @ np.array(cam.up, float)), cam.fovy_deg, cam.width, cam.height)
+    a = oracle.render(sc, cam, env, shade=False)
+    b = oracle.render(mv, cam2, env, shade=False)
+    ok = (a["margins"].min(axis=1) > 1e-4) & (b["margins"].min(axis=1) > 1e-4)
+    assert ok.mean() > 0.8
+    for k in ["T", "W", "depth", "a0", "a1", "a2", "rho0", "rho1", "rho2", "hits"]:
+        np.testing.assert_allclose(a["ch"][ok, CH[k]], b["ch"][ok, CH[k]], atol=2e-4)
