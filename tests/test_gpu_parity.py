@@ -135,7 +135,7 @@ def test_c4_layout_parity_on_pixel_subset():
     samples = tr.alloc_samples(cam, spp)
     rgb = tr.shade(cam, g, env_id, spp=spp, seed=seed, samples=samples)
     tr.sync()
-    pix = S.pixel_subset(cam.width, cam.height, 24, seed=9)
+    pix = S.pixel_subset(cam.width, cam.height, 48, seed=9)
     o = oracle.render(ref, cam, envs[env_id], pix, spp=spp, seed=seed)
     flag_p = flagged(o["margins"])
     flag = flagged(o["margins"], margins_shade=o["margins_shade"])
@@ -144,7 +144,10 @@ def test_c4_layout_parity_on_pixel_subset():
     rg = rgb.reshape(-1, 3).cpu().numpy()[pix].astype(np.float64)
     d = np.abs(np.clip(rg, 0, 1) - np.clip(o["rgb"], 0, 1))[~flag]
     print("C4 gbuf errs", errs, "rgb max", d.max(), "flagged", int(flag_p.sum()), int(flag.sum()), "of", len(pix))
-    assert flag.mean() < 0.25
+    # A pixel carries ~190 shading rays at 64 spp, each with support, opacity
+    # and cosine decisions; the chance that one of them sits within the
+    # FP32/FP64 margin grows with spp, so more pixels are flagged than at 16 spp.
+    assert flag_p.mean() < 0.05 and flag.mean() < 0.75 and (~flag).sum() >= 12
     assert max(errs.values()) <= TOL and d.max() <= TOL
     # adjoint of a loss on the unflagged sampled pixels
     ok = ~flagged(o["margins"], dict(FLAG_GRAD), margins_shade=o["margins_shade"])
