@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from synthetic import scenes as S
-from tests._helpers import OCH, compare_gbuf, flagged, gbuf_at, gpu_tracer
+from tests._helpers import FLAG_SHADE, OCH, compare_gbuf, flagged, gbuf_at, gpu_tracer
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -149,8 +149,15 @@ def test_c4_layout_parity_on_pixel_subset():
     # FP32/FP64 margin grows with spp, so more pixels are flagged than at 16 spp.
     assert flag_p.mean() < 0.05 and flag.mean() < 0.75 and (~flag).sum() >= 12
     assert max(errs.values()) <= TOL and d.max() <= TOL
-    # adjoint of a loss on the unflagged sampled pixels
-    ok = ~flagged(o["margins"], dict(FLAG_GRAD), margins_shade=o["margins_shade"])
+    # adjoint of a loss on the unflagged sampled pixels.  A shading ray's
+    # composite stops where T crosses T_min; the kernel's shading rays start
+    # from the FP32 composite with FP32 directions, which moves T after the
+    # 30-50 hits of this dense scene by up to ~1e-4 relative, and a stop that
+    # moves by one hit changes the secondary record -- and the gradient --
+    # discretely, so pixels with a shading stop within 2e-4 are left out.
+    ok = ~flagged(o["margins"], dict(FLAG_GRAD), margins_shade=o["margins_shade"],
+                  kinds_shade=dict(FLAG_SHADE, stop=2e-4))
+    assert ok.sum() >= 12
     g_rgb = rng.normal(size=(len(pix), 3)) * ok[:, None]
     d_s, d_e = oracle.grad(ref, cam, envs[env_id], pix, spp, seed, g_rgb)
     full = torch.zeros((cam.height * cam.width, 3), device="cuda")
@@ -162,6 +169,10 @@ def test_c4_layout_parity_on_pixel_subset():
                 fwd_samples=samples)
     tr.sync()
     gs, ge = d_surf.cpu().numpy().astype(np.float64), d_env.cpu().numpy().astype(np.float64)
+    if os.path.isdir("gpurun_out"):
+        rows = np.nonzero(np.abs(d_s).sum(1) + np.abs(gs).sum(1))[0]
+        np.save("gpurun_out/grad_c4.npy", dict(rows=rows, d_s=d_s[rows], gs=gs[rows], d_e=d_e, ge=ge,
+                                               pix=pix, ok=ok), allow_pickle=True)
     for name, (ref_g, got) in {"surfels": (d_s, gs), "env": (d_e, ge)}.items():
         rel = np.linalg.norm(got - ref_g) / np.linalg.norm(ref_g)
         print("C4 gradient", name, "L2-relative", rel)
