@@ -173,7 +173,11 @@ def test_c4_layout_parity_on_pixel_subset():
         rows = np.nonzero(np.abs(d_s).sum(1) + np.abs(gs).sum(1))[0]
         np.save("gpurun_out/grad_c4.npy", dict(rows=rows, d_s=d_s[rows], gs=gs[rows], d_e=d_e, ge=ge,
                                                pix=pix, ok=ok), allow_pickle=True)
-    for name, (ref_g, got) in {"surfels": (d_s, gs), "env": (d_e, ge)}.items():
+    groups = dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
+                  metallic=(15, 16), roughness=(16, 17))
+    pairs = {k: (d_s[:, a:b], gs[:, a:b]) for k, (a, b) in groups.items()}
+    pairs["env"] = (d_e, ge)
+    for name, (ref_g, got) in pairs.items():
         rel = np.linalg.norm(got - ref_g) / np.linalg.norm(ref_g)
         print("C4 gradient", name, "L2-relative", rel)
         assert rel <= 1e-3, name
