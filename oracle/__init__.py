@@ -94,6 +94,7 @@ def lib():
         _lib.or_ggx_D.restype = C.c_double
         _lib.or_ggx_D.argtypes = [C.c_double, C.c_double]
         _lib.or_bsdf_pdf.argtypes = [dp, dp, C.c_double, C.c_double, dp, C.c_int, dp]
+        _lib.or_camera_dirs.argtypes = [C.POINTER(_Camera), C.POINTER(C.c_int), C.c_int, dp]
     return _lib
 
 
@@ -187,6 +188,18 @@ def grad(scene, cam, env, pixels, spp, seed, dL_drgb=None, dL_dch=None, shade=Tr
               _p(g_ch, C.c_double) if g_ch is not None else None,
               _p(d_s, C.c_double), _p(d_e, C.c_double), int(threads))
     return d_s, d_e
+
+
+def camera_dirs(cam, pixels=None):
+    """(n, 3) ray directions of camera pixels (FP64 pinhole direction rounded once to FP32)."""
+    L = lib()
+    if pixels is None:
+        pixels = np.arange(cam.width * cam.height, dtype=np.int32)
+    pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+    out = np.zeros((len(pixels), 3), np.float64)
+    cam_c = _camera(cam)
+    L.or_camera_dirs(C.byref(cam_c), _p(pixels, C.c_int), len(pixels), _p(out, C.c_double))
+    return out
 
 
 def rigid(scene, k, R, t):

@@ -945,6 +945,17 @@ void or_shadow_rays(const or_scene* sc_in, const or_params* pp, const double* or
 // (when shade != 0), 2 x NMARGIN margins (nullable): those of the primary
 // ray, then those of the shading rays.  Returns the number of rays
 // traced (primary + shadow + continuation).
+// Pixel ray directions (the FP64 pinhole direction rounded once to FP32).
+void or_camera_dirs(const or_camera* cam_in, const int* pixels, int n, double* dirs) {
+  Cam cam = make_cam(cam_in->eye, cam_in->target, cam_in->up, cam_in->fovy_deg, cam_in->width, cam_in->height);
+  for (int i = 0; i < n; ++i) {
+    const D3 d = cam_dir(cam, pixels[i]);
+    dirs[3 * i] = d.x;
+    dirs[3 * i + 1] = d.y;
+    dirs[3 * i + 2] = d.z;
+  }
+}
+
 int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera* cam_in, const float* env_rgb,
                   const float* env0_rgb, int H, int W, const or_params* pp, const int* pixels, int n_pix, int spp,
                   uint64_t seed, int shade, double* ch_out, double* rgb_out, double* margins, int n_threads) {
