@@ -280,6 +280,30 @@ lf_status lf_profile(lf_ctx* ctx, int enable);
 lf_status lf_profile_read(lf_ctx* ctx, float* ms6);
 
 /*
+ * Geometry-refinement losses of one view on a traced G-buffer (Eq. 8-9):
+ *   L_D  = ||C (D - D*)||_1 / (||C D*||_1 + eps)   depth, confidence-weighted
+ *   L_N  = 1 - <N, N*>_F / (W H)                    rendered normals
+ *   L_DN = 1 - <N^D, N*>_F / (W H)                  depth-derived normals
+ * D and N are the G-buffer's depth (ray distance) and renormalised normal
+ * planes; N^D(x, y) = normalize(P_x x P_y) from central differences of the
+ * back-projected positions P = eye + D d along the G-buffer's ray directions,
+ * P_x = P(x+1, y) - P(x-1, y), P_y = P(x, y-1) - P(x, y+1); it is 0 on the
+ * image border and where the pixel or a 4-neighbour has no composited hit.
+ * depth_ref, depth_conf: W*H device floats; normal_ref: 3 planes of W*H.
+ * weights (host, 3, NULL = ones) weight the terms in the gradient, which is
+ * ADDED to the depth and normal planes of dL_dgbuf (device, the G-buffer
+ * layout; NULL: losses only) and can then be passed to lf_trace_backward.
+ * scratch: device, 256-byte aligned, lf_geometry_loss_scratch_bytes().
+ * losses (host, 3: L_D, L_N, L_DN, unweighted) may be NULL; when given, the
+ * call synchronises the context's stream.
+ */
+size_t lf_geometry_loss_scratch_bytes(int width, int height);
+lf_status lf_geometry_loss(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, const float* depth_ref_dev,
+                           const float* depth_conf_dev, const float* normal_ref_dev, float eps,
+                           const float* weights_host, float* dL_dgbuf_dev, void* scratch_dev, size_t scratch_bytes,
+                           double* losses_host);
+
+/*
  * Measurement helper (no counterpart in the paper): read bandwidth of the L2
  * cache in GB/s, from `reps` passes of float4 loads cached at L2 only over a
  * device buffer of `bytes` (at least 1 MiB; keep it well below the L2 size),

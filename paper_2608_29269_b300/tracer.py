@@ -225,6 +225,25 @@ class Tracer:
         self.check(self.lib.lf_profile_read(self.ctx, ms))
         return list(ms)
 
+    def geometry_loss(self, cam, gbuf: torch.Tensor, depth_ref: torch.Tensor, depth_conf: torch.Tensor,
+                      normal_ref: torch.Tensor, eps: float = 1e-8, weights=(1.0, 1.0, 1.0),
+                      dL_dgbuf: Optional[torch.Tensor] = None):
+        """Geometry-refinement losses (Eq. 8-9) of one view: returns (L_D, L_N, L_DN) and, when dL_dgbuf (a
+        G-buffer-shaped tensor) is given, adds the weighted gradient to its depth and normal planes.
+        depth_ref / depth_conf: (H, W); normal_ref: (3, H, W)."""
+        for t in (gbuf, depth_ref, depth_conf, normal_ref) + ((dL_dgbuf,) if dL_dgbuf is not None else ()):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("geometry_loss: contiguous float32 CUDA tensors expected")
+        c = camera_struct(cam)
+        nbytes = int(self.lib.lf_geometry_loss_scratch_bytes(cam.width, cam.height))
+        scratch = torch.empty((nbytes + 3) // 4, dtype=torch.float32, device="cuda")
+        w = (C.c_float * 3)(*[float(x) for x in weights])
+        out = (C.c_double * 3)()
+        self.check(self.lib.lf_geometry_loss(self.ctx, C.byref(c), _ptr(gbuf), _ptr(depth_ref), _ptr(depth_conf),
+                                             _ptr(normal_ref), C.c_float(eps), w, _ptr(dL_dgbuf), _ptr(scratch),
+                                             nbytes, out))  # synchronises: scratch outlives its use
+        return tuple(out)
+
     def measure_l2_read(self, nbytes: int = 32 << 20, reps: int = 40) -> float:
         """L2 read bandwidth in GB/s (a measurement helper)."""
         gbs = C.c_float()
