@@ -56,4 +56,5 @@ def losses(depth, normal, dirs, hits, eye, depth_ref, conf, normal_ref, eps=1e-8
     L_DN = 1.0 - (ND * Ns).sum() / HW
     total = weights[0] * L_D + weights[1] * L_N + weights[2] * L_DN
     total.backward()
-    return (float(L_D), float(L_N), float(L_DN), D.grad.numpy().copy(), N.grad.numpy().copy())
+    return (float(L_D.detach()), float(L_N.detach()), float(L_DN.detach()), D.grad.numpy().copy(),
+            N.grad.numpy().copy())
