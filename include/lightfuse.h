@@ -304,6 +304,29 @@ lf_status lf_geometry_loss(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_
                            double* losses_host);
 
 /*
+ * Regularisers of the training objectives.  Each ADDS weight * gradient to
+ * the caller's device buffer (NULL: loss only) and, when `loss` (host) is
+ * given, returns the unweighted value after synchronising the stream.
+ *  lf_opacity_loss  L_alpha = ||A - 1||_1 / (W H) (Eq. 4) with A the traced
+ *                   weight sum (G-buffer plane LF_CH_W); gradient into that
+ *                   plane of dL_dgbuf (the G-buffer layout).
+ *  lf_scale_loss    L_s = (1/N) sum_i max(0, max(s_u, s_v)_i / s_max - 1)^2
+ *                   (Eq. 5) over `scale` (device, N x 2); gradient into the
+ *                   scale columns of d_surfel (N x LF_G_STRIDE); a tie of the
+ *                   two scales splits it evenly.
+ *  lf_env_tv_loss   L_TV(E) = (1 / (3 H W)) sum |E(r,c+1) - E(r,c)| +
+ *                   |E(r+1,c) - E(r,c)| (Eq. 14, anisotropic L1; wraps in
+ *                   azimuth, not across the poles) of `rgb` (device H x W x 3);
+ *                   gradient into d_env (H x W x 3).
+ */
+lf_status lf_opacity_loss(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, float weight,
+                          float* dL_dgbuf_dev, double* loss_host);
+lf_status lf_scale_loss(lf_ctx* ctx, const float* scale_dev, int n, float s_max, float weight, float* d_surfel_dev,
+                        double* loss_host);
+lf_status lf_env_tv_loss(lf_ctx* ctx, const float* rgb_dev, int H, int W, float weight, float* d_env_dev,
+                         double* loss_host);
+
+/*
  * Measurement helper (no counterpart in the paper): read bandwidth of the L2
  * cache in GB/s, from `reps` passes of float4 loads cached at L2 only over a
  * device buffer of `bytes` (at least 1 MiB; keep it well below the L2 size),

@@ -82,6 +82,9 @@ SIGNATURES = [
     ("lf_profile_read", C.c_int, [_P, C.POINTER(C.c_float)]),
     ("lf_philox", C.c_int, [_P, _P, C.c_int, C.c_uint32, C.c_uint32, _P]),
     ("lf_measure_l2_read", C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(C.c_float)]),
+    ("lf_opacity_loss", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_float, _P, C.POINTER(C.c_double)]),
+    ("lf_scale_loss", C.c_int, [_P, _P, C.c_int, C.c_float, C.c_float, _P, C.POINTER(C.c_double)]),
+    ("lf_env_tv_loss", C.c_int, [_P, _P, C.c_int, C.c_int, C.c_float, _P, C.POINTER(C.c_double)]),
     ("lf_geometry_loss_scratch_bytes", C.c_size_t, [C.c_int, C.c_int]),
     ("lf_geometry_loss", C.c_int, [_P, C.POINTER(LfCamera), _P, _P, _P, _P, C.c_float, C.POINTER(C.c_float), _P, _P,
                                    C.c_size_t, C.POINTER(C.c_double)]),

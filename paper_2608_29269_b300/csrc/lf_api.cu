@@ -187,6 +187,7 @@ lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out) {
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = dev_alloc(&c->status_dev, 1);
+  if (e == cudaSuccess) e = dev_alloc(&c->loss_dev, 1);
   if (e == cudaSuccess) e = cudaMemset(c->status_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = dev_alloc(&c->offsets_dev, LF_MAX_OBJECTS + 1);
   if (e == cudaSuccess) e = dev_alloc(&c->node_off_dev, LF_MAX_OBJECTS + 1);
@@ -205,7 +206,7 @@ lf_status lf_destroy(lf_ctx* c) {
   if (!c) return LF_ERR_INVALID;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   free_scene_storage(c);
-  dev_free(c->status_dev); dev_free(c->offsets_dev); dev_free(c->node_off_dev); dev_free(c->wnode_off_dev);
+  dev_free(c->status_dev); dev_free(c->loss_dev); dev_free(c->offsets_dev); dev_free(c->node_off_dev); dev_free(c->wnode_off_dev);
   dev_free(c->bounds);
   dev_free(c->insts_dev);
   for (EnvSlot& e : c->env) { dev_free(e.tables); dev_free(e.rowsum); dev_free(e.sin_row); }

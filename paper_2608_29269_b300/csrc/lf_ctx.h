@@ -26,6 +26,7 @@ struct lf_ctx {
   int device = 0;
   int sms = 148;
   int* status_dev = nullptr;
+  double* loss_dev = nullptr;  // loss sum of the regulariser calls
   unsigned long long* counters = nullptr;
   bool profile = false;
   cudaEvent_t prof_ev[8] = {};  // primary | gen | NEE shadow | continuation | secondary shadow | combine

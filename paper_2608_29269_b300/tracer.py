@@ -244,6 +244,36 @@ class Tracer:
                                              nbytes, out))  # synchronises: scratch outlives its use
         return tuple(out)
 
+    @staticmethod
+    def _check_dev(*ts):
+        for t in ts:
+            if t is not None and not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("contiguous float32 CUDA tensors expected")
+
+    def opacity_loss(self, cam, gbuf: torch.Tensor, weight: float = 1.0, dL_dgbuf: Optional[torch.Tensor] = None):
+        """L_alpha (Eq. 4) on the traced weight sums; adds weight * gradient to dL_dgbuf's W plane."""
+        self._check_dev(gbuf, dL_dgbuf)
+        c, out = camera_struct(cam), C.c_double()
+        self.check(self.lib.lf_opacity_loss(self.ctx, C.byref(c), _ptr(gbuf), C.c_float(weight), _ptr(dL_dgbuf),
+                                            C.byref(out)))
+        return out.value
+
+    def scale_loss(self, s_max: float, weight: float = 1.0, d_surfel: Optional[torch.Tensor] = None):
+        """L_s (Eq. 5) over the scene's scales; adds weight * gradient to d_surfel's scale columns."""
+        self._check_dev(self.scene.scale, d_surfel)
+        out = C.c_double()
+        self.check(self.lib.lf_scale_loss(self.ctx, _ptr(self.scene.scale), int(self.scene.n), C.c_float(s_max),
+                                          C.c_float(weight), _ptr(d_surfel), C.byref(out)))
+        return out.value
+
+    def env_tv_loss(self, rgb: torch.Tensor, weight: float = 1.0, d_env: Optional[torch.Tensor] = None):
+        """L_TV (Eq. 14) of an (H, W, 3) environment map; adds weight * gradient to d_env."""
+        self._check_dev(rgb, d_env)
+        out = C.c_double()
+        self.check(self.lib.lf_env_tv_loss(self.ctx, _ptr(rgb), int(rgb.shape[0]), int(rgb.shape[1]),
+                                           C.c_float(weight), _ptr(d_env), C.byref(out)))
+        return out.value
+
     def measure_l2_read(self, nbytes: int = 32 << 20, reps: int = 40) -> float:
         """L2 read bandwidth in GB/s (a measurement helper)."""
         gbs = C.c_float()
