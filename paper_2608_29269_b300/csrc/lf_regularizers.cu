@@ -45,12 +45,11 @@ __global__ void __launch_bounds__(RB) k_scale_loss(const float* __restrict__ sca
   double term = 0.0;
   if (i < n) {
     const float su = scale[2 * i], sv = scale[2 * i + 1];
-    const float m = fmaxf(su, sv);
-    const float r = m / s_max - 1.0f;
-    if (r > 0.0f) {
-      term = (double)r * r;
+    const double r = (double)fmaxf(su, sv) / (double)s_max - 1.0;  // FP64: r is a small difference near s_max
+    if (r > 0.0) {
+      term = r * r;
       if (d_surfel) {
-        const float g = weight * 2.0f * r / (s_max * (float)n);
+        const float g = (float)((double)weight * 2.0 * r / ((double)s_max * (double)n));
         float* o = d_surfel + (size_t)LF_G_STRIDE * i + 9;  // scale columns
         if (su == sv) {
           o[0] += 0.5f * g;
