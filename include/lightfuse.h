@@ -69,6 +69,8 @@ typedef struct {
   int max_rounds;    /* k-buffer rounds per ray before LF_ERR_ROUND_LIMIT    */
   int brdf_mode;     /* 0 Lambert + GGX metallic-roughness, 1 Lambert a/pi   */
   int sampling_mode; /* 0 MIS (NEE + BSDF), 1 BSDF only, 2 NEE only          */
+  int sampler;       /* 0 Philox4x32-10 uniforms; 1 Sobol points (Joe-Kuo     */
+                     /* direction numbers) with a per-pixel Philox rotation   */
 } lf_params;
 
 /* Scene: caller-owned FP32 device arrays, surfel i at index i.  Object k
@@ -127,7 +129,7 @@ enum { LF_G_MU = 0, LF_G_TU = 3, LF_G_TV = 6, LF_G_S = 9, LF_G_O = 11, LF_G_A = 
 typedef struct lf_ctx lf_ctx;
 
 /* Defaults: T_min 1e-4, alpha_min 1/255, alpha_max 0.99, support_r2 9,
- * eps_w 1e-8, t_min 1e-4, ray_offset 1e-3, p_spec 0.5, max_rounds 64. */
+ * eps_w 1e-8, t_min 1e-4, ray_offset 1e-3, p_spec 0.5, max_rounds 64, sampler 0. */
 lf_status lf_params_default(lf_params* out);
 
 /* Create a context bound to the current CUDA device and `stream` (a

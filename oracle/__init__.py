@@ -34,7 +34,7 @@ PARAM_ORDER = ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic", "roug
 
 def default_params(**kw):
     p = dict(T_min=1e-4, alpha_min=1.0 / 255.0, alpha_max=0.99, support_r2=9.0, eps_w=1e-8,
-             t_min=1e-4, ray_offset=1e-3, p_spec=0.5, brdf_mode=0, sampling_mode=0)
+             t_min=1e-4, ray_offset=1e-3, p_spec=0.5, brdf_mode=0, sampling_mode=0, sampler=0)
     p.update(kw)
     return p
 
@@ -61,7 +61,7 @@ class _Camera(C.Structure):
 class _Params(C.Structure):
     _fields_ = [(k, C.c_double) for k in ["T_min", "alpha_min", "alpha_max", "support_r2", "eps_w",
                                           "t_min", "ray_offset", "p_spec"]] + \
-               [("brdf_mode", C.c_int), ("sampling_mode", C.c_int)]
+               [("brdf_mode", C.c_int), ("sampling_mode", C.c_int), ("sampler", C.c_int)]
 
 
 _lib = None
@@ -85,7 +85,8 @@ def lib():
                                        C.c_int, dp, dp]
         _lib.or_shadow_rays.argtypes = [C.POINTER(_Scene), C.POINTER(_Params), dp, dp, C.c_int, dp]
         _lib.or_philox.argtypes = [u32p, C.c_int, C.c_uint32, C.c_uint32, u32p]
-        _lib.or_uniforms.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, dp]
+        _lib.or_uniforms.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, dp]
+        _lib.or_sobol.argtypes = [u32p, C.c_int, C.c_int, u32p]
         _lib.or_env_tables.argtypes = [fp, C.c_int, C.c_int, dp, dp, dp, dp]
         _lib.or_env_sample.argtypes = [fp, C.c_int, C.c_int, dp, C.c_int, dp, dp]
         _lib.or_env_eval.argtypes = [fp, C.c_int, C.c_int, dp, C.c_int, dp, dp]
@@ -128,7 +129,8 @@ def _camera(cam):
 def _params(p):
     p = default_params(**(p or {}))
     return _Params(*[float(p[k]) for k in ["T_min", "alpha_min", "alpha_max", "support_r2", "eps_w", "t_min",
-                                           "ray_offset", "p_spec"]], int(p["brdf_mode"]), int(p["sampling_mode"]))
+                                           "ray_offset", "p_spec"]], int(p["brdf_mode"]), int(p["sampling_mode"]),
+                   int(p["sampler"]))
 
 
 def render(scene, cam, env, pixels=None, spp=0, seed=0, shade=True, params=None, scene0=None, env0=None,
@@ -255,10 +257,18 @@ def philox(counters, key0, key1):
     return out
 
 
-def uniforms(pixel, sample, seed):
+def uniforms(pixel, sample, seed, sampler=0):
     u = np.zeros(9)
-    lib().or_uniforms(C.c_uint32(pixel), C.c_uint32(sample), C.c_uint64(seed), _p(u, C.c_double))
+    lib().or_uniforms(C.c_uint32(pixel), C.c_uint32(sample), C.c_uint64(seed), int(sampler), _p(u, C.c_double))
     return u
+
+
+def sobol(index, dim):
+    """32-bit Sobol fractions of dimension `dim` (0-8) for integer indices."""
+    idx = np.ascontiguousarray(index, dtype=np.uint32)
+    out = np.zeros(len(idx), np.uint32)
+    lib().or_sobol(_p(idx, C.c_uint32), len(idx), int(dim), _p(out, C.c_uint32))
+    return out
 
 
 def env_tables(env):

@@ -74,17 +74,62 @@ void philox4x32_10(const uint32_t in[4], uint32_t k0, uint32_t k1, uint32_t out[
 
 inline double to_unit(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
+// Sobol direction numbers for 9 dimensions (Joe and Kuo 2008: primitive
+// polynomial of degree s with coefficients a, initial numbers m; the first
+// dimension is van der Corput), as 32-bit fractions from the recurrence
+//   v_k = m_k 2^(31-k) (k < s),  v_k = v_{k-s} xor (v_{k-s} >> s) xor (xor over j < s with bit a_j: v_{k-j}).
+struct SobolTable {
+  uint32_t v[9][32];
+  SobolTable() {
+    const int deg[9] = {0, 1, 2, 3, 3, 4, 4, 5, 5};
+    const int coef[9] = {0, 0, 1, 1, 2, 1, 4, 2, 4};
+    const uint32_t init[9][5] = {{1}, {1}, {1, 3}, {1, 3, 1}, {1, 1, 1}, {1, 1, 3, 3}, {1, 3, 5, 13},
+                                 {1, 1, 5, 5, 17}, {1, 1, 5, 5, 5}};
+    for (int k = 0; k < 32; ++k) v[0][k] = 1u << (31 - k);
+    for (int d = 1; d < 9; ++d)
+      for (int k = 0; k < 32; ++k) {
+        const int s = deg[d];
+        if (k < s) { v[d][k] = init[d][k] << (31 - k); continue; }
+        uint32_t x = v[d][k - s] ^ (v[d][k - s] >> s);
+        for (int j = 1; j < s; ++j)
+          if ((coef[d] >> (s - 1 - j)) & 1) x ^= v[d][k - j];
+        v[d][k] = x;
+      }
+  }
+};
+const SobolTable& sobol_table() {
+  static const SobolTable t;
+  return t;
+}
+// Point `index` of Sobol dimension d: XOR of the direction numbers of its set bits.
+uint32_t sobol32(uint32_t index, int d) {
+  uint32_t x = 0;
+  for (int k = 0; index; ++k, index >>= 1)
+    if (index & 1u) x ^= sobol_table().v[d][k];
+  return x;
+}
+
 // The nine uniforms of one (pixel, sample): NEE (0,1), lobe 2, BSDF (3,4),
 // secondary NEE #1 (5,6), secondary NEE #2 (7,8).
-void sample_uniforms(uint32_t pixel, uint32_t sample, uint64_t seed, double u[9]) {
+//  sampler 0: Philox4x32-10 of counter (pixel, sample, group, 0), groups 0-2;
+//  sampler 1: the Sobol point of index `sample`, rotated modulo 1 per pixel by
+//             Philox4x32-10 of counter (pixel, 0xffffffff, group, 1), in 24-bit
+//             fixed point.
+void sample_uniforms(uint32_t pixel, uint32_t sample, uint64_t seed, int sampler, double u[9]) {
   uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
   uint32_t out[4];
   for (uint32_t g = 0; g < 3; ++g) {
-    uint32_t ctr[4] = {pixel, sample, g, 0u};
+    uint32_t ctr[4] = {pixel, sampler == 1 ? 0xffffffffu : sample, g, sampler == 1 ? 1u : 0u};
     philox4x32_10(ctr, k0, k1, out);
     for (int i = 0; i < 4; ++i) {
-      int idx = (int)g * 4 + i;
-      if (idx < 9) u[idx] = to_unit(out[i]);
+      const int idx = (int)g * 4 + i;
+      if (idx >= 9) continue;
+      if (sampler == 1) {
+        const uint32_t x = ((sobol32(sample, idx) >> 8) + (out[i] >> 8)) & 0xffffffu;
+        u[idx] = (double)x * (1.0 / 16777216.0);
+      } else {
+        u[idx] = to_unit(out[i]);
+      }
     }
   }
 }
@@ -177,7 +222,7 @@ inline D3 normalize(const D3& a) {
 // ------------------------------------------------------------------------
 struct Params {
   double T_min, alpha_min, alpha_max, support_r2, eps_w, t_min, ray_offset, p_spec;
-  int brdf_mode, sampling_mode;
+  int brdf_mode, sampling_mode, sampler;
 };
 
 struct SceneD {  // FP64 copy of the FP32 inputs plus the plane normal n^ of each surfel
@@ -687,7 +732,7 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
   for (int s = 0; s < spp; ++s) {
     SampleFz& fz = out[s];
     double u[9];
-    sample_uniforms(pixel, (uint32_t)s, seed, u);
+    sample_uniforms(pixel, (uint32_t)s, seed, P.sampler, u);
     if (P.sampling_mode != 1) {  // (i) environment NEE at the primary record
       env_sample(env0, u[0], u[1], fz.we, fz.pe);
       double ce = dot(n, fz.we);
@@ -818,7 +863,7 @@ struct or_scene {
 struct or_camera { double eye[3], target[3], up[3], fovy_deg; int width, height; };
 struct or_params {
   double T_min, alpha_min, alpha_max, support_r2, eps_w, t_min, ray_offset, p_spec;
-  int brdf_mode, sampling_mode;
+  int brdf_mode, sampling_mode, sampler;
 };
 
 int or_nch() { return NCH; }
@@ -828,13 +873,17 @@ void or_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* o
   for (int i = 0; i < n; ++i) philox4x32_10(ctr + 4 * i, k0, k1, out + 4 * i);
 }
 
-void or_uniforms(uint32_t pixel, uint32_t sample, uint64_t seed, double* u9) {
-  sample_uniforms(pixel, sample, seed, u9);
+void or_uniforms(uint32_t pixel, uint32_t sample, uint64_t seed, int sampler, double* u9) {
+  sample_uniforms(pixel, sample, seed, sampler, u9);
+}
+
+void or_sobol(const uint32_t* index, int n, int dim, uint32_t* out) {
+  for (int i = 0; i < n; ++i) out[i] = sobol32(index[i], dim);
 }
 
 static Params to_params(const or_params* p) {
   return Params{p->T_min, p->alpha_min, p->alpha_max, p->support_r2, p->eps_w, p->t_min,
-                p->ray_offset, p->p_spec, p->brdf_mode, p->sampling_mode};
+                p->ray_offset, p->p_spec, p->brdf_mode, p->sampling_mode, p->sampler};
 }
 static SceneD to_scene(const or_scene* s) {
   return load_scene(s->mu, s->tu, s->tv, s->scale, s->opacity, s->albedo, s->metallic, s->roughness, s->n);

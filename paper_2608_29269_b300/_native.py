@@ -25,7 +25,7 @@ G_STRIDE = 17
 class LfParams(C.Structure):
     _fields_ = [("T_min", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("support_r2", C.c_float),
                 ("eps_w", C.c_float), ("t_min", C.c_float), ("ray_offset", C.c_float), ("p_spec", C.c_float),
-                ("max_rounds", C.c_int), ("brdf_mode", C.c_int), ("sampling_mode", C.c_int)]
+                ("max_rounds", C.c_int), ("brdf_mode", C.c_int), ("sampling_mode", C.c_int), ("sampler", C.c_int)]
 
 
 class LfScene(C.Structure):

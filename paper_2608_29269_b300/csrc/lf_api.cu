@@ -83,7 +83,7 @@ bool cam_ok(const lf_camera* c) {
 
 DevParams to_dev(const lf_params& p) {
   return DevParams{p.T_min, p.alpha_min, p.alpha_max, p.support_r2, p.eps_w, p.t_min, p.ray_offset, p.p_spec,
-                   p.max_rounds, p.brdf_mode, p.sampling_mode};
+                   p.max_rounds, p.brdf_mode, p.sampling_mode, p.sampler};
 }
 
 }  // namespace
@@ -168,6 +168,7 @@ lf_status lf_params_default(lf_params* p) {
   p->max_rounds = 64;
   p->brdf_mode = 0;
   p->sampling_mode = 0;
+  p->sampler = 0;
   return LF_OK;
 }
 
@@ -178,7 +179,7 @@ lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out) {
   if (!(p.T_min >= 0.0f && p.alpha_min >= 0.0f && p.alpha_max > 0.0f && p.alpha_max < 1.0f &&
         p.support_r2 > 0.0f && p.eps_w >= 0.0f && p.t_min >= 0.0f && p.p_spec >= 0.0f && p.p_spec <= 1.0f &&
         p.max_rounds > 0 && (p.brdf_mode == 0 || p.brdf_mode == 1) && p.sampling_mode >= 0 &&
-        p.sampling_mode <= 2))
+        p.sampling_mode <= 2 && (p.sampler == 0 || p.sampler == 1)))
     return LF_ERR_INVALID;
   lf_ctx* c = new lf_ctx();
   c->params = p;

@@ -37,7 +37,7 @@ constexpr float BIG_F = 3.0e38f;
 
 struct DevParams {
   float T_min, alpha_min, alpha_max, support_r2, eps_w, t_min, ray_offset, p_spec;
-  int max_rounds, brdf_mode, sampling_mode;
+  int max_rounds, brdf_mode, sampling_mode, sampler;
 };
 
 // One TLAS entry: an object's BLAS in world space (Eq. 2 after its transform).
@@ -120,17 +120,71 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   }
   return c;
 }
-__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
 // The nine uniforms of (pixel, sample): NEE (0,1), lobe 2, BSDF (3,4),
 // secondary NEE #1 (5,6), #2 (7,8).  Counter (pixel, sample, group, 0).
-__device__ __forceinline__ void sample_uniforms(uint32_t pixel, uint32_t s, uint32_t k0, uint32_t k1, float u[9]) {
-  uint4 a = philox4x32_10(make_uint4(pixel, s, 0u, 0u), k0, k1);
-  uint4 b = philox4x32_10(make_uint4(pixel, s, 1u, 0u), k0, k1);
-  uint4 c = philox4x32_10(make_uint4(pixel, s, 2u, 0u), k0, k1);
-  u[0] = unit24(a.x); u[1] = unit24(a.y); u[2] = unit24(a.z); u[3] = unit24(a.w);
-  u[4] = unit24(b.x); u[5] = unit24(b.y); u[6] = unit24(b.z); u[7] = unit24(b.w);
-  u[8] = unit24(c.x);
+// Sobol points in 9 dimensions (Joe and Kuo 2008 direction numbers: the
+// first dimension is van der Corput, the next eight use the primitive
+// polynomials of degree s with coefficients a and initial numbers m), as
+// 32-bit fractions: point i is the XOR of the direction numbers of the set
+// bits of i.  Tabulated at compile time from the recurrence
+//   v_k = v_{k-s} ^ (v_{k-s} >> s) ^ XOR_{j=1..s-1} a_j v_{k-j},  v_k = m_k 2^(31-k) for k < s.
+struct SobolDirs {
+  uint32_t v[9][32];
+};
+constexpr SobolDirs make_sobol_dirs() {
+  SobolDirs t{};
+  const int S[9] = {0, 1, 2, 3, 3, 4, 4, 5, 5};
+  const int A[9] = {0, 0, 1, 1, 2, 1, 4, 2, 4};
+  const uint32_t M[9][5] = {{1, 0, 0, 0, 0}, {1, 0, 0, 0, 0}, {1, 3, 0, 0, 0}, {1, 3, 1, 0, 0}, {1, 1, 1, 0, 0},
+                            {1, 1, 3, 3, 0}, {1, 3, 5, 13, 0}, {1, 1, 5, 5, 17}, {1, 1, 5, 5, 5}};
+  for (int k = 0; k < 32; ++k) t.v[0][k] = 1u << (31 - k);
+  for (int d = 1; d < 9; ++d) {
+    const int s = S[d];
+    for (int k = 0; k < 32; ++k) {
+      if (k < s) {
+        t.v[d][k] = M[d][k] << (31 - k);
+      } else {
+        uint32_t x = t.v[d][k - s] ^ (t.v[d][k - s] >> s);
+        for (int j = 1; j < s; ++j)
+          if ((A[d] >> (s - 1 - j)) & 1) x ^= t.v[d][k - j];
+        t.v[d][k] = x;
+      }
+    }
+  }
+  return t;
+}
+__constant__ const SobolDirs kSobol = make_sobol_dirs();
+
+__device__ __forceinline__ uint32_t sobol32(uint32_t index, int dim) {
+  uint32_t x = 0u;
+  for (int k = 0; index != 0u; ++k, index >>= 1)
+    if (index & 1u) x ^= kSobol.v[dim][k];
+  return x;
+}
+
+// The nine uniforms of one (pixel, sample): NEE (0,1), lobe 2, BSDF (3,4),
+// secondary NEE #1 (5,6), secondary NEE #2 (7,8).
+//  sampler 0: Philox4x32-10 of counter (pixel, sample, group, 0), groups 0-2.
+//  sampler 1: Sobol point `sample` rotated per pixel (Cranley-Patterson):
+//             u_d = ((sobol_d >> 8) + (r_d >> 8)) mod 2^24, r = Philox of
+//             counter (pixel, 0xffffffff, group, 1), groups 0-2.
+// Both in 24-bit fixed point, so the values are exact.
+__device__ __forceinline__ void sample_uniforms(uint32_t pixel, uint32_t s, uint32_t k0, uint32_t k1, int sampler,
+                                                float u[9]) {
+  uint32_t w[12];
+  const uint32_t ctr1 = sampler == 1 ? 0xffffffffu : s, ctr3 = sampler == 1 ? 1u : 0u;
+#pragma unroll
+  for (uint32_t g = 0; g < 3; ++g) {
+    const uint4 r = philox4x32_10(make_uint4(pixel, ctr1, g, ctr3), k0, k1);
+    w[4 * g] = r.x; w[4 * g + 1] = r.y; w[4 * g + 2] = r.z; w[4 * g + 3] = r.w;
+  }
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    uint32_t x = w[d] >> 8;
+    if (sampler == 1) x = ((sobol32(s, d) >> 8) + x) & 0xffffffu;
+    u[d] = (float)x * (1.0f / 16777216.0f);
+  }
 }
 
 // ------------------------------------------------------------------ Eq. 6

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
     float ek = 0.0f, bc = 0.0f, wb = 0.0f;
     if (q.hits > 0 && dot3(n, wo) > 0.0f) {
       float u[9];
-      sample_uniforms((uint32_t)p, (uint32_t)s, J.k0, J.k1, u);
+      sample_uniforms((uint32_t)p, (uint32_t)s, J.k0, J.k1, P.sampler, u);
       if (P.sampling_mode != 1) {
         float pe;
         env_sample(J.env, u[0], u[1], we, pe);
@@ -297,9 +297,9 @@ __global__ void __launch_bounds__(WB) k_wf_secondary(ShadeBatch B, DevParams P, 
         const float m2 = rec_m2(S)[item], r2 = rec_r2(S)[item];
         const float3 wo2 = -ld3(S.wi, item);
         const float co2 = dot3(n2, wo2);
-        const uint4 gb = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 1u, 0u), J.k0, J.k1);
-        const uint4 gc = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)s, 2u, 0u), J.k0, J.k1);
-        const float uq[4] = {unit24(gb.y), unit24(gb.z), unit24(gb.w), unit24(gc.x)};
+        float u[9];
+        sample_uniforms((uint32_t)p, (uint32_t)s, J.k0, J.k1, P.sampler, u);
+        const float uq[4] = {u[5], u[6], u[7], u[8]};
 #pragma unroll
         for (int qq = 0; qq < 2; ++qq) {
           float3 wq;

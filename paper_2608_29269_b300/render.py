@@ -48,3 +48,24 @@ class SurfelRender(torch.autograd.Function):
 def render(tracer: Tracer, cam, env_id: int = 0, spp: int = 16, seed: int = 0):
     s = tracer.scene
     return SurfelRender.apply(tracer, cam, env_id, spp, seed, tracer.envs[env_id], *s.tensors())
+
+
+def spp_schedule(iteration: int) -> int:
+    """Samples per pixel of the inverse-rendering schedule (Sec. 4.2): 8, then
+    16 from iteration 7,500 and 32 from iteration 12,000."""
+    if iteration < 0:
+        raise ValueError("iteration must be non-negative")
+    return 8 if iteration < 7500 else (16 if iteration < 12000 else 32)
+
+
+def trainable_groups(iteration: int):
+    """Parameter groups the inverse-rendering stages optimise (Sec. 4.2):
+    lighting only until iteration 2,000, lighting and base colour until 9,000,
+    then lighting and every material parameter."""
+    if iteration < 0:
+        raise ValueError("iteration must be non-negative")
+    if iteration < 2000:
+        return ("env",)
+    if iteration < 9000:
+        return ("env", "albedo")
+    return ("env", "albedo", "metallic", "roughness")

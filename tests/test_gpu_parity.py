@@ -64,7 +64,8 @@ def test_c1_primary_gbuffer_parity():
     assert max(errs.values()) <= TOL, errs
 
 
-@pytest.mark.parametrize("params", [dict(), dict(sampling_mode=1), dict(sampling_mode=2), dict(brdf_mode=1)])
+@pytest.mark.parametrize("params", [dict(), dict(sampling_mode=1), dict(sampling_mode=2), dict(brdf_mode=1),
+                                    dict(sampler=1)])
 def test_c1_shaded_parity(params):
     sc, cam, _ = _c1_inputs()
     env = S.env_sky_sun(3)
@@ -275,21 +276,22 @@ def test_wide_bvh_covers_every_leaf_once_and_nests():
         assert len(visited) <= len(slots)
 
 
-def test_c3_gradient_parity():
+@pytest.mark.parametrize("params", [dict(), dict(sampler=1)])
+def test_c3_gradient_parity(params):
     """Adjoint vs the oracle's reverse-mode gradient (1e-3 relative), 512 surfels, 32x32, 4 spp."""
     import torch
     full = S.scene_c2(0)
     cam = S.camera_c2(32, 32)
     sc = S.scene_c3_subset(full, cam, 512, seed=0)
     env = S.env_sky_sun(0)
-    tr, st = gpu_tracer(sc, [env])
+    tr, st = gpu_tracer(sc, [env], **params)
     pix = np.arange(cam.n_pixels, dtype=np.int32)
-    o = oracle.render(sc, cam, env, pix, spp=4, seed=3)
+    o = oracle.render(sc, cam, env, pix, spp=4, seed=3, params=params)
     ok = ~flagged(o["margins"], dict(FLAG_GRAD), margins_shade=o["margins_shade"])
     rng = np.random.default_rng(8)
     g_rgb = rng.normal(size=(cam.n_pixels, 3)) * ok[:, None]
     g_ch = rng.normal(size=(cam.n_pixels, 17)) * 0.2 * ok[:, None]
-    d_s, d_e = oracle.grad(sc, cam, env, pix, 4, 3, g_rgb, g_ch)
+    d_s, d_e = oracle.grad(sc, cam, env, pix, 4, 3, g_rgb, g_ch, params=params)
     g = tr.trace_primary(cam, 0)
     samples = tr.alloc_samples(cam, 4)
     tr.shade(cam, g, 0, spp=4, seed=3, samples=samples)

@@ -64,3 +64,11 @@ def test_request_stream_is_seeded_poisson_with_valid_edits():
             assert np.allclose(R @ R.T, np.eye(3), atol=1e-6) and abs(np.linalg.det(R) - 1) < 1e-6
             assert 1 <= r.edit["object"] < sc.n_objects
         assert r.cam.width in (256, 512, 800, 1024) and r.spp in (4, 8, 16, 32)
+
+
+def test_inverse_rendering_schedule():
+    from paper_2608_29269_b300.render import spp_schedule as sched, trainable_groups as groups
+    assert [sched(i) for i in (0, 7499, 7500, 11999, 12000, 14999)] == [8, 8, 16, 16, 32, 32]
+    assert groups(0) == ("env",) and groups(1999) == ("env",)
+    assert groups(2000) == ("env", "albedo") and groups(8999) == ("env", "albedo")
+    assert groups(9000) == ("env", "albedo", "metallic", "roughness")

@@ -62,6 +62,55 @@ def test_uniforms_are_24_bit_and_in_unit_interval():
     assert np.all(np.round(u * 2 ** 24) == u * 2 ** 24)
 
 
+# ---------------------------------------------------------------- Sobol sampler (variant of the paper's replayed Sobol samples)
+
+
+def test_sobol_first_dimension_is_van_der_corput():
+    i = np.arange(4096, dtype=np.uint32)
+    rev = np.array([int(f"{x:032b}"[::-1], 2) for x in i], np.uint64)
+    np.testing.assert_array_equal(oracle.sobol(i, 0).astype(np.uint64), rev)
+
+
+def test_sobol_second_dimension_known_points():
+    # x -> x + 1 polynomial: 0, 1/2, 3/4, 1/4, 5/8, 1/8, 3/8, 7/8 in index order
+    got = oracle.sobol(np.arange(8), 1) / 2.0 ** 32
+    np.testing.assert_array_equal(got, [0, 0.5, 0.75, 0.25, 0.625, 0.125, 0.375, 0.875])
+
+
+@pytest.mark.parametrize("dim", range(9))
+def test_sobol_dimensions_are_stratified(dim):
+    """The first 2^m points of every dimension put one point in each interval [k/2^m, (k+1)/2^m)."""
+    x = oracle.sobol(np.arange(4096), dim).astype(np.uint64)
+    for m in range(1, 13):
+        cells = x[: 1 << m] >> np.uint64(32 - m)
+        assert len(np.unique(cells)) == 1 << m, (dim, m)
+
+
+def test_sobol_first_two_dimensions_form_a_0m2_net():
+    """Every elementary dyadic box of area 2^-10 holds exactly one of the first 1024 points."""
+    m = 10
+    x0 = oracle.sobol(np.arange(1 << m), 0).astype(np.uint64)
+    x1 = oracle.sobol(np.arange(1 << m), 1).astype(np.uint64)
+    for a in range(m + 1):
+        b = m - a
+        cells = (x0 >> np.uint64(32 - a) if a else np.zeros_like(x0)) * np.uint64(1 << b) + \
+                (x1 >> np.uint64(32 - b) if b else np.zeros_like(x1))
+        assert len(np.unique(cells)) == 1 << m, a
+
+
+def test_sobol_sampler_uniforms_and_white_furnace():
+    u = np.stack([oracle.uniforms(7, s, 99, sampler=1) for s in range(64)])
+    assert np.all(u >= 0) and np.all(u < 1) and np.all(np.round(u * 2 ** 24) == u * 2 ** 24)
+    # one pixel's 64 samples: per dimension, a rotated stratified set (one point per 1/64 cell after the shift)
+    for d in range(9):
+        shifted = np.sort((u[:, d] - u[0, d] + oracle.sobol([0], d)[0] / 2.0 ** 32) % 1.0)
+        assert len(np.unique(np.floor(shifted * 64 + 1e-9))) == 64
+    sc, cam = _furnace_setup()
+    out = oracle.render(sc, cam, env_uniform(1.0, 16, 32), spp=16, seed=1,
+                        params=dict(brdf_mode=1, sampling_mode=1, sampler=1))
+    np.testing.assert_allclose(out["rgb"], 1.0, atol=1e-12)
+
+
 # ---------------------------------------------------------------- Eq. 6
 
 
