@@ -358,15 +358,17 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     LF_CUDA(c, launch_hierarchy(c->keys, c->offsets_dev, c->node_off_dev, n_obj, c->n_nodes, c->nodes,
                                 c->leaf_parent, c->node_parent, c->node_range, c->stream));
     const int n_wide = c->wnode_off_h[n_obj];
-    if (n_wide > 0) {
-      LF_CUDA(c, cudaMemsetAsync(c->wsrc, 0xff, sizeof(int) * WIDE * (size_t)n_wide, c->stream));
+    if (n_wide > 0) LF_CUDA(c, cudaMemsetAsync(c->wsrc, 0xff, sizeof(int) * WIDE * (size_t)n_wide, c->stream));
+    lf_status st = lf_ctx_fit(c, 0, n_obj - 1);  // binary boxes (no wide slots yet)
+    if (st != LF_OK) return st;
+    if (n_wide > 0) {  // collapse by box surface, then the wide boxes
       WideArgs w = lf_ctx_wide_args(c);
       w.first_obj = 0;
       w.n_objs = n_obj;
       LF_CUDA(c, launch_collapse(w, c->stream));
+      w = lf_ctx_wide_args(c);
+      LF_CUDA(c, launch_wide_boxes(w, WIDE * n_wide, c->stream));
     }
-    lf_status st = lf_ctx_fit(c, 0, n_obj - 1);
-    if (st != LF_OK) return st;
   }
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   c->built = true;

@@ -331,12 +331,14 @@ __global__ void k_pack_fit(SceneDev s, FitArgs a) {
 // The binary BLAS of each object is collapsed into a WIDE-ary tree whose
 // nodes are traversed by WIDE lanes at once (one child slot per lane).  A wide
 // node starts from a binary node's two children and repeatedly replaces the
-// child with the most leaves by its own two children, while fewer than WIDE
-// children are held and that child has more than WLEAF leaves.  A child with
-// at most WLEAF leaves becomes a leaf slot (its surfels are consecutive in
-// leaf order); a larger one becomes a wide node of its own.  The rule depends
-// on leaf counts only, so the wide topology is fixed by the build and a refit
-// only copies boxes (k_wide_boxes).  A wide node that is not full holds only
+// child with the largest box surface (the one rays enter most often) by its
+// own two children, while fewer than WIDE children are held and that child has
+// more than WLEAF leaves.  A child with at most WLEAF leaves becomes a leaf
+// slot (its surfels are consecutive in leaf order); a larger one becomes a
+// wide node of its own.  The collapse runs once per build, after the first
+// fit; a refit keeps the topology and only copies boxes (k_wide_boxes) --
+// a rigid motion moves every box of an object together, so the choices stay
+// as good.  A wide node that is not full holds only
 // leaf slots and covers more than WLEAF surfels; with I nodes, at most
 // n / (WLEAF + 1) of them not full and n leaf slots, I (WIDE - 1) <= n +
 // (WIDE - 2) n / (WLEAF + 1), the capacity wide_capacity() allocates.
@@ -368,24 +370,36 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
       const int item = chunk + threadIdx.x;
       const bool valid = item < level_end;
       int code[WIDE], cnt[WIDE], src[WIDE];
+      float prio[WIDE];
       int nc = 0, n_int = 0;
+      // expansion priority of a child: the surface of its box (stored in its
+      // binary parent), half of it
+      auto priority = [&](int parent, int side) -> float {
+        const float* f = reinterpret_cast<const float*>(bnodes + 4 * parent) + (side ? 6 : 0);
+        const float dx = f[3] - f[0], dy = f[4] - f[1], dz = f[5] - f[2];
+        return dx * dy + dy * dz + dz * dx;
+      };
       if (valid) {
         const int b = queue[item];
         const float4 f = bnodes[4 * b + 3];
         const int cl = __float_as_int(f.x), cr = __float_as_int(f.y);
         code[0] = cl; src[0] = 2 * b + 0; cnt[0] = cl >= 0 ? a.node_range[nb + cl].y : 1;
         code[1] = cr; src[1] = 2 * b + 1; cnt[1] = cr >= 0 ? a.node_range[nb + cr].y : 1;
+        prio[0] = priority(b, 0);
+        prio[1] = priority(b, 1);
         nc = 2;
         while (nc < WIDE) {
           int best = -1;
           for (int c = 0; c < nc; ++c)
-            if (code[c] >= 0 && cnt[c] > WLEAF && (best < 0 || cnt[c] > cnt[best])) best = c;
+            if (code[c] >= 0 && cnt[c] > WLEAF && (best < 0 || prio[c] > prio[best])) best = c;
           if (best < 0) break;
           const int e = code[best];
           const float4 g = bnodes[4 * e + 3];
           const int el = __float_as_int(g.x), er = __float_as_int(g.y);
           code[best] = el; src[best] = 2 * e + 0; cnt[best] = el >= 0 ? a.node_range[nb + el].y : 1;
           code[nc] = er; src[nc] = 2 * e + 1; cnt[nc] = er >= 0 ? a.node_range[nb + er].y : 1;
+          prio[best] = priority(e, 0);
+          prio[nc] = priority(e, 1);
           ++nc;
         }
         for (int c = 0; c < nc; ++c) n_int += (code[c] >= 0 && cnt[c] > WLEAF) ? 1 : 0;
