@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev 
   FarKCoop kb;
   kb.P = Pm;
   const Ray ray = make_ray(o, d);
-  Counters cnt;
+  NoCounters cnt;
   for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
     kb.reset(bound, inclusive);
     coop_traverse(g, a.insts, a.n_inst, ray, kb, st, a.status, cnt);

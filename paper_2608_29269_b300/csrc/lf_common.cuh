@@ -571,8 +571,20 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
   return tnear <= tfar;
 }
 
+// Traversal counters of one thread (for the roofline accounting): the trace
+// kernels are compiled with Counters when the caller asked for counts and
+// with NoCounters, which costs nothing, otherwise.
 struct Counters {
+  static constexpr bool on = true;
   unsigned nodes = 0, tests = 0;
+  __device__ __forceinline__ void node() { ++nodes; }
+  __device__ __forceinline__ void test(int n) { tests += (unsigned)n; }
+};
+struct NoCounters {
+  static constexpr bool on = false;
+  unsigned nodes = 0, tests = 0;
+  __device__ __forceinline__ void node() {}
+  __device__ __forceinline__ void test(int) {}
 };
 
 // Stack entries name (instance, node or leaf): instance << 25 | leaf flag

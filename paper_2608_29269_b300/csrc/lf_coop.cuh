@@ -82,9 +82,9 @@ __device__ __forceinline__ int wentry(int ii, int code) {
 //   tlo(), thi()  culling interval of the ray
 //   leaf(g, ray, ii, first, count, I)  lanes c < count handle surfel first + c
 //   done(), abort()
-template <class V>
+template <class V, class Cnt>
 __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, int n_inst, const Ray& ray, V& vis,
-                                              const CStack& st, int* status, Counters& cnt) {
+                                              const CStack& st, int* status, Cnt& cnt) {
   int sp = 0;
   // instance boxes, WIDE at a time; instance 0 (background) ends up deepest
   for (int i0 = 0; i0 < n_inst; i0 += WIDE) {
@@ -129,7 +129,7 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
       const int ii = e >> 25;
       const Inst& I = insts[ii];
       if (e & LEAF_BIT) {
-        if (g.c == 0) cnt.tests += ec;
+        if (g.c == 0) cnt.test(ec);
         vis.leaf(g, ray, ii, e & 0xffffff, ec, I);
         if (vis.done()) return;
         break;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
         vis.abort();
         return;
       }
-      if (g.c == 0) ++cnt.nodes;
+      if (g.c == 0) cnt.node();
       const float4* node = I.wnodes + 2 * WIDE * (size_t)(e & 0xffffff);
       const float4 A = __ldg(node + g.c), Bx = __ldg(node + WIDE + g.c);
       const int code = __float_as_int(A.w), count = __float_as_int(Bx.w);
@@ -388,8 +388,9 @@ __device__ __forceinline__ float gsum(const Grp& g, float v) {
 // in front of each hit by a prefix product over the lanes, the stop at the
 // first hit whose transmittance behind it falls below T_min, weighted sums by
 // butterflies.  Every lane ends with the same Surface.
+template <class Cnt>
 __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, int n_inst, float3 o, float3 d,
-                                               const DevParams& P, const CStack& st, int* status, Counters& cnt,
+                                               const DevParams& P, const CStack& st, int* status, Cnt& cnt,
                                                Surface& s, unsigned& composited) {
   NearKCoop kb;
   kb.P = P;

@@ -12,6 +12,7 @@ constexpr int TILE_H = RGROUPS / TILE_W;
 
 // WIDE lanes per pixel: cooperative k-buffer composite of the primary ray
 // (lf_coop.cuh); lane 0 writes the G-buffer.
+template <class Cnt>
 __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
   extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
@@ -24,7 +25,7 @@ __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam
   float3 d = f3(0.f, 0.f, 0.f);
   if (g.c == 0) d = camera_dir(cam, p);  // FP64 once per pixel
   d = f3(gshfl(g, d.x, 0), gshfl(g, d.y, 0), gshfl(g, d.z, 0));
-  Counters cnt;
+  Cnt cnt;
   unsigned comp = 0;
   Surface s;
   coop_composite(g, a.insts, a.n_inst, cam.eye, d, a.P, st, a.status, cnt, s, comp);
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam
   gp[LF_CH_IDSTOP * P] = s.hits ? (float)(int)(s.stop_key & 0xffffffull) : -1.0f;
   gp[(LF_CH_DIR + 0) * P] = d.x; gp[(LF_CH_DIR + 1) * P] = d.y; gp[(LF_CH_DIR + 2) * P] = d.z;
   gp[LF_CH_STOPKEY_LO * P] = __uint_as_float((unsigned)(s.stop_key & 0xffffffffull));
-  if (a.counters) {  // slot 0 of the per-kernel counters: primary rays
+  if (Cnt::on && a.counters) {  // slot 0 of the per-kernel counters: primary rays
     atomicAdd(a.counters + 0, (unsigned long long)cnt.nodes);
     atomicAdd(a.counters + 1, (unsigned long long)cnt.tests);
     atomicAdd(a.counters + 2, (unsigned long long)comp);
@@ -56,7 +57,8 @@ __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam
 
 cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, cudaStream_t st) {
   dim3 grid((cam.W + TILE_W - 1) / TILE_W, (cam.H + TILE_H - 1) / TILE_H);
-  k_trace_primary<<<grid, TB, RSTACK_SMEM, st>>>(a, cam, gbuf);
+  if (a.counters) k_trace_primary<Counters><<<grid, TB, RSTACK_SMEM, st>>>(a, cam, gbuf);
+  else k_trace_primary<NoCounters><<<grid, TB, RSTACK_SMEM, st>>>(a, cam, gbuf);
   return cudaGetLastError();
 }
 

@@ -182,6 +182,7 @@ __device__ __forceinline__ int group_fetch(const Grp& g, int* cursor) {
   return gshfl(g, k, 0);
 }
 
+template <class Cnt>
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBatch B, DevParams P, SampleBuf S,
                                                                         int which, int* status,
                                                                         unsigned long long* counters) {
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
   const int* q = which == 0 ? S.qA : S.qC;
   const int n = which == 0 ? S.counts[0] : S.counts[2];
   int* cursor = S.counts + (which == 0 ? CURSOR_A : CURSOR_C);
-  Counters cnt;
+  Cnt cnt;
   for (int k = group_fetch(g, cursor); k < n; k = group_fetch(g, cursor)) {
     const int e = q[k];
     const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
       else S.Vq0[item] = v.V;
     }
   }
-  if (counters && g.c == 0) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
+  if (Cnt::on && counters && g.c == 0) {  // slot 1: NEE shadow rays, slot 3: secondary shadow rays
     unsigned long long* c = counters + 4 * (which == 0 ? 1 : 3);
     atomicAdd(c + 0, (unsigned long long)cnt.nodes);
     atomicAdd(c + 1, (unsigned long long)cnt.tests);
@@ -239,6 +240,7 @@ __device__ __forceinline__ float* rec_r2(const SampleBuf& S) { return S.Vq1; }
 // found a surface (then T2 < 1), the record for k_wf_secondary: the NEE
 // origin in xs2 and normal, base colour, metallic and roughness in planes
 // that k_wf_secondary and the secondary shadow rays overwrite afterwards.
+template <class Cnt>
 __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(ShadeBatch B, DevParams P, SampleBuf S,
                                                                             int* status,
                                                                             unsigned long long* counters) {
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
   const Grp g = make_grp();
   const CStack st = group_stack(s_cstack);
   const int n = S.counts[1];
-  Counters cnt;
+  Cnt cnt;
   unsigned comp = 0;
   for (int k = group_fetch(g, S.counts + CURSOR_B); k < n; k = group_fetch(g, S.counts + CURSOR_B)) {
     const long long item = S.qB[k];
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
       }
     }
   }
-  if (counters && g.c == 0) {  // slot 2: continuation rays
+  if (Cnt::on && counters && g.c == 0) {  // slot 2: continuation rays
     atomicAdd(counters + 8, (unsigned long long)cnt.nodes);
     atomicAdd(counters + 9, (unsigned long long)cnt.tests);
     atomicAdd(counters + 10, (unsigned long long)comp);
@@ -530,15 +532,17 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
   mark(1);
   // queue lengths are known only on the device: the trace kernels size
   // their loops from the counters (grids cover the worst case).
-  k_wf_shadow<<<resident_grid(k_wf_shadow, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
-      B, P, S, 0, status, counters);
+  // kernels compiled with counting only when the caller asked for counts
+  auto shadow = counters ? k_wf_shadow<Counters> : k_wf_shadow<NoCounters>;
+  auto cont = counters ? k_wf_continue<Counters> : k_wf_continue<NoCounters>;
+  shadow<<<resident_grid(shadow, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(B, P, S, 0, status,
+                                                                                              counters);
   mark(2);
-  k_wf_continue<<<resident_grid(k_wf_continue, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
-      B, P, S, status, counters);
+  cont<<<resident_grid(cont, B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(B, P, S, status, counters);
   k_wf_secondary<<<wf_grid(B.n_items, sms), WB, 0, st>>>(B, P, S);
   mark(3);
-  k_wf_shadow<<<resident_grid(k_wf_shadow, 2 * B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(
-      B, P, S, 1, status, counters);
+  shadow<<<resident_grid(shadow, 2 * B.n_items, sms, CSTACK_SMEM, WGROUPS), WB, CSTACK_SMEM, st>>>(B, P, S, 1,
+                                                                                                  status, counters);
   mark(4);
   k_wf_count<<<1, 32, 0, st>>>(S.counts, ray_count);
   return cudaGetLastError();
