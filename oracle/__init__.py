@@ -224,6 +224,46 @@ def rigid(scene, k, R, t):
     return out
 
 
+def assemble_state(canonical, R, t):
+    """Eq. 2: the scene S_k of one state from the shared canonical scene.  The
+    background (object 0) enters as it is; object o = 1..M is placed by
+    T_{k,o} = (R[o-1], t[o-1]) acting on its centres and tangent axes only,
+    evaluated as `rigid` does (FP64, one rounding per component)."""
+    R = np.asarray(R, np.float32).reshape(-1, 3, 3)
+    t = np.asarray(t, np.float32).reshape(-1, 3)
+    M = canonical.n_objects - 1
+    if len(R) != M or len(t) != M:
+        raise ValueError(f"need {M} object transforms")
+    out = canonical.copy()
+    for o in range(1, M + 1):
+        out = rigid(out, o, R[o - 1], t[o - 1])
+    return out
+
+
+def state_pullback(object_offsets, R, d_world):
+    """Adjoint of `assemble_state` (chain rule through Eq. 2): the gradient of
+    the canonical parameters given the gradient d_world (n, 17) of the state's
+    parameters, in the per-surfel layout mu 3 | tu 3 | tv 3 | scale 2 |
+    opacity | albedo 3 | metallic | roughness.  For a surfel of object o >= 1
+    the mu, tu and tv triples g become R^T g, (R^T g)_j = (R_0j g_0 + R_1j g_1)
+    + R_2j g_2 in FP64 (t drops out: it does not depend on the surfel); every
+    other entry, and every entry of the background, passes unchanged."""
+    R = np.asarray(R, np.float32).astype(np.float64).reshape(-1, 3, 3)
+    g = np.asarray(d_world, np.float64).reshape(-1, 17)
+    out = g.copy()
+    off = np.asarray(object_offsets)
+    if len(R) != len(off) - 2:
+        raise ValueError(f"need {len(off) - 2} object transforms")
+    for o in range(1, len(off) - 1):
+        lo, hi = int(off[o]), int(off[o + 1])
+        Ro = R[o - 1]
+        for a in (0, 3, 6):
+            x = g[lo:hi, a:a + 3]
+            for j in range(3):
+                out[lo:hi, a + j] = (Ro[0, j] * x[:, 0] + Ro[1, j] * x[:, 1]) + Ro[2, j] * x[:, 2]
+    return out
+
+
 def trace_rays(scene, env, origins, dirs, params=None):
     """Eq. 6-7 composite of explicit rays.  Returns (ch (n,NCH), margins (n,8))."""
     L = lib()

@@ -520,3 +520,89 @@ def test_moving_scene_and_camera_together_leaves_the_image_unchanged():
     assert ok.mean() > 0.8
     for k in ["T", "W", "depth", "a0", "a1", "a2", "rho0", "rho1", "rho2", "hits"]:
         np.testing.assert_allclose(a["ch"][ok, CH[k]], b["ch"][ok, CH[k]], atol=2e-4)
+
+
+# ---------------------------------------------------------------- Eq. 2 state assembly and its adjoint
+
+
+def _three_objects():
+    sc = scene_c1()
+    return Scene(sc.mu, sc.tu, sc.tv, sc.scale, sc.opacity, sc.albedo, sc.metallic, sc.roughness,
+                 np.array([0, 300, 650, sc.n], np.int32))
+
+
+def _flat17(sc):
+    return np.concatenate([sc.mu, sc.tu, sc.tv, sc.scale, sc.opacity[:, None], sc.albedo,
+                           sc.metallic[:, None], sc.roughness[:, None]], axis=1).astype(np.float64)
+
+
+_FIELD_OF_COLUMN = [("mu", 0), ("mu", 1), ("mu", 2), ("tu", 0), ("tu", 1), ("tu", 2), ("tv", 0), ("tv", 1),
+                    ("tv", 2), ("scale", 0), ("scale", 1), ("opacity", None), ("albedo", 0), ("albedo", 1),
+                    ("albedo", 2), ("metallic", None), ("roughness", None)]
+
+
+def _state_transforms():
+    R = np.stack([_rot_y(0.8), _rot_y(-2.3) @ np.array([[1, 0, 0], [0, 0.6, -0.8], [0, 0.8, 0.6]], np.float32)])
+    t = np.array([[0.3, -0.1, 0.25], [-0.4, 0.2, 0.05]], np.float32)
+    return R.astype(np.float32), t
+
+
+def test_state_assembly_moves_only_object_centres_and_axes():
+    sc = _three_objects()
+    R, t = _state_transforms()
+    st = oracle.assemble_state(sc, R, t)
+    for k in ["scale", "opacity", "albedo", "metallic", "roughness"]:
+        np.testing.assert_array_equal(getattr(st, k), getattr(sc, k))
+    for k in ["mu", "tu", "tv"]:  # the background B enters every state as it is
+        np.testing.assert_array_equal(getattr(st, k)[:300], getattr(sc, k)[:300])
+        assert not np.allclose(getattr(st, k)[300:650], getattr(sc, k)[300:650])
+    # identity transforms reproduce the canonical scene bit for bit
+    same = oracle.assemble_state(sc, np.stack([np.eye(3)] * 2), np.zeros((2, 3)))
+    np.testing.assert_array_equal(_flat17(same), _flat17(sc))
+    with pytest.raises(ValueError):
+        oracle.assemble_state(sc, R[:1], t[:1])
+
+
+def test_state_pullback_matches_finite_differences_of_the_assembly():
+    """The assembly is affine in the canonical parameters, so a central
+    difference of <c, S_k(x)> is exact up to the FP32 rounding of the moved
+    values; it must reproduce the pulled-back cotangent for every kind of
+    entry (moved centres and axes, shared attributes, background)."""
+    sc = _three_objects()
+    R, t = _state_transforms()
+    rng = np.random.default_rng(11)
+    c = rng.normal(size=(sc.n, 17))
+    g = oracle.state_pullback(sc.object_offsets, R, c)
+    h = 2.0 ** -6
+    picks = [(i, k) for i in (5, 299, 300, 477, 649, 650, 999) for k in range(17)]
+    for i, k in picks:
+        field, comp = _FIELD_OF_COLUMN[k]
+        vals = []
+        for sgn in (1.0, -1.0):
+            x = sc.copy()
+            arr = getattr(x, field)
+            if comp is None:
+                arr[i] += np.float32(sgn * h)
+            else:
+                arr[i, comp] += np.float32(sgn * h)
+            vals.append(float(np.sum(c * _flat17(oracle.assemble_state(x, R, t)))))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[i, k]) < 1e-4 * np.abs(c).max(), (i, k, fd, g[i, k])
+
+
+def test_state_pullback_special_cases():
+    sc = _three_objects()
+    rng = np.random.default_rng(12)
+    c = rng.normal(size=(sc.n, 17))
+    # identity transforms: the cotangent passes unchanged
+    np.testing.assert_array_equal(oracle.state_pullback(sc.object_offsets, np.stack([np.eye(3)] * 2), c), c)
+    # a quarter turn about +y maps canonical +z to world +x and canonical -x to world +z,
+    # so world-space gradients along +x and +z pull back to +z and -x
+    Q = np.array([[0, 0, 1], [0, 1, 0], [-1, 0, 0]], np.float32)
+    e = np.zeros((sc.n, 17))
+    e[400, 0] = 1.0   # d/d mu_x of a surfel of object 1
+    e[700, 5] = 1.0   # d/d tu_z of a surfel of object 2
+    g = oracle.state_pullback(sc.object_offsets, np.stack([Q, Q]), e)
+    np.testing.assert_array_equal(g[400, 0:3], [0.0, 0.0, 1.0])
+    np.testing.assert_array_equal(g[700, 3:6], [-1.0, 0.0, 0.0])
+    assert np.count_nonzero(g) == 2
