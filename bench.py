@@ -459,6 +459,7 @@ def main():
         "config": dict(workload(args.size, args.spp), parallelism=f"replicas x{world}",
                        l2="flushed between steps (256 MB write)"),
         "fwd_mrays_s": fwd_value,
+        "step_ms": {"median": statistics.median(per_step_ms), "min": min(per_step_ms), "max": max(per_step_ms)},
         "rays_per_step": rays_all / args.steps / world,
         "phase_ms": {n: round(v, 3) for n, v in avg.items()},
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",

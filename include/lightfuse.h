@@ -172,6 +172,36 @@ lf_status lf_scene_sync(lf_ctx* ctx, int object_id);
 lf_status lf_material_set(lf_ctx* ctx, int object_id, const float* rgb, float metallic, float roughness);
 
 /*
+ * Cross-state supervision (Sec. 3.2, "Cross-state supervision"; Eq. 2).  A
+ * single canonical scene holds the shared parameters; observed state k is
+ * S_k = B u T_{k,1}(O_1) u ... u T_{k,M}(O_M): the background (object 0) as
+ * it is and object o = 1..M moved by the rigid transform
+ * T_{k,o} = (R_{k,o}, t_{k,o}), which acts only on the surfel centres and
+ * tangent axes (mu = R mu^c + t, tu = R tu^c, tv = R tv^c).
+ *
+ * lf_state_assemble writes state k's mu, tu, tv into the scene the context
+ * was built on (each component in FP64 with exact products, one rounding, as
+ * lf_bvh_refit), copies scale, opacity and materials from `canonical` where
+ * its arrays are not the built scene's own (they may be shared), and refits
+ * every BLAS and the TLAS on the build's topology.  `canonical` is a
+ * caller-owned device scene with the built scene's n and object_offsets; its
+ * mu, tu, tv must not be the built scene's arrays.  R: host, (n_objects - 1)
+ * row-major 3x3 rotations for objects 1..M; t: host, (n_objects - 1) x 3.
+ * Errors: LF_ERR_NOT_BUILT before lf_bvh_build; LF_ERR_INVALID for a
+ * mismatched scene, aliased geometry arrays or a transform that is not
+ * rigid (nothing is enqueued then).
+ *
+ * lf_state_pullback is its adjoint, so that the residuals of every state
+ * update the same canonical surfels: d_canonical += J^T d_world over the
+ * LF_G_* layout (N x 17 FP32, device, caller-owned, must not overlap).  For
+ * a surfel of object o >= 1 the mu, tu and tv triples g add R^T g (FP64,
+ * one rounding, then an FP32 add); every other entry, and all of the
+ * background's, adds unchanged.  R as above (t does not enter).
+ */
+lf_status lf_state_assemble(lf_ctx* ctx, const lf_scene* canonical, const float* R, const float* t);
+lf_status lf_state_pullback(lf_ctx* ctx, const float* R, const float* d_world, float* d_canonical);
+
+/*
  * Register environment map `env_id` (0 <= env_id < LF_MAX_ENVS): H x W x 3 FP32
  * texels, row 0 looking up (+y), column 0 at phi = 0 of the y-up
  * equirectangular mapping theta = acos(w_y), phi = atan2(w_x, -w_z) + pi.

@@ -68,6 +68,8 @@ SIGNATURES = [
     ("lf_bvh_refit", C.c_int, [_P, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     ("lf_scene_sync", C.c_int, [_P, C.c_int]),
     ("lf_material_set", C.c_int, [_P, C.c_int, C.POINTER(C.c_float), C.c_float, C.c_float]),
+    ("lf_state_assemble", C.c_int, [_P, C.POINTER(LfScene), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    ("lf_state_pullback", C.c_int, [_P, C.POINTER(C.c_float), _P, _P]),
     ("lf_env_set", C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int]),
     ("lf_trace_primary", C.c_int, [_P, C.POINTER(LfCamera), C.c_int, _P]),
     ("lf_shade_scratch_bytes", C.c_size_t, [C.c_int, C.c_int, C.c_int]),

@@ -153,6 +153,21 @@ TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id) {
 
 CamDev lf_ctx_cam(const lf_camera& c) { return to_cam(c); }
 
+// R must be a rotation (R R^T = I, det = +1, within FP32 tolerance) and t finite.
+bool lf_is_rigid(const float R[9], const float t[3]) {
+  double dmax = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < 3; ++m) s += (double)R[3 * i + m] * R[3 * j + m];
+      dmax = std::max(dmax, std::fabs(s - (i == j ? 1.0 : 0.0)));
+    }
+  double det = (double)R[0] * (R[4] * R[8] - R[5] * R[7]) - (double)R[1] * (R[3] * R[8] - R[5] * R[6]) +
+               (double)R[2] * (R[3] * R[7] - R[4] * R[6]);
+  return dmax < 1e-4 && std::fabs(det - 1.0) < 1e-4 && (!t || (std::isfinite(t[0]) && std::isfinite(t[1]) &&
+                                                             std::isfinite(t[2])));
+}
+
 extern "C" {
 
 lf_status lf_params_default(lf_params* p) {
@@ -381,19 +396,7 @@ lf_status lf_bvh_refit(lf_ctx* c, int k, const float R[9], const float t[3]) {
   if (!c || !R || !t) return LF_ERR_INVALID;
   if (!c->built) return fail(c, LF_ERR_NOT_BUILT, "no BVH");
   if (k < 0 || k >= c->n_obj) return fail(c, LF_ERR_INVALID, "bad object id");
-  // R must be a rotation: R R^T = I, det = +1 (within FP32 tolerance)
-  double dmax = 0.0;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
-      for (int m = 0; m < 3; ++m) s += (double)R[3 * i + m] * R[3 * j + m];
-      dmax = std::max(dmax, std::fabs(s - (i == j ? 1.0 : 0.0)));
-    }
-  double det = (double)R[0] * (R[4] * R[8] - R[5] * R[7]) - (double)R[1] * (R[3] * R[8] - R[5] * R[6]) +
-               (double)R[2] * (R[3] * R[7] - R[4] * R[6]);
-  if (!(dmax < 1e-4) || !(std::fabs(det - 1.0) < 1e-4) || !std::isfinite(t[0]) || !std::isfinite(t[1]) ||
-      !std::isfinite(t[2]))
-    return fail(c, LF_ERR_INVALID, "transform is not rigid");
+  if (!lf_is_rigid(R, t)) return fail(c, LF_ERR_INVALID, "transform is not rigid");
   Mat34 T;
   std::memcpy(T.R, R, sizeof(T.R));
   std::memcpy(T.t, t, sizeof(T.t));

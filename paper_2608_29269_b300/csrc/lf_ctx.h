@@ -63,6 +63,8 @@ struct lf_ctx {
   EnvSlot env[LF_MAX_ENVS];
 };
 
+// R (row-major 3x3) is a rotation within FP32 tolerance and t (nullable) is finite (lf_api.cu).
+bool lf_is_rigid(const float R[9], const float t[3]);
 // Repack + refit objects [first_obj, last_obj] (lf_api.cu).
 lf_status lf_ctx_fit(lf_ctx* c, int first_obj, int last_obj);
 lf::TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id);

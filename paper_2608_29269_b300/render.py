@@ -45,6 +45,55 @@ class SurfelRender(torch.autograd.Function):
         return (None, None, None, None, None, d_env, *grads)
 
 
+class StateRender(torch.autograd.Function):
+    """rgb, gbuf = StateRender.apply(tracer, canonical, R, t, cam, env_id, spp, seed, env_rgb, *canonical.tensors())
+
+    Cross-state supervision (Sec. 3.2): state k of the shared canonical scene
+    is assembled by Eq. 2 (objects 1..M at (R[o-1], t[o-1])) into the scene
+    the tracer was built on, rendered, and its gradient carried back to the
+    canonical parameters, so the residuals of every state accumulate on the
+    same surfels.  The backward re-assembles its state when another state was
+    assembled since its forward.
+    """
+
+    @staticmethod
+    def forward(ctx, tracer: Tracer, canonical, R, t, cam, env_id: int, spp: int, seed: int, env_rgb, *params):
+        tracer.assemble_state(canonical, R, t)
+        token = tracer.state_token
+        gbuf = tracer.trace_primary(cam, env_id)
+        samples = tracer.alloc_samples(cam, spp)
+        rgb = tracer.shade(cam, gbuf, env_id, spp, seed, samples=samples)
+        ctx.tracer, ctx.canonical, ctx.R, ctx.t, ctx.token = tracer, canonical, R, t, token
+        ctx.cam, ctx.env_id, ctx.spp, ctx.seed = cam, env_id, spp, seed
+        ctx.save_for_backward(gbuf, env_rgb, samples)
+        ctx.mark_non_differentiable(gbuf)
+        return rgb, gbuf
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_gbuf):
+        gbuf, env_rgb, samples = ctx.saved_tensors
+        tr = ctx.tracer
+        if tr.state_token != ctx.token:
+            tr.assemble_state(ctx.canonical, ctx.R, ctx.t)
+        d_world = torch.zeros((tr.scene.n, N.G_STRIDE), device=gbuf.device, dtype=torch.float32)
+        d_env = torch.zeros_like(env_rgb) if ctx.needs_input_grad[8] else None
+        tr.backward(ctx.cam, gbuf, ctx.env_id, ctx.spp, ctx.seed,
+                    dL_drgb=g_rgb.contiguous() if g_rgb is not None else None,
+                    dL_dgbuf=None, d_surfel=d_world, d_env=d_env, fwd_samples=samples)
+        d_can = torch.zeros_like(d_world)
+        tr.state_pullback(ctx.R, d_world, d_can)
+        grads = []
+        for k in SCENE_FIELDS:
+            a, b = GRAD_SLICES[k]
+            grads.append(d_can[:, a:b].reshape(getattr(ctx.canonical, k).shape))
+        return (None, None, None, None, None, None, None, None, d_env, *grads)
+
+
+def render_state(tracer: Tracer, canonical, R, t, cam, env_id: int = 0, spp: int = 16, seed: int = 0):
+    return StateRender.apply(tracer, canonical, R, t, cam, env_id, spp, seed, tracer.envs[env_id],
+                             *canonical.tensors())
+
+
 def render(tracer: Tracer, cam, env_id: int = 0, spp: int = 16, seed: int = 0):
     s = tracer.scene
     return SurfelRender.apply(tracer, cam, env_id, spp, seed, tracer.envs[env_id], *s.tensors())

@@ -98,6 +98,7 @@ class Tracer:
         self.scene: Optional[SceneTensors] = None
         self.envs = {}
         self._counters = None
+        self.state_token = 0  # counts lf_state_assemble calls
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -118,6 +119,14 @@ class Tracer:
 
     # ------------------------------------------------------------ scene
     def build(self, scene: SceneTensors):
+        s, arr = self._scene_struct(scene)
+        self.check(self.lib.lf_bvh_build(self.ctx, C.byref(s)))
+        self.state_token += 1
+        self.scene = scene
+        self._offsets = list(arr)
+
+    @staticmethod
+    def _scene_struct(scene: SceneTensors):
         for k in SCENE_FIELDS:
             t = getattr(scene, k)
             if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
@@ -126,15 +135,44 @@ class Tracer:
                 raise ValueError(f"{k}: expected {scene.n} x {SCENE_WIDTH[k]} values")
         offs = list(scene.object_offsets) or [0, scene.n]
         arr = (C.c_int * len(offs))(*offs)
-        s = N.LfScene(*[_ptr(getattr(scene, k)) for k in SCENE_FIELDS], scene.n, arr, len(offs) - 1)
-        self.check(self.lib.lf_bvh_build(self.ctx, C.byref(s)))
-        self.scene = scene
-        self._offsets = offs
+        return N.LfScene(*[_ptr(getattr(scene, k)) for k in SCENE_FIELDS], scene.n, arr, len(offs) - 1), arr
+
+    def _state_transforms(self, R, t=None):
+        m = len(self._offsets) - 2
+        Rv = torch.as_tensor(R, dtype=torch.float32).reshape(-1).tolist()
+        if len(Rv) != 9 * m:
+            raise ValueError(f"expected {m} rotations (objects 1..{m})")
+        Rf = (C.c_float * max(1, 9 * m))(*Rv)
+        if t is None:
+            return Rf, None
+        tv = torch.as_tensor(t, dtype=torch.float32).reshape(-1).tolist()
+        if len(tv) != 3 * m:
+            raise ValueError(f"expected {m} translations (objects 1..{m})")
+        return Rf, (C.c_float * max(1, 3 * m))(*tv)
+
+    def assemble_state(self, canonical: SceneTensors, R, t):
+        """Eq. 2: write the state whose objects 1..M sit at (R[o-1], t[o-1])
+        into the built scene from the canonical (shared) parameters, and refit."""
+        s, _keep = self._scene_struct(canonical)
+        Rf, tf = self._state_transforms(R, t)
+        self.check(self.lib.lf_state_assemble(self.ctx, C.byref(s), Rf, tf))
+        self.state_token += 1
+
+    def state_pullback(self, R, d_world: torch.Tensor, d_canonical: torch.Tensor):
+        """d_canonical += the state's per-surfel gradient d_world carried back
+        through Eq. 2 (both N x 17)."""
+        self._check_dev(d_world, d_canonical)
+        n = self.scene.n
+        if d_world.numel() != n * N.G_STRIDE or d_canonical.numel() != n * N.G_STRIDE:
+            raise ValueError(f"expected {n} x {N.G_STRIDE} gradients")
+        Rf, _ = self._state_transforms(R)
+        self.check(self.lib.lf_state_pullback(self.ctx, Rf, _ptr(d_world), _ptr(d_canonical)))
 
     def refit(self, object_id: int, R, t):
         Rf = (C.c_float * 9)(*[float(v) for v in torch.as_tensor(R).reshape(-1).tolist()])
         tf = (C.c_float * 3)(*[float(v) for v in torch.as_tensor(t).reshape(-1).tolist()])
         self.check(self.lib.lf_bvh_refit(self.ctx, int(object_id), Rf, tf))
+        self.state_token += 1
 
     def sync_scene(self, object_id: int = -1):
         self.check(self.lib.lf_scene_sync(self.ctx, int(object_id)))

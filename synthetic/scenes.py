@@ -56,10 +56,17 @@ class Scene:
         return Scene(**{k: v.copy() for k, v in self.arrays().items()},
                      object_offsets=self.object_offsets.copy())
 
-    def subset(self, idx) -> "Scene":
+    def subset(self, idx, keep_objects: bool = False) -> "Scene":
+        """Surfels idx as one object, or (keep_objects, idx sorted) each in its
+        original object."""
         idx = np.asarray(idx)
-        return Scene(**{k: np.ascontiguousarray(v[idx]) for k, v in self.arrays().items()},
-                     object_offsets=np.array([0, len(idx)], np.int32))
+        if keep_objects:
+            if np.any(np.diff(idx) <= 0):
+                raise ValueError("keep_objects needs sorted, distinct indices")
+            offs = np.searchsorted(idx, self.object_offsets).astype(np.int32)
+        else:
+            offs = np.array([0, len(idx)], np.int32)
+        return Scene(**{k: np.ascontiguousarray(v[idx]) for k, v in self.arrays().items()}, object_offsets=offs)
 
 
 @dataclass
@@ -296,8 +303,9 @@ def camera_c4(width: int = 1024, height: int = 1024) -> Camera:
     return Camera((0.0, -0.2, 1.9), (0.0, -1.5, -0.2), (0.0, 1.0, 0.0), 60.0, width, height)
 
 
-def scene_c3_subset(scene: Scene, cam: Camera, n: int = 512, seed: int = 0) -> Scene:
-    """First n surfels of a seeded permutation whose centres lie in the view cone."""
+def scene_c3_subset(scene: Scene, cam: Camera, n: int = 512, seed: int = 0, keep_objects: bool = False) -> Scene:
+    """First n surfels of a seeded permutation whose centres lie in the view
+    cone (as one object, or each in its original object)."""
     rng = np.random.default_rng(seed)
     eye = np.asarray(cam.eye)
     fwd = np.asarray(cam.target) - eye
@@ -306,7 +314,7 @@ def scene_c3_subset(scene: Scene, cam: Camera, n: int = 512, seed: int = 0) -> S
     cosang = (v @ fwd) / np.linalg.norm(v, axis=1)
     inside = np.nonzero(cosang > np.cos(np.radians(0.45 * cam.fovy_deg)))[0]
     pick = rng.permutation(inside)[:n]
-    return scene.subset(np.sort(pick))
+    return scene.subset(np.sort(pick), keep_objects=keep_objects)
 
 
 def perturb_scene(scene: Scene, seed: int = 1, sigma_mu: float = 0.01, shift: float = 0.1) -> Scene:
