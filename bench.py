@@ -430,12 +430,12 @@ def main():
     hbm, peak_kind = read_peaks()
     avg = {n: statistics.mean(v) for n, v in phase_ms.items()}
     kavg = {n: statistics.mean(v) for n, v in kern_ms.items()}
-    # algorithmic bytes per launch: node visits x node bytes (a wide node is WIDE slots of 32 B),
+    # algorithmic bytes per launch: node visits x node bytes (a wide node: a 16 B header and WIDE slots of 16 B),
     # surfel tests x 48 B (the quick-test quads of the packed record), composited hits x 80 B (the
     # record's fourth quad read by the precise test, two quads and the 16 B material read by the
     # composite), plus each kernel's per-ray input and output
-    wide = step.tr.bvh_wide(0)[0].shape[1]
-    node_bytes = {n: 32 * wide for n in ["primary", "nee_shadow", "continuation", "secondary_shadow"]}
+    wnode = step.tr.lib.lf_bvh_wide_node_bytes()
+    node_bytes = {n: wnode for n in ["primary", "nee_shadow", "continuation", "secondary_shadow"]}
     per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32}
     kbytes = {n: node_bytes[n] * counters[n][0] + 48 * counters[n][1] + 80 * counters[n][2] +
               per_ray_io[n] * counters[n][3] for n in per_ray_io}

@@ -378,14 +378,19 @@ lf_status lf_env_tables(lf_ctx* ctx, int env_id, float* pmf_row_dev, float* cdf_
  * its nodes (16 floats each: child boxes and child codes, see the build). */
 lf_status lf_bvh_info(lf_ctx* ctx, int object_id, int* n_internal, int* root_code);
 lf_status lf_bvh_copy_nodes(lf_ctx* ctx, int object_id, float* host_out, size_t bytes);
-/* Wide BVH inspection: host copy of object k's wide-node storage (capacity
- * *cap_nodes nodes; a node is *wide quads (lo.xyz, child code as int bits)
- * followed by *wide quads (hi.xyz, leaf surfel count as int bits), one pair
- * per child slot), and its root (code >= 0 wide node, < 0 leaf of
+/* Wide BVH inspection: host copy of object k's wide nodes, decoded
+ * (capacity *cap_nodes nodes; a node is *wide quads (lo.xyz, child code as
+ * int bits) followed by *wide quads (hi.xyz, leaf surfel count as int bits),
+ * one pair per child slot; compressed boxes are decoded rounding outward, so
+ * each contains the box the traversal tests), and its root (code >= 0 wide node, < 0 leaf of
  * *root_count surfels from leaf ~code, INT_MIN empty).  host_out may be NULL
  * to query the sizes only. */
 lf_status lf_bvh_copy_wide(lf_ctx* ctx, int object_id, float* host_out, size_t bytes, int* cap_nodes, int* root_code,
                            int* root_count, int* wide);
+/* Bytes one wide node occupies on the device (the traversal reads all of them
+ * per node visit): a 16-byte header plus 16 bytes per child slot (FP16 boxes
+ * relative to the node centre), or 32 bytes per slot in the FP32 build. */
+int lf_bvh_wide_node_bytes(void);
 
 /* ---------------------------------------------------------------- serving
  *

@@ -92,6 +92,7 @@ SIGNATURES = [
                                    C.c_size_t, C.POINTER(C.c_double)]),
     ("lf_env_tables", C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     ("lf_bvh_info", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("lf_bvh_wide_node_bytes", C.c_int, []),
     ("lf_bvh_copy_wide", C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("lf_bvh_copy_nodes", C.c_int, [_P, C.c_int, _P, C.c_size_t]),

@@ -316,7 +316,7 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     if (e == cudaSuccess) e = dev_alloc(&c->node_range, cap);
     // wide nodes: the sum over objects of wide_capacity(n_k) is at most wide_capacity(cap) + 2 LF_MAX_OBJECTS
     const size_t wcap = (size_t)wide_capacity((int)std::min<size_t>(cap, 1u << 30)) + 2 * LF_MAX_OBJECTS;
-    if (e == cudaSuccess) e = dev_alloc(&c->wnodes, 2 * WIDE * wcap);
+    if (e == cudaSuccess) e = dev_alloc(&c->wnodes, WNODE_Q * wcap);
     if (e == cudaSuccess) e = dev_alloc(&c->wsrc, WIDE * wcap);
     if (e == cudaSuccess) e = dev_alloc(&c->wqueue, wcap);
     c->wcap = wcap;
@@ -357,7 +357,7 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     I.mat = c->mat + (size_t)c->offsets[k];
     I.id_base = c->offsets[k];
     I.pad = 0;
-    I.wnodes = c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k];
+    I.wnodes = c->wnodes + WNODE_Q * (size_t)c->wnode_off_h[k];
     I.wroot = nk > WLEAF ? 0 : (nk >= 1 ? ~0 : INT_MIN);
     I.wroot_count = nk > WLEAF ? 0 : nk;
   }
@@ -596,6 +596,8 @@ lf_status lf_bvh_copy_nodes(lf_ctx* c, int k, float* host_out, size_t bytes) {
   return LF_OK;
 }
 
+int lf_bvh_wide_node_bytes(void) { return (int)(WNODE_Q * sizeof(float4)); }
+
 lf_status lf_bvh_copy_wide(lf_ctx* c, int k, float* host_out, size_t bytes, int* cap_nodes, int* root_code,
                            int* root_count, int* wide) {
   if (!c) return LF_ERR_INVALID;
@@ -610,8 +612,51 @@ lf_status lf_bvh_copy_wide(lf_ctx* c, int k, float* host_out, size_t bytes, int*
   const size_t need = nn * 2 * WIDE * sizeof(float4);
   if (bytes < need) return fail(c, LF_ERR_INVALID, "buffer too small");
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (nn)
-    LF_CUDA(c, cudaMemcpy(host_out, c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k], need, cudaMemcpyDeviceToHost));
+  if (!nn) return LF_OK;
+#if LF_WIDE_FP16
+  // decode the compressed slots into the inspection layout; each corner is
+  // centre + offset rounded outward, a box containing the one traversal tests
+  std::vector<float4> raw(nn * WNODE_Q);
+  LF_CUDA(c, cudaMemcpy(raw.data(), c->wnodes + WNODE_Q * (size_t)c->wnode_off_h[k], raw.size() * sizeof(float4),
+                        cudaMemcpyDeviceToHost));
+  auto half_at = [](unsigned word, int hi16) {
+    return (double)__half2float(__ushort_as_half((unsigned short)(hi16 ? word >> 16 : word & 0xffffu)));
+  };
+  auto outward = [](double v, bool up) {
+    float f = (float)v;
+    if (up && (double)f < v) f = std::nextafter(f, INFINITY);
+    if (!up && (double)f > v) f = std::nextafter(f, -INFINITY);
+    return f;
+  };
+  float4* out = reinterpret_cast<float4*>(host_out);
+  for (size_t w = 0; w < nn; ++w) {
+    const float4 H = raw[WNODE_Q * w];
+    for (int s = 0; s < WIDE; ++s) {
+      const float4 q = raw[WNODE_Q * w + 1 + s];
+      unsigned u[4];
+      std::memcpy(u, &q, sizeof(u));
+      int code = INT_MIN, count = 0;
+      if (u[3] != WSLOT_EMPTY) {
+        if ((int)u[3] >= 0) {
+          code = (int)u[3];
+        } else {
+          count = (int)((u[3] >> 24) & 31u) + 1;
+          code = ~(int)(u[3] & 0xffffffu);
+        }
+      }
+      const double lo[3] = {H.x + half_at(u[0], 0), H.y + half_at(u[0], 1), H.z + half_at(u[1], 0)};
+      const double hi[3] = {H.x + half_at(u[1], 1), H.y + half_at(u[2], 0), H.z + half_at(u[2], 1)};
+      float4 L = make_float4(outward(lo[0], false), outward(lo[1], false), outward(lo[2], false), 0.0f);
+      float4 U = make_float4(outward(hi[0], true), outward(hi[1], true), outward(hi[2], true), 0.0f);
+      std::memcpy(&L.w, &code, sizeof(int));
+      std::memcpy(&U.w, &count, sizeof(int));
+      out[2 * WIDE * w + s] = L;
+      out[2 * WIDE * w + WIDE + s] = U;
+    }
+  }
+#else
+  LF_CUDA(c, cudaMemcpy(host_out, c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k], need, cudaMemcpyDeviceToHost));
+#endif
   return LF_OK;
 }
 

@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
   const int wb = a.wnode_off[obj];                     // wide nodes, global numbering
   const int cap = a.wnode_off[obj + 1] - wb;
   const float4* bnodes = a.nodes + 4 * (size_t)(nb - a.node_base);
-  float4* wn = a.wnodes + 2 * WIDE * (size_t)(wb - a.wnode_base);
+  float4* wn = a.wnodes + WNODE_Q * (size_t)(wb - a.wnode_base);
   int* wsrc = a.wsrc + WIDE * (size_t)(wb - a.wsrc_base);
   int* queue = a.wqueue + (wb - a.wnode_base);
   if (threadIdx.x == 0) queue[0] = 0;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
       if (total + chunk_total > cap) {
         overflow = true;  // uniform: every thread read the same scan total
       } else if (valid) {
-        float4* node = wn + 2 * WIDE * (size_t)item;
+        float4* node = wn + WNODE_Q * (size_t)item;
         for (int c = 0; c < WIDE; ++c) {
           int cd = INT_MIN, ct = 0, sr = -1;
           if (c < nc) {
@@ -431,8 +431,15 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
               ct = cnt[c];
             }
           }
+#if LF_WIDE_FP16
+          const unsigned word = cd == INT_MIN ? WSLOT_EMPTY
+                                : cd >= 0   ? (unsigned)cd
+                                            : (0x80000000u | ((unsigned)(ct - 1) << 24) | (unsigned)~cd);
+          reinterpret_cast<uint4*>(node)[1 + c] = make_uint4(0u, 0u, 0u, word);
+#else
           node[c] = make_float4(1.0f, 1.0f, 1.0f, __int_as_float(cd));
           node[WIDE + c] = make_float4(-1.0f, -1.0f, -1.0f, __int_as_float(ct));
+#endif
           wsrc[WIDE * item + c] = sr;
         }
       }
@@ -446,21 +453,66 @@ __global__ void __launch_bounds__(COLLAPSE_THREADS) k_collapse(WideArgs a) {
 }
 
 // Box of every wide slot from the binary node holding it (build and refit).
+#if LF_WIDE_FP16
+// Compressed slots: one warp per wide node (slots of a node are WIDE
+// consecutive threads; first_slot and n_slots are multiples of WIDE).  The
+// node's centre is the centre of the union of its slot boxes; each corner is
+// stored as an FP16 offset from it, rounded down (lo) or up (hi) after a
+// subtraction rounded the same way, so the decoded box contains the slot's
+// FP32 box.
+__device__ __forceinline__ unsigned pack_h2(__half lo_half, __half hi_half) {
+  return (unsigned)__half_as_ushort(lo_half) | ((unsigned)__half_as_ushort(hi_half) << 16);
+}
+#endif
+
 __global__ void k_wide_boxes(WideArgs a, int n_slots) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_slots) return;
   const int slot = a.first_slot + k;
   const int sr = a.wsrc[slot - WIDE * a.wsrc_base];
+  const int local = slot - WIDE * a.wnode_base;  // node * WIDE + c in the storage
+#if LF_WIDE_FP16
+  static_assert(WIDE == 32, "one warp per wide node");
+  float b[6] = {BIG_F, BIG_F, BIG_F, -BIG_F, -BIG_F, -BIG_F};
+  if (sr >= 0) {
+    const int obj = object_of(a.wnode_off, a.n_obj_total, slot / WIDE);
+    const int nb = a.node_off[obj] - a.node_base;
+    const float* f = reinterpret_cast<const float*>(a.nodes + 4 * (size_t)(nb + (sr >> 1))) + ((sr & 1) ? 6 : 0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) b[q] = f[q];
+  }
+  float u[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) u[q] = b[q];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      u[q] = fminf(u[q], __shfl_xor_sync(0xffffffffu, u[q], off));
+      u[q + 3] = fmaxf(u[q + 3], __shfl_xor_sync(0xffffffffu, u[q + 3], off));
+    }
+  const float cx = 0.5f * (u[0] + u[3]), cy = 0.5f * (u[1] + u[4]), cz = 0.5f * (u[2] + u[5]);
+  float4* node = a.wnodes + WNODE_Q * (size_t)(local / WIDE);
+  if ((local % WIDE) == 0) node[0] = make_float4(cx, cy, cz, 0.0f);
+  if (sr < 0) return;
+  const __half lx = __float2half_rd(__fsub_rd(b[0], cx)), ly = __float2half_rd(__fsub_rd(b[1], cy)),
+               lz = __float2half_rd(__fsub_rd(b[2], cz));
+  const __half hx = __float2half_ru(__fsub_ru(b[3], cx)), hy = __float2half_ru(__fsub_ru(b[4], cy)),
+               hz = __float2half_ru(__fsub_ru(b[5], cz));
+  uint4* w = reinterpret_cast<uint4*>(node) + 1 + (local % WIDE);
+  const unsigned word = w->w;
+  *w = make_uint4(pack_h2(lx, ly), pack_h2(lz, hx), pack_h2(hy, hz), word);
+#else
   if (sr < 0) return;
   const int obj = object_of(a.wnode_off, a.n_obj_total, slot / WIDE);
   const int nb = a.node_off[obj] - a.node_base;
   const float* f = reinterpret_cast<const float*>(a.nodes + 4 * (size_t)(nb + (sr >> 1)));
   const int o = (sr & 1) ? 6 : 0;
-  const int local = slot - WIDE * a.wnode_base;  // node * WIDE + c in the storage
   float4* w = a.wnodes + 2 * (size_t)WIDE * (local / WIDE) + (local % WIDE);
   const float4 p = w[0], q = w[WIDE];
   w[0] = make_float4(f[o + 0], f[o + 1], f[o + 2], p.w);
   w[WIDE] = make_float4(f[o + 3], f[o + 4], f[o + 5], q.w);
+#endif
 }
 
 // ---------------------------------------------------------------- rigid transform

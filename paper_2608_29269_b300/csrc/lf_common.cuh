@@ -10,10 +10,17 @@
 //   BVH2 node (64 B, child boxes stored in the parent):
 //     n0 = (L.lo.xyz, L.hi.x)  n1 = (L.hi.yz, R.lo.xy)  n2 = (R.lo.z, R.hi.xyz)
 //     n3 = (left code, right code, -, -) ; code >= 0 internal node, code < 0 leaf ~code
-//   Wide node (WIDE child slots; lane c of a ray's warp reads slot c): WIDE
-//     quads (lo.xyz, code) then WIDE quads (hi.xyz, count); code >= 0 wide
-//     node, code < 0 leaf of `count` consecutive surfels from ~code, INT_MIN empty
+//   Wide node (WIDE child slots; lane c of a ray's warp reads slot c):
+//     LF_WIDE_FP16 = 1: a header quad (centre.xyz of the node's box, 0), then
+//       one quad per slot: (lo.xy, lo.z hi.x, hi.yz) as FP16 pairs relative to
+//       the centre, rounded outward, and the slot word; slot word >= 0 wide
+//       node, WSLOT_EMPTY empty, else a leaf: bit 31 | (count - 1) << 24 |
+//       first surfel (24 bits)
+//     LF_WIDE_FP16 = 0: WIDE quads (lo.xyz, code) then WIDE quads (hi.xyz,
+//       count); code >= 0 wide node, code < 0 leaf of `count` consecutive
+//       surfels from ~code, INT_MIN empty
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +37,18 @@ constexpr int WIDE = LF_KBUF;
 #endif
 constexpr int WLEAF = LF_WIDE_LEAF;
 static_assert(WLEAF >= 1 && WLEAF <= WIDE, "a leaf is tested by at most WIDE lanes");
+// Wide-node format: FP16 child boxes relative to the node centre (16 B per
+// slot) or FP32 boxes (32 B per slot).
+#ifndef LF_WIDE_FP16
+#define LF_WIDE_FP16 0
+#endif
+#if LF_WIDE_FP16
+constexpr int WNODE_Q = WIDE + 1;  // float4 quads per wide node
+static_assert(WLEAF <= 32, "leaf counts take 5 bits of the slot word");
+#else
+constexpr int WNODE_Q = 2 * WIDE;
+#endif
+constexpr unsigned WSLOT_EMPTY = 0xffffffffu;
 constexpr float PI_F = 3.14159265358979323846f;
 constexpr float INV_PI_F = 0.318309886183790671538f;
 constexpr float INV_2PI_F = 0.159154943091895335769f;
@@ -568,6 +587,27 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
   float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
   tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
   float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
+  return tnear <= tfar;
+}
+
+// Slab test of a compressed wide slot: FP16 box corners relative to the node
+// centre H (rounded outward when packed).  The plane distances are
+// (H + rel - o) / d = rel * inv + (H * inv - o * inv): one FMA per plane after
+// the node's three centre terms.
+__device__ __forceinline__ float2 h2_bits(unsigned u) {  // low half -> .x
+  return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(u & 0xffffu)),
+                                       __ushort_as_half((unsigned short)(u >> 16))));
+}
+__device__ __forceinline__ bool slab_rel(const uint4& S, const float4& H, const Ray& r, float tlo, float thi,
+                                         float& tnear) {
+  const float cx = fmaf(H.x, r.inv.x, -r.oinv.x), cy = fmaf(H.y, r.inv.y, -r.oinv.y),
+              cz = fmaf(H.z, r.inv.z, -r.oinv.z);
+  const float2 lxy = h2_bits(S.x), lzhx = h2_bits(S.y), hyz = h2_bits(S.z);
+  const float tx0 = fmaf(lxy.x, r.inv.x, cx), tx1 = fmaf(lzhx.y, r.inv.x, cx);
+  const float ty0 = fmaf(lxy.y, r.inv.y, cy), ty1 = fmaf(hyz.x, r.inv.y, cy);
+  const float tz0 = fmaf(lzhx.x, r.inv.z, cz), tz1 = fmaf(hyz.y, r.inv.z, cz);
+  tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
+  const float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
   return tnear <= tfar;
 }
 

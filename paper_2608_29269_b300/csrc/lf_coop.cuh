@@ -140,11 +140,23 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
         return;
       }
       if (g.c == 0) cnt.node();
-      const float4* node = I.wnodes + 2 * WIDE * (size_t)(e & 0xffffff);
+      const float4* node = I.wnodes + WNODE_Q * (size_t)(e & 0xffffff);
+#if LF_WIDE_FP16
+      const float4 H = __ldg(node);
+      const uint4 S = __ldg(reinterpret_cast<const uint4*>(node + 1 + g.c));
+      int code = (int)S.w, count = 0;
+      if (code < 0) {  // leaf: count and first surfel from the slot word
+        count = ((code >> 24) & 31) + 1;
+        code = ~(code & 0xffffff);
+      }
+      float tn = 0.0f;
+      const bool hit = S.w != WSLOT_EMPTY && slab_rel(S, H, ray, vis.tlo(), vis.thi(), tn);
+#else
       const float4 A = __ldg(node + g.c), Bx = __ldg(node + WIDE + g.c);
       const int code = __float_as_int(A.w), count = __float_as_int(Bx.w);
       float tn = 0.0f;
       const bool hit = code != INT_MIN && slab(A.x, A.y, A.z, Bx.x, Bx.y, Bx.z, ray, vis.tlo(), vis.thi(), tn);
+#endif
       const unsigned m = gballot(g, hit);
       if (m == 0u) break;
       // nearest child: smallest entry distance (positive floats order as their bits)

@@ -156,7 +156,7 @@ size_t frame_bytes_of(const lf_camera& c, int spp) {
 
 size_t version_bytes(int n) {
   return sizeof(float) * RAW_FLOATS * (size_t)n + sizeof(float4) * (GEO + 1 + 4) * (size_t)n +
-         sizeof(float4) * 2 * WIDE * (size_t)wide_capacity(n) + sizeof(int) * (size_t)n + sizeof(Inst) + 1280;
+         sizeof(float4) * WNODE_Q * (size_t)wide_capacity(n) + sizeof(int) * (size_t)n + sizeof(Inst) + 1280;
 }
 
 // New version of object k: copy the current one, apply the edit, repack and
@@ -178,7 +178,7 @@ lf_status make_version(lf_serve* s, const lf_edit& e, Version** out) {
   v->mat = reinterpret_cast<float4*>(take(sizeof(float4) * n));
   v->nodes = reinterpret_cast<float4*>(take(sizeof(float4) * 4 * std::max(1, n - 1)));
   const int nw = c->wnode_off_h[k + 1] - c->wnode_off_h[k];
-  v->wnodes = reinterpret_cast<float4*>(take(sizeof(float4) * 2 * WIDE * std::max(1, nw)));
+  v->wnodes = reinterpret_cast<float4*>(take(sizeof(float4) * WNODE_Q * std::max(1, nw)));
   v->flags = reinterpret_cast<int*>(take(sizeof(int) * n));
   v->inst = reinterpret_cast<Inst*>(take(sizeof(Inst)));
   // copy attributes, nodes (child codes) and the instance entry
@@ -201,7 +201,7 @@ lf_status make_version(lf_serve* s, const lf_edit& e, Version** out) {
   if (n >= 2 && cudaMemcpyAsync(v->nodes, cur->nodes, sizeof(float4) * 4 * (n - 1), cudaMemcpyDeviceToDevice,
                                 s->edit_stream) != cudaSuccess)
     return LF_ERR_CUDA;
-  if (nw > 0 && cudaMemcpyAsync(v->wnodes, cur->wnodes, sizeof(float4) * 2 * WIDE * nw, cudaMemcpyDeviceToDevice,
+  if (nw > 0 && cudaMemcpyAsync(v->wnodes, cur->wnodes, sizeof(float4) * WNODE_Q * nw, cudaMemcpyDeviceToDevice,
                                 s->edit_stream) != cudaSuccess)
     return LF_ERR_CUDA;
   // the instance entry points at the version's arrays (its box is written by the fit)
@@ -556,7 +556,7 @@ lf_status lf_serve_create(lf_ctx* c, size_t budget, int max_slots, int n_streams
     v->base = true;
     v->inst = c->insts_dev + k;
     v->nodes = c->nodes + 4 * (size_t)c->node_off_h[k];
-    v->wnodes = c->wnodes + 2 * WIDE * (size_t)c->wnode_off_h[k];
+    v->wnodes = c->wnodes + WNODE_Q * (size_t)c->wnode_off_h[k];
     v->refs = 1;
     s->current.push_back(v.get());
     s->versions.push_back(std::move(v));

@@ -266,7 +266,10 @@ def test_wide_bvh_covers_every_leaf_once_and_nests():
                 if code >= 0:
                     clive = codes[code] != np.iinfo(np.int32).min
                     assert clive.sum() >= 2
-                    assert np.all(slots[code, clive, 0:3] >= lo) and np.all(slots[code, clive, 4:7] <= hi)
+                    # compressed boxes are rounded outward per node (FP16 offsets from the node
+                    # centre): a child may stick out of its parent's slot by one FP16 step
+                    tol = 2.0 ** -10 * (hi - lo) + 1e-6
+                    assert np.all(slots[code, clive, 0:3] >= lo - tol) and np.all(slots[code, clive, 4:7] <= hi + tol)
                     stack.append(code)
                 else:
                     first, cnt = ~code, int(counts[n, c])
