@@ -380,17 +380,37 @@ __global__ void __launch_bounds__(WB) k_wf_combine(ShadeBatch B, DevParams P, Sa
   J.rgb[3 * p + 2] = L.z;
 }
 
-// d_env += v at the four bilinear texels of direction w.
+// d_env += v at the four bilinear texels of direction w, warp-aggregated:
+// the lanes that reach the same texel together (matched on its index) sum
+// their contributions over shuffles and one of them adds the sum, so a
+// texel that many lanes sample (the sun of an importance-sampled map) takes
+// one atomic per warp instead of one per lane.
 __device__ __forceinline__ void env_scatter(const EnvDev& e, float* __restrict__ d_env, float3 w, float3 v) {
   if (!d_env) return;
   const Bilin b = env_bilinear(e, w);
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (b.w[k] == 0.0f) continue;
-    float* t = d_env + 3 * b.idx[k];
-    atomicAdd(t + 0, b.w[k] * v.x);
-    atomicAdd(t + 1, b.w[k] * v.y);
-    atomicAdd(t + 2, b.w[k] * v.z);
+    const int idx = b.w[k] != 0.0f ? b.idx[k] : -1;
+    const unsigned peers = __match_any_sync(__activemask(), idx);
+    if (idx < 0) continue;
+    float3 c = v * b.w[k];
+    if (peers != (1u << lane)) {
+      float3 acc = f3(0.f, 0.f, 0.f);
+      for (unsigned m = peers; m; m &= m - 1u) {  // the same order in every lane of the group
+        const int src = __ffs(m) - 1;
+        acc.x += __shfl_sync(peers, c.x, src);
+        acc.y += __shfl_sync(peers, c.y, src);
+        acc.z += __shfl_sync(peers, c.z, src);
+      }
+      c = acc;
+    }
+    if (lane == __ffs(peers) - 1) {
+      float* t = d_env + 3 * idx;
+      atomicAdd(t + 0, c.x);
+      atomicAdd(t + 1, c.y);
+      atomicAdd(t + 2, c.z);
+    }
   }
 }
 
