@@ -181,9 +181,11 @@ class Step:
 
 
 KERNELS_PER_STEP = {  # launches of this library's kernels in one step
-    "build": 2 + 1 + 1 + 5 * 3 + 1 + 1,  # bounds init+reduce, morton, radix 5x(hist, scan, scatter), hierarchy, fit
+    # bounds init + reduce, morton, radix 5 x (hist, scan, scatter), hierarchy, fit (pack + wide boxes),
+    # collapse, wide boxes
+    "build": 2 + 1 + 5 * 3 + 1 + 2 + 1 + 1,
     "env": 2,
-    "refit": 2,
+    "refit": 3,  # rigid transform, pack + fit, wide boxes
     "primary": 1,
     "shade": 7,  # gen, shadow A, continue, secondary sampling, shadow C, count, combine
     "backward": 2,  # combine adjoint, trace backward
@@ -374,22 +376,22 @@ def main():
     stage("counted run")
 
     # counted run (outside the timed region): traversal counters per kernel slot
-    cnt16 = torch.zeros(16, dtype=torch.int64, device="cuda")
-    step.tr.set_counters(cnt16)
-    step.tr.trace_primary(cam, 0, out=step.gbuf)
-    step.tr.shade(cam, step.gbuf, 0, args.spp, step.seed, out=step.rgb, samples=step.samples)
+    cnt20 = torch.zeros(20, dtype=torch.int64, device="cuda")
+    step.tr.set_counters(cnt20)
+    step.run()
     step.tr.sync()
     step.tr.set_counters(None)
-    c = [int(v) for v in cnt16.tolist()]
+    c = [int(v) for v in cnt20.tolist()]
     counters = {name: c[4 * k:4 * k + 4] for k, name in
-                enumerate(["primary", "nee_shadow", "continuation", "secondary_shadow"])}
+                enumerate(["primary", "nee_shadow", "continuation", "secondary_shadow", "trace_backward"])}
 
     stage("timed steps")
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
     step.rays.zero_()
     clocks = ClockSampler(local)
     per_step_ms, phase_ms = [], {n: [] for n in names}
-    kern_names = ["primary", "gen", "nee_shadow", "continuation", "secondary_shadow", "combine"]
+    kern_names = ["primary", "gen", "nee_shadow", "continuation", "secondary_shadow", "combine", "shade_adjoint",
+                  "trace_backward"]
     kern_ms = {n: [] for n in kern_names}
     step.tr.profile(True)  # CUDA events around the library's kernels, on its stream
     barrier()
@@ -430,14 +432,17 @@ def main():
     hbm, peak_kind = read_peaks()
     avg = {n: statistics.mean(v) for n, v in phase_ms.items()}
     kavg = {n: statistics.mean(v) for n, v in kern_ms.items()}
-    # algorithmic bytes per launch: node visits x node bytes (a wide node: a 16 B header and WIDE slots of 16 B),
-    # surfel tests x 48 B (the quick-test quads of the packed record), composited hits x 80 B (the
-    # record's fourth quad read by the precise test, two quads and the 16 B material read by the
-    # composite), plus each kernel's per-ray input and output
+    # algorithmic bytes per launch: node visits x node bytes (lf_bvh_wide_node_bytes), surfel tests x 48 B
+    # (the quick-test quads of the packed record), composited hits x 80 B (the record's fourth quad read
+    # by the precise test, two quads and the 16 B material read by the composite; in the adjoint 196 B:
+    # the 64 B record, 16 B material, 48 B of raw surfel parameters and 17 gradient atomics of 4 B),
+    # plus each kernel's per-ray input and output (adjoint: 25 G-buffer and 9 shading-gradient floats)
     wnode = step.tr.lib.lf_bvh_wide_node_bytes()
-    node_bytes = {n: wnode for n in ["primary", "nee_shadow", "continuation", "secondary_shadow"]}
-    per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32}
-    kbytes = {n: node_bytes[n] * counters[n][0] + 48 * counters[n][1] + 80 * counters[n][2] +
+    per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32,
+                  "trace_backward": 136}
+    per_hit = {n: (196 if n == "trace_backward" else 80) for n in per_ray_io}
+    node_bytes = {n: wnode for n in per_ray_io}
+    kbytes = {n: node_bytes[n] * counters[n][0] + 48 * counters[n][1] + per_hit[n] * counters[n][2] +
               per_ray_io[n] * counters[n][3] for n in per_ray_io}
     kernels = {n: {"ms": round(kavg[n], 3), "algorithmic_bytes": kbytes.get(n),
                    "achieved_gbs": (kbytes[n] / (kavg[n] * 1e-3) / 1e9) if n in kbytes else None}
@@ -513,7 +518,8 @@ def reduce_over_ranks(total_ms, fwd_ms, rays, device):
 
 
 KERNEL_NAMES = {"primary": "k_trace_primary", "nee_shadow": "k_wf_shadow (NEE)",
-                "continuation": "k_wf_continue", "secondary_shadow": "k_wf_shadow (secondary)"}
+                "continuation": "k_wf_continue", "secondary_shadow": "k_wf_shadow (secondary)",
+                "trace_backward": "k_trace_backward"}
 
 
 def read_traffic(kernel, field="dram_bytes_per_launch"):

@@ -293,11 +293,12 @@ lf_status lf_trace_backward(lf_ctx* ctx, const lf_camera* cam, const float* gbuf
                             size_t scratch_bytes);
 
 /*
- * Traversal counters for roofline accounting: when counters_dev (16 x uint64
+ * Traversal counters for roofline accounting: when counters_dev (20 x uint64
  * on the device) is non-NULL, the trace kernels ADD, per kernel slot k
  * (0 primary rays, 1 NEE shadow rays, 2 continuation rays, 3 secondary
- * shadow rays), [node visits, surfel tests, composited hits, rays] to
- * counters_dev[4k .. 4k+3].  NULL turns counting off.
+ * shadow rays, 4 adjoint re-traversal), [node visits, surfel tests,
+ * composited hits (slot 4: hits whose gradient is scattered), rays (slot 4:
+ * pixels with a hit)] to counters_dev[4k .. 4k+3].  NULL turns counting off.
  */
 lf_status lf_set_counters(lf_ctx* ctx, unsigned long long* counters_dev);
 
@@ -306,10 +307,12 @@ lf_status lf_set_counters(lf_ctx* ctx, unsigned long long* counters_dev);
  * lf_trace_primary and lf_shade_bounce record events around their kernels;
  * lf_profile_read waits for them and returns the milliseconds of the last
  * calls' kernels: [primary, sample generation, NEE shadow rays, continuation
- * rays, secondary shadow rays, combine].
+ * rays, secondary shadow rays, combine, shading adjoint (with the replayed
+ * wavefront when no forward sample buffer is given), adjoint re-traversal];
+ * the last two are 0 until a profiled lf_trace_backward has run.
  */
 lf_status lf_profile(lf_ctx* ctx, int enable);
-lf_status lf_profile_read(lf_ctx* ctx, float* ms6);
+lf_status lf_profile_read(lf_ctx* ctx, float* ms8);
 
 /*
  * Geometry-refinement losses of one view on a traced G-buffer (Eq. 8-9):

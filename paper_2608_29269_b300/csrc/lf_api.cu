@@ -265,9 +265,14 @@ lf_status lf_profile(lf_ctx* c, int enable) {
 lf_status lf_profile_read(lf_ctx* c, float* ms) {
   if (!c || !ms) return LF_ERR_INVALID;
   if (!c->prof_ev[0]) return fail(c, LF_ERR_NOT_BUILT, "profiling was never enabled");
-  // primary, gen, NEE shadow, continuation, secondary shadow, count + combine
-  const int a[6] = {0, 2, 3, 4, 5, 6}, b[6] = {1, 3, 4, 5, 6, 7};
-  for (int i = 0; i < 6; ++i) {
+  // primary, gen, NEE shadow, continuation, secondary shadow, count + combine;
+  // shading adjoint, trace backward (0 until a profiled lf_trace_backward)
+  const int a[8] = {0, 2, 3, 4, 5, 6, 8, 9}, b[8] = {1, 3, 4, 5, 6, 7, 9, 10};
+  for (int i = 0; i < 8; ++i) {
+    if (i >= 6 && !c->prof_bwd) {
+      ms[i] = 0.0f;
+      continue;
+    }
     LF_CUDA(c, cudaEventSynchronize(c->prof_ev[b[i]]));
     LF_CUDA(c, cudaEventElapsedTime(ms + i, c->prof_ev[a[i]], c->prof_ev[b[i]]));
   }
@@ -551,6 +556,7 @@ lf_status lf_trace_backward(lf_ctx* c, const lf_camera* cam, const float* gbuf, 
   const int n_pix = cam->width * cam->height;
   float* sg = nullptr;
   TraceArgs a = lf_ctx_trace_args(c, env_id);
+  if (c->profile) LF_CUDA(c, cudaEventRecord(c->prof_ev[8], c->stream));
   if (dL_drgb) {
     const size_t sg_bytes = sizeof(float) * (size_t)SHADE_GRAD_CH * n_pix + 256;
     const size_t need = fwd_samples ? sg_bytes : lf_backward_scratch_bytes(cam->width, cam->height, spp);
@@ -566,7 +572,12 @@ lf_status lf_trace_backward(lf_ctx* c, const lf_camera* cam, const float* gbuf, 
     }
     LF_CUDA(c, launch_shade_combine_adjoint(B, c->dp, S, dL_drgb, sg, d_env, c->stream));
   }
+  if (c->profile) LF_CUDA(c, cudaEventRecord(c->prof_ev[9], c->stream));
   LF_CUDA(c, launch_trace_backward(a, c->scene, to_cam(*cam), gbuf, sg, dL_dgbuf, d_surfel, d_env, c->stream));
+  if (c->profile) {
+    LF_CUDA(c, cudaEventRecord(c->prof_ev[10], c->stream));
+    c->prof_bwd = true;
+  }
   return LF_OK;
 }
 

@@ -79,6 +79,7 @@ __device__ __forceinline__ void surfel_adjoint(const SceneDev& sc, int id, float
 // them at once: with P_c = prod_{i <= c} (1 - alpha_i) over the lanes,
 // T_c = T_in / P_c, and the running sum S of the later hits' gw w is an
 // exclusive prefix sum; each lane scatters its own hit's adjoint.
+template <class Cnt>
 __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
                                                        const float* __restrict__ gbuf,
                                                        const float* __restrict__ sg,
@@ -144,7 +145,8 @@ __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev 
   FarKCoop kb;
   kb.P = Pm;
   const Ray ray = make_ray(o, d);
-  NoCounters cnt;
+  Cnt cnt;
+  unsigned adj = 0;  // hits whose gradient this ray scatters
   for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {
     kb.reset(bound, inclusive);
     coop_traverse(g, a.insts, a.n_inst, ray, kb, st, a.status, cnt);
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev 
       Tn = gshfl(g, Tj, take - 1);
     }
     remaining -= take;
+    adj += (unsigned)take;
     if (remaining > 0) {
       if (n < WIDE) {  // the forward composited more hits than the re-traversal finds
         if (g.c == 0) report(a.status, LF_ERR_ROUND_LIMIT);
@@ -204,13 +207,23 @@ __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev 
       inclusive = false;
     }
   }
+  if (Cnt::on && a.counters && g.c == 0) {  // slot 4 of the per-kernel counters: adjoint rays
+    atomicAdd(a.counters + 16, (unsigned long long)cnt.nodes);
+    atomicAdd(a.counters + 17, (unsigned long long)cnt.tests);
+    atomicAdd(a.counters + 18, (unsigned long long)adj);
+    atomicAdd(a.counters + 19, 1ull);
+  }
 }
 
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,
                                   const float* shade_grad, const float* dL_dgbuf, float* d_surfel, float* d_env,
                                   cudaStream_t st) {
   dim3 grid((cam.W + BTILE_W - 1) / BTILE_W, (cam.H + BTILE_H - 1) / BTILE_H);
-  k_trace_backward<<<grid, TB, BSTACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env);
+  if (a.counters)
+    k_trace_backward<Counters><<<grid, TB, BSTACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel, d_env);
+  else
+    k_trace_backward<NoCounters><<<grid, TB, BSTACK_SMEM, st>>>(a, s, cam, gbuf, shade_grad, dL_dgbuf, d_surfel,
+                                                                d_env);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,9 @@ struct lf_ctx {
   double* loss_dev = nullptr;  // loss sum of the regulariser calls
   unsigned long long* counters = nullptr;
   bool profile = false;
-  cudaEvent_t prof_ev[8] = {};  // primary | gen | NEE shadow | continuation | secondary shadow | combine
+  cudaEvent_t prof_ev[11] = {};  // primary | gen | NEE shadow | continuation | secondary shadow | combine;
+                                 // 8..10: shading adjoint | trace backward
+  bool prof_bwd = false;         // a profiled lf_trace_backward recorded events 8..10
   std::string err;
   // scene (caller-owned arrays) and its object layout
   lf::SceneDev scene{};

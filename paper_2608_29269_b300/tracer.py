@@ -247,10 +247,10 @@ class Tracer:
         return d_surfel, d_env
 
     def set_counters(self, counters: Optional[torch.Tensor]):
-        """counters: int64 CUDA tensor of 16 (4 kernel slots x [nodes, tests, composited, rays]) or None."""
+        """counters: int64 CUDA tensor of 20 (5 kernel slots x [nodes, tests, composited, rays]) or None."""
         if counters is not None and (not counters.is_cuda or counters.dtype != torch.int64
-                                     or not counters.is_contiguous() or counters.numel() < 16):
-            raise ValueError("counters must be a contiguous int64 CUDA tensor of at least 16 elements")
+                                     or not counters.is_contiguous() or counters.numel() < 20):
+            raise ValueError("counters must be a contiguous int64 CUDA tensor of at least 20 elements")
         self._counters = counters
         self.check(self.lib.lf_set_counters(self.ctx, _ptr(counters)))
 
@@ -258,8 +258,9 @@ class Tracer:
         self.check(self.lib.lf_profile(self.ctx, int(bool(enable))))
 
     def profile_read(self):
-        """ms of [primary, gen, NEE shadow, continuation, secondary shadow, combine] of the last calls."""
-        ms = (C.c_float * 6)()
+        """ms of [primary, gen, NEE shadow, continuation, secondary shadow, combine, shading adjoint,
+        adjoint re-traversal] of the last calls (the last two 0 before a profiled backward)."""
+        ms = (C.c_float * 8)()
         self.check(self.lib.lf_profile_read(self.ctx, ms))
         return list(ms)
 

@@ -342,7 +342,7 @@ def test_counters_and_kernel_timing_are_consistent():
     import torch
     sc, cam, env = _c1_inputs()
     tr, _ = gpu_tracer(sc, [env])
-    cnt = torch.zeros(16, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(20, dtype=torch.int64, device="cuda")
     rays = torch.zeros(1, dtype=torch.int64, device="cuda")
     with pytest.raises(ValueError):
         tr.set_counters(torch.zeros(4, dtype=torch.int64, device="cuda"))
@@ -352,19 +352,27 @@ def test_counters_and_kernel_timing_are_consistent():
     tr.sync()
     t0.record()
     g = tr.trace_primary(cam, 0)
-    tr.shade(cam, g, 0, spp=4, seed=5, ray_count=rays)
+    samples = tr.alloc_samples(cam, 4)
+    tr.shade(cam, g, 0, spp=4, seed=5, ray_count=rays, samples=samples)
+    assert tr.profile_read()[6:] == [0.0, 0.0]  # no backward profiled yet
+    d_s = torch.zeros((sc.n, 17), device="cuda")
+    tr.backward(cam, g, 0, 4, 5, dL_drgb=torch.ones((cam.height, cam.width, 3), device="cuda"), d_surfel=d_s,
+                fwd_samples=samples)
     tr.sync()
     t1.record()
     torch.cuda.synchronize()
     ms = tr.profile_read()
     tr.profile(False)
     tr.set_counters(None)
-    c = cnt.cpu().numpy().reshape(4, 4)
+    c = cnt.cpu().numpy().reshape(5, 4)
+    hits = int((g[18] > 0).sum().item())
     assert c[0, 3] == cam.width * cam.height
+    # the adjoint re-traverses every pixel with a hit and scatters each composited hit once
+    assert c[4, 3] == hits and c[4, 2] == c[0, 2] and c[4, 0] > 0 and c[4, 1] > 0
     assert c[1, 3] + c[2, 3] + c[3, 3] == int(rays.item())
     for k in range(4):
         if c[k, 3] > 0:
             assert c[k, 0] > 0 and c[k, 1] > 0
     assert c[0, 2] > 0 and c[2, 2] >= 0 and c[1, 2] == 0 and c[3, 2] == 0
-    assert len(ms) == 6 and all(v > 0 for v in ms)
+    assert len(ms) == 8 and all(v > 0 for v in ms)
     assert sum(ms) <= t0.elapsed_time(t1) * 1.05 + 0.05
