@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rates", default="0.5,1,2")
     ap.add_argument("--serve-scene", default="c4", choices=["c2", "c4"])
+    ap.add_argument("--multistate", action="store_true",
+                    help="multi-state relighting on the 1M-surfel scene only (3 environments x layouts)")
+    ap.add_argument("--ms-size", type=int, default=1024)
+    ap.add_argument("--ms-spp", type=int, default=64)
+    ap.add_argument("--ms-layouts", type=int, default=8)
     return ap.parse_args()
 
 
@@ -332,6 +337,101 @@ def run_serve_sweep(args):
     print(json.dumps(line))
 
 
+def run_multistate(args):
+    """Multi-state relighting (cross-state supervision, Sec. 3.2): the 1M-surfel
+    scene (shell + 12 objects) as one canonical scene, 3 environment states x
+    `--ms-layouts` layouts, each layout moving 1-4 random objects (rotation
+    about +y through the object's centre, x/z shift U[-0.5, 0.5]).  Per
+    (environment, layout): the state is assembled from the canonical scene
+    (Eq. 2, every BLAS refit), traced at ms-size^2, shaded at ms-spp,
+    differentiated, and its surfel gradient carried back to the canonical
+    parameters.  One warm-up state, then every state timed with CUDA events."""
+    import numpy as np
+    import torch
+    from synthetic import scenes as S
+    from paper_2608_29269_b300 import SceneTensors, Tracer
+    stage("multi-state workload")
+    sc = S.scene_c4(0)
+    cam = S.camera_c4(args.ms_size, args.ms_size)
+    envs = [S.env_sky_sun(i) for i in range(3)]
+    tr = Tracer()
+    can = SceneTensors.from_numpy(sc)
+    world = SceneTensors.from_numpy(sc)
+    for k in ["scale", "opacity", "albedo", "metallic", "roughness"]:  # shared with the canonical scene
+        setattr(world, k, getattr(can, k))
+    tr.build(world)
+    env_t = [torch.as_tensor(e.rgb, device="cuda").contiguous() for e in envs]
+    for i, e in enumerate(env_t):
+        tr.set_env(i, e)
+    rng = np.random.default_rng(7)
+    M = sc.n_objects - 1
+    layouts = []
+    for _ in range(args.ms_layouts):
+        R = np.stack([np.eye(3, dtype=np.float32)] * M)
+        t = np.zeros((M, 3), np.float32)
+        for o in rng.choice(np.arange(1, M + 1), size=int(rng.integers(1, 5)), replace=False):
+            lo, hi = sc.object_offsets[o], sc.object_offsets[o + 1]
+            R[o - 1], t[o - 1] = S.rigid_motion(rng, sc.mu[lo:hi].mean(0), max_shift=0.5)
+        layouts.append((R, t))
+    spp, P = args.ms_spp, cam.width * cam.height
+    gbuf = torch.empty((25, cam.height, cam.width), device="cuda")
+    rgb = torch.empty((cam.height, cam.width, 3), device="cuda")
+    samples = tr.alloc_samples(cam, spp)
+    scratch = torch.empty((9 * P * 4 + 256 + 3) // 4, device="cuda")
+    d_world = torch.zeros((sc.n, 17), device="cuda")
+    d_can = torch.zeros((sc.n, 17), device="cuda")
+    d_env = [torch.zeros_like(e) for e in env_t]
+    g = torch.Generator(device="cpu").manual_seed(3)
+    dL = ((torch.rand((cam.height, cam.width, 3), generator=g) > 0.5).float() * 2 - 1).div_(3 * P).to("cuda")
+    rays = torch.zeros(1, dtype=torch.int64, device="cuda")
+    names = ["assemble", "primary", "shade", "backward", "pullback"]
+    states = [(e, l) for e in range(len(envs)) for l in range(len(layouts))]
+
+    def run_state(e, l, ev):
+        R, t = layouts[l]
+        rec = (lambda n, i: ev[n][i].record()) if ev else (lambda n, i: None)
+        seed = 100 + 17 * e + l
+        rec("assemble", 0); tr.assemble_state(can, R, t); rec("assemble", 1)
+        rec("primary", 0); tr.trace_primary(cam, e, out=gbuf); rec("primary", 1)
+        rec("shade", 0)
+        tr.shade(cam, gbuf, e, spp, seed, out=rgb, ray_count=rays if ev else None, samples=samples)
+        rec("shade", 1)
+        rec("backward", 0)
+        d_world.zero_()
+        tr.backward(cam, gbuf, e, spp, seed, dL_drgb=dL, d_surfel=d_world, d_env=d_env[e], scratch=scratch,
+                    fwd_samples=samples)
+        rec("backward", 1)
+        rec("pullback", 0); tr.state_pullback(R, d_world, d_can); rec("pullback", 1)
+
+    stage("multi-state warm-up")
+    run_state(0, 0, None)
+    tr.sync()
+    stage("multi-state timed")
+    evs = []
+    for e, l in states:
+        ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in names}
+        run_state(e, l, ev)
+        evs.append(ev)
+    tr.sync()
+    per_state = [ev["assemble"][0].elapsed_time(ev["pullback"][1]) for ev in evs]
+    phase = {n: statistics.mean(ev[n][0].elapsed_time(ev[n][1]) for ev in evs) for n in names}
+    total_rays = int(rays.item()) + len(states) * P
+    total_ms = sum(per_state)
+    line = {"metric": "Mrays/s fwd+bwd, multi-state relighting (canonical scene, per-state assembly)",
+            "value": total_rays / (total_ms * 1e-3) / 1e6, "unit": "Mrays/s", "higher_is_better": True,
+            "states": len(states), "ms_per_state": total_ms / len(states),
+            "state_ms": {"median": statistics.median(per_state), "min": min(per_state), "max": max(per_state)},
+            "rays_per_state": total_rays / len(states), "phase_ms": {n: round(v, 3) for n, v in phase.items()},
+            "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": f"multi-state relighting: {sc.n} surfels (shell 6x40k + {M} objects), "
+                                   f"{cam.width}x{cam.height}, {spp} spp, 3 env states x {len(layouts)} layouts "
+                                   "(1-4 objects moved each), fwd+bwd + pullback to the canonical scene",
+                       "surfels": sc.n, "width": cam.width, "height": cam.height, "spp": spp,
+                       "states": len(states)},
+            "canonical_grad_abs_sum": float(d_can.abs().sum().item())}
+    print(json.dumps(line))
+
+
 def stage(msg):
     """Progress of the run on stderr (the JSON line alone goes to stdout)."""
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
@@ -341,6 +441,9 @@ def main():
     args = parse()
     if args.serve:
         run_serve_sweep(args)
+        return
+    if args.multistate:
+        run_multistate(args)
         return
     if args.impl == "reference":
         run_reference(args)
