@@ -362,18 +362,44 @@ __device__ __forceinline__ float3 sample_value(const SampleBuf& S, long long i, 
   return c;
 }
 
+// The combine and its adjoint run CG lanes per pixel: lane l of a pixel's
+// group takes samples l, l + CG, ..., so each load of a per-sample plane
+// reads CG consecutive floats (a full 32-byte sector) instead of one float
+// per pixel at a stride of spp; the group then sums over shuffles in a fixed
+// tree order.  Every lane of a warp reaches the shuffles (no early return).
+constexpr int CG = 8;
+
+template <class T>
+__device__ __forceinline__ T group_sum(T v);
+template <>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int off = CG / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, CG);
+  return v;
+}
+template <>
+__device__ __forceinline__ float3 group_sum(float3 v) {
+  return f3(group_sum(v.x), group_sum(v.y), group_sum(v.z));
+}
+
 __global__ void __launch_bounds__(WB) k_wf_combine(ShadeBatch B, DevParams P, SampleBuf S) {
-  const int gp = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= B.n_pix_total) return;
-  const ShadeJob& J = B.jobs[job_of_pixel(B, gp)];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gp = t / CG, l = t % CG;
+  const bool live = gp < B.n_pix_total;
+  const ShadeJob& J = B.jobs[live ? job_of_pixel(B, gp) : 0];
   const int p = gp - J.pix0;
-  const PixRec q = pix_record(J, p);
   float3 sum = f3(0.f, 0.f, 0.f);
-  if (q.hits > 0 && dot3(q.n, -q.d) > 0.0f) {
-    const long long i0 = J.item0 + (long long)p * J.spp;
-    SampleTerms Et;
-    for (int s = 0; s < J.spp; ++s) add3(sum, sample_value(S, i0 + s, q, J.env, P, Et));
+  PixRec q{};
+  if (live) {
+    q = pix_record(J, p);
+    if (q.hits > 0 && dot3(q.n, -q.d) > 0.0f) {
+      const long long i0 = J.item0 + (long long)p * J.spp;
+      SampleTerms Et;
+      for (int s = l; s < J.spp; s += CG) add3(sum, sample_value(S, i0 + s, q, J.env, P, Et));
+    }
   }
+  sum = group_sum(sum);
+  if (!live || l != 0) return;
   const float3 L = env_lookup(J.env, q.d) * q.T + sum * ((1.0f - q.T) / (float)J.spp);
   J.rgb[3 * p + 0] = L.x;
   J.rgb[3 * p + 1] = L.y;
@@ -420,20 +446,25 @@ __device__ __forceinline__ void env_scatter(const EnvDev& e, float* __restrict__
 __global__ void __launch_bounds__(WB) k_wf_combine_adjoint(ShadeBatch B, DevParams P, SampleBuf S,
                                                            const float* __restrict__ dL_drgb,
                                                            float* __restrict__ sg, float* __restrict__ d_env) {
-  const int gp = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= B.n_pix_total) return;
-  const ShadeJob& J = B.jobs[job_of_pixel(B, gp)];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gp = t / CG, l = t % CG;
+  const bool live = gp < B.n_pix_total;
+  const ShadeJob& J = B.jobs[live ? job_of_pixel(B, gp) : 0];
   const int p = gp - J.pix0;
   const size_t NP = (size_t)J.n_pix;
-  const PixRec q = pix_record(J, p);
-  const float3 g = f3(__ldg(dL_drgb + 3 * p), __ldg(dL_drgb + 3 * p + 1), __ldg(dL_drgb + 3 * p + 2));
+  PixRec q{};
+  float3 g = f3(0.f, 0.f, 0.f);
+  if (live) {
+    q = pix_record(J, p);
+    g = f3(__ldg(dL_drgb + 3 * p), __ldg(dL_drgb + 3 * p + 1), __ldg(dL_drgb + 3 * p + 2));
+  }
   const float3 wo = -q.d;
   float3 sum = f3(0.f, 0.f, 0.f), gn = sum, ga = sum;
   float gm = 0.f, gr = 0.f;
-  if (q.hits > 0 && dot3(q.n, wo) > 0.0f) {
+  if (live && q.hits > 0 && dot3(q.n, wo) > 0.0f) {
     const float3 gc = g * ((1.0f - q.T) / (float)J.spp);
     const long long i0 = J.item0 + (long long)p * J.spp;
-    for (int s = 0; s < J.spp; ++s) {
+    for (int s = l; s < J.spp; s += CG) {
       const long long i = i0 + s;
       const float ek = S.ek[i];
       if (ek > 0.0f) {
@@ -473,6 +504,12 @@ __global__ void __launch_bounds__(WB) k_wf_combine_adjoint(ShadeBatch B, DevPara
       }
     }
   }
+  sum = group_sum(sum);
+  gn = group_sum(gn);
+  ga = group_sum(ga);
+  gm = group_sum(gm);
+  gr = group_sum(gr);
+  if (!live || l != 0) return;
   const float3 Ed = env_lookup(J.env, q.d);
   const float inv = 1.0f / (float)J.spp;
   const float gT = g.x * (Ed.x - sum.x * inv) + g.y * (Ed.y - sum.y * inv) + g.z * (Ed.z - sum.z * inv);
@@ -569,14 +606,16 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
 }
 
 cudaError_t launch_shade_combine(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, cudaStream_t st) {
-  if (B.n_pix_total > 0) k_wf_combine<<<(B.n_pix_total + WB - 1) / WB, WB, 0, st>>>(B, P, S);
+  const long long threads = (long long)B.n_pix_total * CG;
+  if (B.n_pix_total > 0) k_wf_combine<<<(unsigned)((threads + WB - 1) / WB), WB, 0, st>>>(B, P, S);
   return cudaGetLastError();
 }
 
 cudaError_t launch_shade_combine_adjoint(const ShadeBatch& B, const DevParams& P, const SampleBuf& S,
                                          const float* dL_drgb, float* sg, float* d_env, cudaStream_t st) {
   if (B.n_pix_total > 0)
-    k_wf_combine_adjoint<<<(B.n_pix_total + WB - 1) / WB, WB, 0, st>>>(B, P, S, dL_drgb, sg, d_env);
+    k_wf_combine_adjoint<<<(unsigned)(((long long)B.n_pix_total * CG + WB - 1) / WB), WB, 0, st>>>(B, P, S, dL_drgb,
+                                                                                                     sg, d_env);
   return cudaGetLastError();
 }
 
