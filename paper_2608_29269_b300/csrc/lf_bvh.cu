@@ -547,43 +547,90 @@ __global__ void k_material(SceneDev s, int beg, int end, float3 rgb, int set_rgb
 // ---------------------------------------------------------------- environment tables
 // Texel weight (Rec.709 luminance + 1e-6) * sin(theta at the row centre) in
 // FP64 with explicit rounding (no contraction); sequential sums per row.
-__global__ void k_env_rows(const float* __restrict__ rgb, const double* __restrict__ sin_row, int H, int W,
-                           double* __restrict__ rowsum, float* __restrict__ pmf_col, float* __restrict__ cdf_col) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= H) return;
+// One block per row.  The texel weights w_c = (lum + 1e-6) sin(theta) are
+// formed in parallel into shared memory, chunk by chunk (coalesced loads);
+// one thread sums them in column order (the same FP64 operations, in the
+// same order, as a single thread walking the row), and the pmf / cdf
+// divisions run in parallel again.
+constexpr int ENV_T = 256;    // threads per row block
+constexpr int ENV_CH = 1024;  // texels per shared-memory chunk
+
+__device__ __forceinline__ double texel_weight(const float* t, double st) {
+  double lum = __dadd_rn(__dmul_rn(0.2126, (double)t[0]), __dmul_rn(0.7152, (double)t[1]));
+  lum = __dadd_rn(lum, __dmul_rn(0.0722, (double)t[2]));
+  lum = __dadd_rn(lum, 1e-6);
+  return __dmul_rn(lum, st);
+}
+
+__global__ void __launch_bounds__(ENV_T) k_env_rows(const float* __restrict__ rgb, const double* __restrict__ sin_row,
+                                                    int H, int W, double* __restrict__ rowsum,
+                                                    float* __restrict__ pmf_col, float* __restrict__ cdf_col) {
+  __shared__ double s_w[ENV_CH], s_p[ENV_CH];
+  __shared__ double s_acc;
+  const int r = blockIdx.x;
+  if (r >= H) return;  // uniform over the block
   const double st = sin_row[r];
-  double acc = 0.0;
-  for (int c = 0; c < W; ++c) {
-    const float* t = rgb + 3 * ((size_t)r * W + c);
-    double lum = __dadd_rn(__dmul_rn(0.2126, (double)t[0]), __dmul_rn(0.7152, (double)t[1]));
-    lum = __dadd_rn(lum, __dmul_rn(0.0722, (double)t[2]));
-    lum = __dadd_rn(lum, 1e-6);
-    acc = __dadd_rn(acc, __dmul_rn(lum, st));
+  const float* row = rgb + 3 * (size_t)r * W;
+  if (threadIdx.x == 0) s_acc = 0.0;
+  // pass 1: the row sum, in column order
+  for (int c0 = 0; c0 < W; c0 += ENV_CH) {
+    const int n = min(ENV_CH, W - c0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += ENV_T) s_w[c] = texel_weight(row + 3 * (size_t)(c0 + c), st);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double acc = s_acc;
+      for (int c = 0; c < n; ++c) acc = __dadd_rn(acc, s_w[c]);
+      s_acc = acc;
+    }
   }
-  rowsum[r] = acc;
-  double pc = 0.0;
-  for (int c = 0; c < W; ++c) {
-    const float* t = rgb + 3 * ((size_t)r * W + c);
-    double lum = __dadd_rn(__dmul_rn(0.2126, (double)t[0]), __dmul_rn(0.7152, (double)t[1]));
-    lum = __dadd_rn(lum, __dmul_rn(0.0722, (double)t[2]));
-    lum = __dadd_rn(lum, 1e-6);
-    const double w = __dmul_rn(lum, st);
-    pc = __dadd_rn(pc, w);
-    pmf_col[(size_t)r * W + c] = (float)__ddiv_rn(w, acc);
-    cdf_col[(size_t)r * W + c] = (float)__ddiv_rn(pc, acc);
+  __syncthreads();
+  const double acc = s_acc;
+  if (threadIdx.x == 0) rowsum[r] = acc;
+  // pass 2: the column cdf (prefix sums in column order) and pmf
+  double pc = 0.0;  // running prefix, held by thread 0
+  for (int c0 = 0; c0 < W; c0 += ENV_CH) {
+    const int n = min(ENV_CH, W - c0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += ENV_T) s_w[c] = texel_weight(row + 3 * (size_t)(c0 + c), st);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int c = 0; c < n; ++c) {
+        pc = __dadd_rn(pc, s_w[c]);
+        s_p[c] = pc;
+      }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += ENV_T) {
+      pmf_col[(size_t)r * W + c0 + c] = (float)__ddiv_rn(s_w[c], acc);
+      cdf_col[(size_t)r * W + c0 + c] = (float)__ddiv_rn(s_p[c], acc);
+    }
   }
 }
 
-__global__ void k_env_marginal(const double* __restrict__ rowsum, int H, float* __restrict__ pmf_row,
-                               float* __restrict__ cdf_row) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double total = 0.0;
-  for (int r = 0; r < H; ++r) total = __dadd_rn(total, rowsum[r]);
-  double pre = 0.0;
-  for (int r = 0; r < H; ++r) {
-    pre = __dadd_rn(pre, rowsum[r]);
-    pmf_row[r] = (float)__ddiv_rn(rowsum[r], total);
-    cdf_row[r] = (float)__ddiv_rn(pre, total);
+__global__ void __launch_bounds__(ENV_T) k_env_marginal(const double* __restrict__ rowsum, int H,
+                                                        float* __restrict__ pmf_row, float* __restrict__ cdf_row) {
+  __shared__ double s_pre[ENV_CH];
+  __shared__ double s_total;
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int r = 0; r < H; ++r) total = __dadd_rn(total, rowsum[r]);
+    s_total = total;
+  }
+  double pre = 0.0;  // running prefix, held by thread 0
+  for (int r0 = 0; r0 < H; r0 += ENV_CH) {
+    const int n = min(ENV_CH, H - r0);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int r = 0; r < n; ++r) {
+        pre = __dadd_rn(pre, rowsum[r0 + r]);
+        s_pre[r] = pre;
+      }
+    __syncthreads();
+    const double total = s_total;
+    for (int r = threadIdx.x; r < n; r += ENV_T) {
+      pmf_row[r0 + r] = (float)__ddiv_rn(rowsum[r0 + r], total);
+      cdf_row[r0 + r] = (float)__ddiv_rn(s_pre[r], total);
+    }
   }
 }
 
@@ -676,8 +723,8 @@ cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int
 
 cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, int W, double* rowsum, float* pmf_row,
                               float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st) {
-  k_env_rows<<<(H + 63) / 64, 64, 0, st>>>(rgb, sin_row, H, W, rowsum, pmf_col, cdf_col);
-  k_env_marginal<<<1, 1, 0, st>>>(rowsum, H, pmf_row, cdf_row);
+  k_env_rows<<<H, ENV_T, 0, st>>>(rgb, sin_row, H, W, rowsum, pmf_col, cdf_col);
+  k_env_marginal<<<1, ENV_T, 0, st>>>(rowsum, H, pmf_row, cdf_row);
   return cudaGetLastError();
 }
 
