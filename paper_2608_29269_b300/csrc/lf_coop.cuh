@@ -82,6 +82,10 @@ __device__ __forceinline__ int wentry(int ii, int code) {
 //   tlo(), thi()  culling interval of the ray
 //   leaf(g, ray, ii, first, count, I)  lanes c < count handle surfel first + c
 //   done(), abort()
+//   any_order  true when the result does not depend on the visiting order
+//              (shadow rays): the walk then descends into the first hit
+//              child slot instead of the nearest one, saving the min-reduce
+//              of every node visit
 template <class V, class Cnt>
 __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, int n_inst, const Ray& ray, V& vis,
                                               const CStack& st, int* status, Cnt& cnt) {
@@ -160,9 +164,14 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
       const unsigned m = gballot(g, hit);
       if (m == 0u) break;
       // nearest child: smallest entry distance (positive floats order as their bits)
-      const unsigned key = hit ? __float_as_uint(tn) : 0xffffffffu;
-      const unsigned kmin = __reduce_min_sync(g.mask, key);
-      const int near = __ffs(gballot(g, hit && key == kmin)) - 1;
+      int near;
+      if (V::any_order) {
+        near = __ffs(m) - 1;
+      } else {
+        const unsigned key = hit ? __float_as_uint(tn) : 0xffffffffu;
+        const unsigned kmin = __reduce_min_sync(g.mask, key);
+        near = __ffs(gballot(g, hit && key == kmin)) - 1;
+      }
       const unsigned others = m & ~(1u << near);
       if (sp + __popc(others) > CSTACK) {
         if (g.c == 0) report(status, LF_ERR_STACK);
@@ -188,6 +197,7 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
 // once below T_min.  The product of a leaf's factors is formed over the
 // group by a butterfly, which leaves every lane with the same bits.
 struct ShadowCoop {
+  static constexpr bool any_order = true;
   float V;
   bool stop;
   DevParams P;
@@ -226,6 +236,7 @@ struct ShadowCoop {
 // in front of s, which moves the stop forward, so nothing beyond entry s is
 // ever composited and the far bound of the traversal drops to its depth.
 struct NearKCoop {
+  static constexpr bool any_order = false;
   unsigned long long bk;    // this lane's entry (~0: empty)
   int bc;                   // its hit code: instance << 24 | leaf
   float ba;                 // its alpha~
@@ -319,6 +330,7 @@ struct NearKCoop {
 // keys below a bound (inclusive on the first round), sorted descending over
 // the lanes (lane c holds entry c; 0 = empty).
 struct FarKCoop {
+  static constexpr bool any_order = false;
   unsigned long long bk;
   int bc;
   int cnt;
