@@ -7,6 +7,7 @@ All compute runs in the hand-written sm_103a kernels of liblightfuse.so
 from . import _native  # noqa: F401
 from .tracer import SceneTensors, Tracer, camera_struct, default_params, split_surfel_grad  # noqa: F401
 from .render import StateRender, SurfelRender, render, render_state  # noqa: F401
+from .checkpoint import Checkpoint, load_checkpoint, restore, save_checkpoint  # noqa: F401
 
 
 def load_library():

@@ -72,3 +72,38 @@ def test_inverse_rendering_schedule():
     assert groups(0) == ("env",) and groups(1999) == ("env",)
     assert groups(2000) == ("env", "albedo") and groups(8999) == ("env", "albedo")
     assert groups(9000) == ("env", "albedo", "metallic", "roughness")
+
+
+def test_checkpoint_round_trip_on_the_host(tmp_path):
+    """Scene, environments, constants, per-state transforms and the replay
+    seed survive a save / load unchanged (CPU tensors, no library call)."""
+    import torch
+    from paper_2608_29269_b300 import SceneTensors, load_checkpoint, save_checkpoint
+    from paper_2608_29269_b300._native import LfParams
+    from synthetic import scenes as S
+    sc = S.scene_c2(0, per_face=200, per_object=300)
+    st = SceneTensors.from_numpy(sc, device="cpu")
+    envs = {0: torch.as_tensor(S.env_sky_sun(0, H=16, W=32).rgb), 3: torch.full((8, 16, 3), 0.5)}
+    p = LfParams()
+    p.T_min, p.alpha_min, p.max_rounds, p.sampler = 1e-4, 1.0 / 255.0, 64, 1
+    rng = np.random.default_rng(0)
+    R = np.stack([S.rigid_motion(rng, np.zeros(3))[0] for _ in range(sc.n_objects - 1)])
+    t = rng.normal(size=(sc.n_objects - 1, 3)).astype(np.float32)
+    path = tmp_path / "scene.npz"
+    save_checkpoint(path, st, envs=envs, params=p, states={"layout 3": (R, t)}, seed=1234, spp=16)
+    ck = load_checkpoint(path, device="cpu")
+    for k in ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic", "roughness"]:
+        assert torch.equal(getattr(ck.scene, k), getattr(st, k)), k
+    assert list(ck.scene.object_offsets) == [int(v) for v in sc.object_offsets]
+    assert sorted(ck.envs) == [0, 3] and all(torch.equal(ck.envs[s], envs[s]) for s in envs)
+    assert ck.params["max_rounds"] == 64 and ck.params["sampler"] == 1
+    assert ck.params["T_min"] == np.float32(1e-4) and ck.lf_params().alpha_min == np.float32(1.0 / 255.0)
+    np.testing.assert_array_equal(ck.states["layout 3"][0], R)
+    np.testing.assert_array_equal(ck.states["layout 3"][1], t)
+    assert ck.seed == 1234 and ck.spp == 16
+    # a file whose offsets do not partition the surfels is refused
+    bad = SceneTensors(**{k: getattr(st, k) for k in ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic",
+                                                     "roughness"]}, object_offsets=[0, 5, 3, sc.n])
+    save_checkpoint(tmp_path / "bad.npz", bad)
+    with pytest.raises(ValueError):
+        load_checkpoint(tmp_path / "bad.npz", device="cpu")
