@@ -50,7 +50,8 @@ typedef enum {
   LF_ERR_ROUND_LIMIT = 5, /* a ray needed more than max_rounds k-buffer rounds */
   LF_ERR_TIMEOUT = 6,     /* a wait ran out of time                          */
   LF_ERR_BUSY = 7,        /* no free slot (serving)                          */
-  LF_ERR_NOT_BUILT = 8    /* render before lf_bvh_build / lf_env_set         */
+  LF_ERR_NOT_BUILT = 8,   /* render before lf_bvh_build / lf_env_set         */
+  LF_ERR_BOUNDS = 9       /* a device bounds check failed (LF_CHECKED builds) */
 } lf_status;
 
 /*

@@ -8,9 +8,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblightfuse.so")
 
 LF_OK, LF_ERR_INVALID, LF_ERR_OOM, LF_ERR_CUDA, LF_ERR_STACK, LF_ERR_ROUND_LIMIT, LF_ERR_TIMEOUT, LF_ERR_BUSY, \
-    LF_ERR_NOT_BUILT = range(9)
+    LF_ERR_NOT_BUILT, LF_ERR_BOUNDS = range(10)
 STATUS_NAMES = ["LF_OK", "LF_ERR_INVALID", "LF_ERR_OOM", "LF_ERR_CUDA", "LF_ERR_STACK", "LF_ERR_ROUND_LIMIT",
-                "LF_ERR_TIMEOUT", "LF_ERR_BUSY", "LF_ERR_NOT_BUILT"]
+                "LF_ERR_TIMEOUT", "LF_ERR_BUSY", "LF_ERR_NOT_BUILT", "LF_ERR_BOUNDS"]
 
 LF_MAX_OBJECTS = 64
 LF_MAX_ENVS = 16
@@ -106,11 +106,15 @@ SIGNATURES = [
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load liblightfuse.so; fails loudly when the CUDA extension is missing."""
+def load(path: str = None):
+    """Load liblightfuse.so; fails loudly when the CUDA extension is missing.
+    LIGHTFUSE_LIB, when set, names another build of the same sources to load
+    (the bounds-checked one, for instance)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("LIGHTFUSE_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA extension not built: {path} is missing (run paper_2608_29269_b300/build.py)")
     lib = C.CDLL(path)

@@ -249,6 +249,7 @@ lf_status lf_sync(lf_ctx* c) {
     LF_CUDA(c, cudaMemset(c->status_dev, 0, sizeof(int)));
     return fail(c, (lf_status)st, st == LF_ERR_STACK ? "traversal stack overflow"
                                    : st == LF_ERR_ROUND_LIMIT ? "k-buffer round limit reached"
+                                   : st == LF_ERR_BOUNDS      ? "device bounds check failed (see the printed index)"
                                                               : "device error");
   }
   return LF_OK;
@@ -361,7 +362,7 @@ lf_status lf_bvh_build(lf_ctx* c, const lf_scene* s) {
     I.geo = c->geo + (size_t)GEO * c->offsets[k];
     I.mat = c->mat + (size_t)c->offsets[k];
     I.id_base = c->offsets[k];
-    I.pad = 0;
+    I.n_wide = c->wnode_off_h[k + 1] - c->wnode_off_h[k];
     I.wnodes = c->wnodes + WNODE_Q * (size_t)c->wnode_off_h[k];
     I.wroot = nk > WLEAF ? 0 : (nk >= 1 ? ~0 : INT_MIN);
     I.wroot_count = nk > WLEAF ? 0 : nk;

@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev 
     coop_traverse(g, a.insts, a.n_inst, ray, kb, st, a.status, cnt);
     const int n = kb.cnt;
     const int take = min(n, remaining);
-    const bool have = g.c < take;
+    bool have = g.c < take;
+    if (have) have = LF_IN_BOUNDS(kb.bc >> 24, a.n_inst, a.status, "hit instance") &&
+                     LF_IN_BOUNDS(kb.bc & 0xffffff, a.insts[kb.bc >> 24].n_leaves, a.status, "hit surfel");
     float alpha = 0.0f, t = 0.0f, gw = 0.0f;
     Rec rc;
     float4 mt = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -69,7 +69,7 @@ struct __align__(16) Inst {
   const float4* geo;
   const float4* mat;
   int id_base;  // surfel id of the object's first surfel
-  int pad;
+  int n_wide;   // wide BLAS nodes of the object
   const float4* wnodes;  // wide BLAS (WIDE children per node)
   int wroot;             // wide root: >= 0 node, < 0 leaf ~first; INT_MIN: empty
   int wroot_count;       // surfels of a leaf root
@@ -99,6 +99,31 @@ struct CamDev {
 __device__ __forceinline__ void report(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
+
+// Bounds checks of the LF_CHECKED build (off by default; then every check is
+// the constant true and the kernels are the unchecked ones).  A failed check
+// reports LF_ERR_BOUNDS through the status word, prints the index and its
+// limit, and the caller skips the access -- no trap, so the context stays
+// usable and lf_sync returns the error.
+#ifndef LF_CHECKED
+#define LF_CHECKED 0
+#endif
+#if LF_CHECKED
+}  // namespace lf
+#include <cstdio>
+namespace lf {
+static __device__ __noinline__ bool lf_bounds_fail(long long idx, long long lim, int* status, const char* what) {
+  report(status, LF_ERR_BOUNDS);
+  printf("lightfuse bounds check failed: %s index %lld outside [0, %lld)\n", what, idx, lim);
+  return false;
+}
+#define LF_IN_BOUNDS(idx, lim, status, what)                                                     \
+  ((long long)(idx) >= 0 && (long long)(idx) < (long long)(lim)                                \
+       ? true                                                                                    \
+       : ::lf::lf_bounds_fail((long long)(idx), (long long)(lim), (status), (what)))
+#else
+#define LF_IN_BOUNDS(idx, lim, status, what) true
+#endif
 
 // ------------------------------------------------------------------ vectors
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }

@@ -133,6 +133,11 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
       const int ii = e >> 25;
       const Inst& I = insts[ii];
       if (e & LEAF_BIT) {
+        if (!LF_IN_BOUNDS((e & 0xffffff) + ec - 1, I.n_leaves, status, "leaf surfel") ||
+            !LF_IN_BOUNDS(e & 0xffffff, I.n_leaves, status, "leaf first surfel")) {
+          vis.abort();
+          return;
+        }
         if (g.c == 0) cnt.test(ec);
         vis.leaf(g, ray, ii, e & 0xffffff, ec, I);
         if (vis.done()) return;
@@ -144,6 +149,10 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
         return;
       }
       if (g.c == 0) cnt.node();
+      if (!LF_IN_BOUNDS(e & 0xffffff, I.n_wide, status, "wide node")) {
+        vis.abort();
+        return;
+      }
       const float4* node = I.wnodes + WNODE_Q * (size_t)(e & 0xffffff);
 #if LF_WIDE_FP16
       const float4 H = __ldg(node);
@@ -432,7 +441,9 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     coop_traverse(g, insts, n_inst, ray, kb, st, status, cnt);
     const int n = kb.cnt;
     if (n == 0) break;
-    const bool have = g.c < n;
+    bool have = g.c < n;
+    if (have) have = LF_IN_BOUNDS(kb.bc >> 24, n_inst, status, "hit instance") &&
+                     LF_IN_BOUNDS(kb.bc & 0xffffff, insts[kb.bc >> 24].n_leaves, status, "hit surfel");
     // depth and alpha~ of each entry as the hit test computed them
     const float alpha = have ? kb.ba : 0.0f, t = have ? key_t(kb.bk) : 0.0f;
     float mtl = 0.0f, rgh = 0.0f;

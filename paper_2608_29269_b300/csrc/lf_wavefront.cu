@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
   for (int k = group_fetch(g, cursor); k < n; k = group_fetch(g, cursor)) {
     const int e = q[k];
     const long long item = which == 0 ? (long long)e : (long long)(e >> 1);
+    if (!LF_IN_BOUNDS(item, B.n_items, status, "shadow ray item")) continue;
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     ShadowCoop v;
     v.P = P;
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
   unsigned comp = 0;
   for (int k = group_fetch(g, S.counts + CURSOR_B); k < n; k = group_fetch(g, S.counts + CURSOR_B)) {
     const long long item = S.qB[k];
+    if (!LF_IN_BOUNDS(item, B.n_items, status, "continuation ray item")) continue;
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     const long long loc = item - J.item0;
     const float3 xs = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
