@@ -18,8 +18,9 @@
  *     tables) when the scene or map grows.
  *   - Errors are returned as lf_status; the library never aborts, traps or
  *     exits.  Kernels report device-side conditions (traversal stack
- *     overflow, round limit) through a device status word that lf_sync
- *     returns.  lf_last_error gives a human-readable message.
+ *     overflow, round limit; in a build compiled with LF_CHECKED=1 also a
+ *     failed bounds check, LF_ERR_BOUNDS) through a device status word that
+ *     lf_sync returns.  lf_last_error gives a human-readable message.
  *   - Floating point data are FP32.  Gradients are ACCUMULATED (+=) into the
  *     caller's buffers; the caller zeroes them.
  *   - Limits: at most LF_MAX_OBJECTS objects (background included), at most
