@@ -52,7 +52,8 @@ typedef enum {
   LF_ERR_TIMEOUT = 6,     /* a wait ran out of time                          */
   LF_ERR_BUSY = 7,        /* no free slot (serving)                          */
   LF_ERR_NOT_BUILT = 8,   /* render before lf_bvh_build / lf_env_set         */
-  LF_ERR_BOUNDS = 9       /* a device bounds check failed (LF_CHECKED builds) */
+  LF_ERR_BOUNDS = 9,      /* a device bounds check failed (LF_CHECKED builds) */
+  LF_ERR_CANCELLED = 10   /* a served request was cancelled before admission */
 } lf_status;
 
 /*
@@ -456,6 +457,12 @@ lf_status lf_serve_poll(lf_serve* srv, uint64_t ticket, int* done, float* frame_
                         lf_timing* timing);
 /* Block until the ticket is done or timeout_ms passes (LF_ERR_TIMEOUT). */
 lf_status lf_serve_wait(lf_serve* srv, uint64_t ticket, int timeout_ms);
+/* Withdraw a request that has not been admitted yet: LF_OK, and the ticket
+ * is done with status LF_ERR_CANCELLED (lf_serve_poll returns it and frees
+ * the ticket; no frame).  A request already admitted runs to the end and
+ * LF_ERR_BUSY is returned (poll it as usual); an unknown ticket gives
+ * LF_ERR_INVALID.  Nothing on the GPU is interrupted. */
+lf_status lf_serve_cancel(lf_serve* srv, uint64_t ticket);
 lf_status lf_serve_destroy(lf_serve* srv);
 
 #ifdef __cplusplus

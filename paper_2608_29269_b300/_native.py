@@ -8,9 +8,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblightfuse.so")
 
 LF_OK, LF_ERR_INVALID, LF_ERR_OOM, LF_ERR_CUDA, LF_ERR_STACK, LF_ERR_ROUND_LIMIT, LF_ERR_TIMEOUT, LF_ERR_BUSY, \
-    LF_ERR_NOT_BUILT, LF_ERR_BOUNDS = range(10)
+    LF_ERR_NOT_BUILT, LF_ERR_BOUNDS, LF_ERR_CANCELLED = range(11)
 STATUS_NAMES = ["LF_OK", "LF_ERR_INVALID", "LF_ERR_OOM", "LF_ERR_CUDA", "LF_ERR_STACK", "LF_ERR_ROUND_LIMIT",
-                "LF_ERR_TIMEOUT", "LF_ERR_BUSY", "LF_ERR_NOT_BUILT", "LF_ERR_BOUNDS"]
+                "LF_ERR_TIMEOUT", "LF_ERR_BUSY", "LF_ERR_NOT_BUILT", "LF_ERR_BOUNDS", "LF_ERR_CANCELLED"]
 
 LF_MAX_OBJECTS = 64
 LF_MAX_ENVS = 16
@@ -100,6 +100,7 @@ SIGNATURES = [
     ("lf_serve_submit", C.c_int, [_P, C.POINTER(LfRequest), C.POINTER(C.c_uint64)]),
     ("lf_serve_poll", C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int), _P, C.c_size_t, C.POINTER(LfTiming)]),
     ("lf_serve_wait", C.c_int, [_P, C.c_uint64, C.c_int]),
+    ("lf_serve_cancel", C.c_int, [_P, C.c_uint64]),
     ("lf_serve_destroy", C.c_int, [_P]),
 ]
 

@@ -625,6 +625,24 @@ lf_status lf_serve_poll(lf_serve* s, uint64_t ticket, int* done, float* frame, s
   return st;
 }
 
+lf_status lf_serve_cancel(lf_serve* s, uint64_t ticket) {
+  if (!s) return LF_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return LF_ERR_INVALID;
+  Job* j = it->second.get();
+  // a pending job is in the queue until the scheduler admits it, under this lock
+  auto q = std::find(s->pending.begin(), s->pending.end(), j);
+  if (j->state != 0 || q == s->pending.end()) return LF_ERR_BUSY;
+  s->pending.erase(q);
+  j->state = 2;
+  j->status = LF_ERR_CANCELLED;
+  j->t_admit = j->t_start = j->t_done = now_s();
+  s->cv_done.notify_all();
+  s->cv_work.notify_one();
+  return LF_OK;
+}
+
 lf_status lf_serve_wait(lf_serve* s, uint64_t ticket, int timeout_ms) {
   if (!s) return LF_ERR_INVALID;
   std::unique_lock<std::mutex> lock(s->mu);

@@ -66,6 +66,11 @@ class Server:
             raise N.LightFuseError(st, "lf_serve_submit")
         return t.value
 
+    def cancel(self, ticket: int) -> int:
+        """LF_OK when the request had not been admitted (its poll then returns
+        LF_ERR_CANCELLED), LF_ERR_BUSY when it is already running or done."""
+        return self.lib.lf_serve_cancel(self.h, C.c_uint64(ticket))
+
     def wait(self, ticket: int, timeout_ms: int = 600_000) -> int:
         return self.lib.lf_serve_wait(self.h, C.c_uint64(ticket), int(timeout_ms))
 

@@ -97,3 +97,29 @@ def test_more_finished_requests_than_frames_keep_admission_going():
         assert stt == N.LF_OK and frame is not None and np.isfinite(frame).all()
     assert time.perf_counter() - t0 < 30.0
     srv.close()
+
+
+def test_pending_requests_can_be_cancelled():
+    """A request withdrawn before admission finishes as LF_ERR_CANCELLED with
+    no frame; one already admitted runs to the end; the server goes on."""
+    from paper_2608_29269_b300 import _native as N
+    from paper_2608_29269_b300.serve import Server
+    sc, tr, st = _setup()
+    cam = S.Camera((0.0, -0.5, 1.8), (0.0, -1.5, 0.0), (0.0, 1.0, 0.0), 60.0, 96, 96)
+    srv = Server(tr, budget_bytes=2 << 30, max_slots=1, n_streams=1)
+    tickets = [srv.submit(None, cam, 8, s) for s in range(6)]
+    codes = [srv.cancel(t) for t in tickets[::-1]]  # the tail of a one-slot queue is still pending
+    assert codes[0] == N.LF_OK
+    assert srv.cancel(tickets[-1]) == N.LF_ERR_BUSY  # already done (cancelled)
+    assert srv.cancel(10 ** 9) == N.LF_ERR_INVALID
+    for t, c in zip(tickets[::-1], codes):
+        assert c in (N.LF_OK, N.LF_ERR_BUSY)
+        assert srv.wait(t, 60_000) == N.LF_OK
+        status, frame, tm = srv.result(t, cam)
+        if c == N.LF_OK:
+            assert status == N.LF_ERR_CANCELLED and frame is None and tm["rays"] == 0
+        else:
+            assert status == N.LF_OK and np.isfinite(frame).all()
+    t = srv.submit(None, cam, 4, 9)
+    assert srv.wait(t, 60_000) == N.LF_OK and srv.result(t, cam)[0] == N.LF_OK
+    srv.close()
