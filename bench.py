@@ -14,6 +14,9 @@ nodes) fits in L2, so L2 is flushed between timed steps.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the reference arm of this comparison).
+`--serve` runs the served-vs-plain latency sweep on the 1M-surfel scene and
+`--multistate` the multi-state relighting workload (3 environments x 8
+layouts assembled from one canonical scene); each prints its own JSON line.
 Multi-GPU: every rank renders its own replica (no collective on the data
 path), timing is the max over ranks, `value` counts the rays of all ranks.
 """
