@@ -4,7 +4,6 @@ Tolerances: 1e-4 absolute per channel (radiance clamped to [0,1]) on every
 pixel the oracle does not flag as sitting on a discontinuity; hit counts
 identical there; the flagged fraction is reported and bounded.
 """
-import os
 
 import numpy as np
 import pytest
@@ -170,10 +169,6 @@ def test_c4_layout_parity_on_pixel_subset():
                 fwd_samples=samples)
     tr.sync()
     gs, ge = d_surf.cpu().numpy().astype(np.float64), d_env.cpu().numpy().astype(np.float64)
-    if os.path.isdir("gpurun_out"):
-        rows = np.nonzero(np.abs(d_s).sum(1) + np.abs(gs).sum(1))[0]
-        np.save("gpurun_out/grad_c4.npy", dict(rows=rows, d_s=d_s[rows], gs=gs[rows], d_e=d_e, ge=ge,
-                                               pix=pix, ok=ok), allow_pickle=True)
     groups = dict(mu=(0, 3), tu=(3, 6), tv=(6, 9), scale=(9, 11), opacity=(11, 12), albedo=(12, 15),
                   metallic=(15, 16), roughness=(16, 17))
     pairs = {k: (d_s[:, a:b], gs[:, a:b]) for k, (a, b) in groups.items()}
@@ -313,8 +308,6 @@ def test_c3_gradient_parity(params):
     tr.sync()
     np.testing.assert_allclose(d_surf2.cpu().numpy(), gs, rtol=1e-5, atol=1e-6 * np.abs(gs).max())
     np.testing.assert_allclose(d_env2.cpu().numpy(), ge, rtol=1e-5, atol=1e-6 * np.abs(ge).max())
-    np.save("gpurun_out/grad_dump.npy", dict(d_s=d_s, gs=gs, d_e=d_e, ge=ge), allow_pickle=True) \
-        if os.path.isdir("gpurun_out") else None
     # Criterion: per attribute group the L2-relative error is at most 1e-3, and
     # element-wise |g - g_ref| <= 1e-3 |g_ref| + 1e-4 max|g_ref| (the floor covers
     # FP32 cancellation when large per-pixel contributions sum to a small value).
