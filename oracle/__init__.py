@@ -28,7 +28,8 @@ _LIB = os.path.join(_HERE, "liblf_oracle.so")
 CHANNELS = ["T", "W", "depth", "x0", "x1", "x2", "n0", "n1", "n2", "a0", "a1", "a2", "m", "r",
             "rho0", "rho1", "rho2", "nlen", "hits", "t_stop", "id_stop", "sig"]
 NDIFF = 17  # channels 0..16 are differentiable
-MARGINS = ["support", "alpha", "cap", "tmin", "tie", "stop", "cos", "frame"]
+MARGINS = ["support", "alpha", "cap", "tmin", "tie", "stop", "cos", "frame", "cdf", "ptex", "support_shift",
+           "alpha_shift", "tie_shift"]
 PARAM_ORDER = ["mu", "tu", "tv", "scale", "opacity", "albedo", "metallic", "roughness"]
 
 
@@ -70,33 +71,67 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        dp, fp, ip, u32p = (C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int),
-                            C.POINTER(C.c_uint32))
-        _lib.or_render.restype = C.c_int64
-        _lib.or_render.argtypes = [C.POINTER(_Scene), C.POINTER(_Scene), C.POINTER(_Camera), fp, fp, C.c_int,
-                                   C.c_int, C.POINTER(_Params), ip, C.c_int, C.c_int, C.c_uint64, C.c_int, dp,
-                                   dp, dp, C.c_int]
-        _lib.or_grad.restype = None
-        _lib.or_grad.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), fp, C.c_int, C.c_int,
-                                 C.POINTER(_Params), ip, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, dp, dp, dp,
-                                 C.c_int]
-        _lib.or_trace_rays.argtypes = [C.POINTER(_Scene), fp, C.c_int, C.c_int, C.POINTER(_Params), dp, dp,
-                                       C.c_int, dp, dp]
-        _lib.or_shadow_rays.argtypes = [C.POINTER(_Scene), C.POINTER(_Params), dp, dp, C.c_int, dp]
-        _lib.or_philox.argtypes = [u32p, C.c_int, C.c_uint32, C.c_uint32, u32p]
-        _lib.or_uniforms.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, dp]
-        _lib.or_sobol.argtypes = [u32p, C.c_int, C.c_int, u32p]
-        _lib.or_env_tables.argtypes = [fp, C.c_int, C.c_int, dp, dp, dp, dp]
-        _lib.or_env_sample.argtypes = [fp, C.c_int, C.c_int, dp, C.c_int, dp, dp]
-        _lib.or_env_eval.argtypes = [fp, C.c_int, C.c_int, dp, C.c_int, dp, dp]
-        _lib.or_brdf.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, C.c_int, dp]
-        _lib.or_bsdf_sample.argtypes = [dp, dp, C.c_double, C.c_double, dp, C.c_int, dp, dp]
-        _lib.or_ggx_D.restype = C.c_double
-        _lib.or_ggx_D.argtypes = [C.c_double, C.c_double]
-        _lib.or_bsdf_pdf.argtypes = [dp, dp, C.c_double, C.c_double, dp, C.c_int, dp]
-        _lib.or_camera_dirs.argtypes = [C.POINTER(_Camera), C.POINTER(C.c_int), C.c_int, dp]
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def compile_variant(source_text: str, out_path: str) -> str:
+    """Compile a modified copy of the oracle source (test use: a test plants a
+    mistake in the text and checks that a pin catches it)."""
+    src = out_path + ".cpp"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC", src,
+                           "-o", out_path])
+    return out_path
+
+
+class using:
+    """Context manager: route this module's calls to another build of the
+    oracle (a `compile_variant` output) and back."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = _declare(C.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _declare(L):
+    """Argument and result types of the C interface on a loaded library."""
+    dp, fp, ip, u32p = (C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_uint32))
+    L.or_render.restype = C.c_int64
+    L.or_render.argtypes = [C.POINTER(_Scene), C.POINTER(_Scene), C.POINTER(_Camera), fp, fp, C.c_int,
+                            C.c_int, C.POINTER(_Params), ip, C.c_int, C.c_int, C.c_uint64, C.c_int, dp,
+                            dp, dp, C.c_int, dp, dp]
+    L.or_grad.restype = None
+    L.or_grad.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), fp, C.c_int, C.c_int,
+                          C.POINTER(_Params), ip, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, dp, dp, dp,
+                          C.c_int]
+    L.or_trace_rays.argtypes = [C.POINTER(_Scene), fp, C.c_int, C.c_int, C.POINTER(_Params), dp, dp,
+                                C.c_int, dp, dp]
+    L.or_shadow_rays.argtypes = [C.POINTER(_Scene), C.POINTER(_Params), dp, dp, C.c_int, dp]
+    L.or_philox.argtypes = [u32p, C.c_int, C.c_uint32, C.c_uint32, u32p]
+    L.or_uniforms.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, dp]
+    L.or_sobol.argtypes = [u32p, C.c_int, C.c_int, u32p]
+    L.or_env_tables.argtypes = [fp, C.c_int, C.c_int, dp, dp, dp, dp]
+    L.or_env_sample.argtypes = [fp, C.c_int, C.c_int, dp, C.c_int, dp, dp]
+    L.or_env_eval.argtypes = [fp, C.c_int, C.c_int, dp, C.c_int, dp, dp]
+    L.or_brdf.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, C.c_int, dp]
+    L.or_bsdf_sample.argtypes = [dp, dp, C.c_double, C.c_double, dp, C.c_int, dp, dp]
+    L.or_ggx_D.restype = C.c_double
+    L.or_ggx_D.argtypes = [C.c_double, C.c_double]
+    L.or_bsdf_pdf.argtypes = [dp, dp, C.c_double, C.c_double, dp, C.c_int, dp]
+    L.or_camera_dirs.argtypes = [C.POINTER(_Camera), C.POINTER(C.c_int), C.c_int, dp]
+    return L
 
 
 def _p(a, ct):
@@ -137,8 +172,11 @@ def render(scene, cam, env, pixels=None, spp=0, seed=0, shade=True, params=None,
            threads=0):
     """Render camera pixels.
 
-    Returns dict(ch=(n,NCH), rgb=(n,3), margins=(n,8) of the primary ray,
-    margins_shade=(n,8) of the shading rays, rays=int).
+    Returns dict(ch=(n,NCH), rgb=(n,3), margins=(n,NM) of the primary ray,
+    margins_shade=(n,NM) of all shading rays of each pixel, rays=int) and,
+    when shading, the per-sample terms of Eq. 11: samples=(n,spp,3) (c_s, so
+    that rgb = T E(d) + (1 - T)/spp * sum_s c_s) and margins_sample=(n,spp,NM)
+    (each sample's own decisions plus the pixel-level shading decisions).
 
     scene0/env0: parameters the frozen path-replay data come from (default:
     the same as scene/env).
@@ -155,13 +193,20 @@ def render(scene, cam, env, pixels=None, spp=0, seed=0, shade=True, params=None,
     ch = np.zeros((n, len(CHANNELS)), np.float64)
     rgb = np.zeros((n, 3), np.float64)
     mg = np.zeros((n, 2, len(MARGINS)), np.float64)
+    per = bool(shade) and spp > 0
+    srgb = np.zeros((n, spp, 3), np.float64) if per else None
+    smg = np.zeros((n, spp, len(MARGINS)), np.float64) if per else None
     cam_c = _camera(cam)
     prm = _params(params)
     rays = L.or_render(C.byref(sh.s), C.byref(sh0.s), C.byref(cam_c), _p(rgb_env, C.c_float),
                        _p(rgb_env0, C.c_float), env.height, env.width, C.byref(prm), _p(pixels, C.c_int), n,
                        int(spp), C.c_uint64(seed), int(bool(shade)), _p(ch, C.c_double), _p(rgb, C.c_double),
-                       _p(mg, C.c_double), int(threads))
-    return dict(ch=ch, rgb=rgb, margins=mg[:, 0].copy(), margins_shade=mg[:, 1].copy(), rays=int(rays))
+                       _p(mg, C.c_double), int(threads), _p(srgb, C.c_double) if per else None,
+                       _p(smg, C.c_double) if per else None)
+    out = dict(ch=ch, rgb=rgb, margins=mg[:, 0].copy(), margins_shade=mg[:, 1].copy(), rays=int(rays))
+    if per:
+        out.update(samples=srgb, margins_sample=smg)
+    return out
 
 
 def grad(scene, cam, env, pixels, spp, seed, dL_drgb=None, dL_dch=None, shade=True, params=None, threads=0):

@@ -33,10 +33,10 @@
 //
 // Readings of points the paper leaves open (support radius, thresholds, eps,
 // stop rule, env mapping, lobe probability, ...) come in through or_params.
-// The environment importance sampler decides WHICH texel a uniform selects by
-// comparing it with CDF entries rounded to FP32, the precision of the GPU
-// kernel, so both sides take that integer decision in the same precision; the
-// CDF sums themselves are FP64 on both sides.
+// The environment importance sampler works on the FP64 tables throughout: the
+// texel a uniform selects and its position inside the texel.  Where a uniform
+// sits within FP32 rounding of a CDF entry (a renderer with FP32 tables may
+// pick the neighbouring texel) the sample records a margin and is flagged.
 //
 // Compile (see oracle/__init__.py):  g++ -O2 -fopenmp -ffp-contract=off -shared -fPIC
 
@@ -231,11 +231,33 @@ struct SceneD {  // FP64 copy of the FP32 inputs plus the plane normal n^ of eac
   std::vector<double> su, sv, op, m, r;
 };
 
+// ------------------------------------------------------------------------
+// Discontinuity margins (smallest distance of any decision that could change
+// the result to its threshold), kept per ray group: the primary ray of a
+// pixel, and each shading sample.
+// ------------------------------------------------------------------------
+// CDF: distance (in the uniform) of an environment sample's uniforms to the
+// CDF entries that bound the selected texel.  PTEX: angular distance (in
+// radians) of a continuation direction to the texel edges of the
+// piecewise-constant environment pdf that its MIS weight reads.
+// SUPPORT_SHIFT, ALPHA_SHIFT, TIE_SHIFT: the support, opacity-threshold and
+// depth-order decisions again, measured as the shift of the ray (world
+// units, first order, a change of direction counted as (1 + t) times one of
+// the origin) that flips them: a shading ray that starts from another
+// rounding of the same composite moves by such a shift.
+enum { M_SUPPORT, M_ALPHA, M_CAP, M_TMIN, M_TIE, M_STOP, M_COS, M_FRAME, M_CDF, M_PTEX, M_SUPPORT_SHIFT,
+       M_ALPHA_SHIFT, M_TIE_SHIFT, NMARGIN };
+struct Margins {
+  double m[NMARGIN];
+  Margins() { for (double& x : m) x = std::numeric_limits<double>::infinity(); }
+  void put(int k, double v) { m[k] = std::min(m[k], std::fabs(v)); }
+  void merge(const Margins& o) { for (int k = 0; k < NMARGIN; ++k) m[k] = std::min(m[k], o.m[k]); }
+};
+
 struct Env {
   int H = 0, W = 0;
   const float* rgb = nullptr;        // (H, W, 3) lookups (live values)
   std::vector<double> pmf_row, cdf_row, pmf_col, cdf_col;  // sampling tables (FP64)
-  std::vector<float> cdf_row_f, cdf_col_f;                 // the same, rounded to FP32
 };
 
 // Sampling tables: texel weight = (Rec.709 luminance + 1e-6) * sin(theta at the
@@ -273,9 +295,6 @@ void build_env_tables(Env& e) {
       e.cdf_col[(size_t)r * W + c] = pc / rowsum[r];
     }
   }
-  e.cdf_row_f.resize(H); e.cdf_col_f.resize((size_t)H * W);
-  for (int r = 0; r < H; ++r) e.cdf_row_f[r] = (float)e.cdf_row[r];
-  for (size_t i = 0; i < (size_t)H * W; ++i) e.cdf_col_f[i] = (float)e.cdf_col[i];
 }
 
 // y-up equirectangular mapping: theta = acos(w_y), phi = atan2(w_x, -w_z) + pi.
@@ -289,32 +308,56 @@ inline D3 angles_to_dir(double th, double ph) {
 }
 
 // First index i in [0,n) with f[i] > u (f non-decreasing, f[n-1] == 1 > u).
-int first_greater(const float* f, int n, double u) {
+int first_greater(const double* f, int n, double u) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     int mid = (lo + hi) / 2;
-    if ((double)f[mid] > u) hi = mid; else lo = mid + 1;
+    if (f[mid] > u) hi = mid; else lo = mid + 1;
   }
   return lo;
 }
 
-double env_pdf(const Env& e, const D3& w) {
-  double th, ph;
+// Texel (row, column) of a direction in the piecewise-constant pdf; with a
+// margin sink, also the angular distance of the direction to the nearest
+// texel edge (the row edges at the poles are not decisions).
+void pdf_texel(const Env& e, const D3& w, int& r, int& c, double& th, Margins* mg) {
+  double ph;
   dir_to_angles(w, th, ph);
-  int r = std::min(e.H - 1, std::max(0, (int)std::floor(th / PI * e.H)));
-  int c = std::min(e.W - 1, std::max(0, (int)std::floor(ph / (2 * PI) * e.W)));
+  const double y = th / PI * e.H, x = ph / (2 * PI) * e.W;
+  r = std::min(e.H - 1, std::max(0, (int)std::floor(y)));
+  c = std::min(e.W - 1, std::max(0, (int)std::floor(x)));
+  if (mg) {
+    if (y > 0.5 && y < e.H - 0.5) mg->put(M_PTEX, (y - std::nearbyint(y)) * PI / e.H);
+    mg->put(M_PTEX, (x - std::nearbyint(x)) * 2.0 * PI / e.W * std::sin(th));
+  }
+}
+
+double env_pdf(const Env& e, const D3& w, Margins* mg = nullptr) {
+  int r, c;
+  double th;
+  pdf_texel(e, w, r, c, th, mg);
   double st = std::max(std::sin(th), 1e-12);
   return e.pmf_row[r] * e.pmf_col[(size_t)r * e.W + c] * (double)e.H * (double)e.W / (2.0 * PI * PI * st);
 }
 
-void env_sample(const Env& e, double u1, double u2, D3& w, double& pdf) {
-  int r = first_greater(e.cdf_row_f.data(), e.H, u1);
-  double lo = r > 0 ? (double)e.cdf_row_f[r - 1] : 0.0, hi = (double)e.cdf_row_f[r];
+// Inverse-CDF sample of the piecewise-constant environment density: the row
+// from the marginal table, the column from that row's conditional table,
+// uniform inside the texel.  Margin: distance of each uniform to the CDF
+// entries that bound its choice.
+void env_sample(const Env& e, double u1, double u2, D3& w, double& pdf, Margins* mg = nullptr) {
+  int r = first_greater(e.cdf_row.data(), e.H, u1);
+  double lo = r > 0 ? e.cdf_row[r - 1] : 0.0, hi = e.cdf_row[r];
   double fr = std::min(std::max((u1 - lo) / (hi - lo), 0.0), 1.0);
-  const float* row = e.cdf_col_f.data() + (size_t)r * e.W;
+  const double* row = e.cdf_col.data() + (size_t)r * e.W;
   int c = first_greater(row, e.W, u2);
-  double clo = c > 0 ? (double)row[c - 1] : 0.0, chi = (double)row[c];
+  double clo = c > 0 ? row[c - 1] : 0.0, chi = row[c];
   double fc = std::min(std::max((u2 - clo) / (chi - clo), 0.0), 1.0);
+  if (mg) {
+    if (r > 0) mg->put(M_CDF, u1 - lo);
+    if (r < e.H - 1) mg->put(M_CDF, hi - u1);
+    if (c > 0) mg->put(M_CDF, u2 - clo);
+    if (c < e.W - 1) mg->put(M_CDF, chi - u2);
+  }
   double th = PI * ((double)r + fr) / (double)e.H;
   double ph = 2.0 * PI * ((double)c + fc) / (double)e.W;
   w = angles_to_dir(th, ph);
@@ -441,18 +484,7 @@ template <class S> HitS<S> intersect(const Surfel<S>& s, const D3& o, const D3& 
   return h;
 }
 
-// ------------------------------------------------------------------------
-// Per-pixel discontinuity margins (smallest distance of any decision that
-// could change the result to its threshold).
-// ------------------------------------------------------------------------
-enum { M_SUPPORT, M_ALPHA, M_CAP, M_TMIN, M_TIE, M_STOP, M_COS, M_FRAME, NMARGIN };
-struct Margins {
-  double m[NMARGIN];
-  Margins() { for (double& x : m) x = std::numeric_limits<double>::infinity(); }
-  void put(int k, double v) { m[k] = std::min(m[k], std::fabs(v)); }
-};
-
-struct Cand { double t; int id; double r2, alpha, oG; };
+struct Cand { double t; int id; double r2, alpha, oG, g, cosv; };  // g = |grad of r2 / 2| in the plane, cosv = |d.n|
 
 // All candidates of one ray (plane hit in front of the origin); those that
 // pass Eq. 6's support and opacity tests are marked accepted.
@@ -469,13 +501,24 @@ void collect(const SceneD& sc, const Params& P, const D3& o, const D3& d, std::v
     double r2 = u * u + v * v;
     double oG = sc.op[i] * std::exp(-0.5 * r2);
     double alpha = std::min(P.alpha_max, oG);
-    Cand c{t, i, r2, alpha, oG};
+    const double gu = u / sc.su[i], gv = v / sc.sv[i];
+    Cand c{t, i, r2, alpha, oG, std::sqrt(gu * gu + gv * gv), std::fabs(denom)};
     if (r2 <= 4.0 * P.support_r2) cands.push_back(c);  // only near ones can matter for margins
     if (t > P.t_min && r2 <= P.support_r2 && alpha >= P.alpha_min) acc.push_back(c);
   }
   std::sort(acc.begin(), acc.end(), [](const Cand& a, const Cand& b) {
     return a.t < b.t || (a.t == b.t && a.id < b.id);
   });
+}
+
+// Ray shift (world units) that moves u^2 + v^2 of a candidate by `dr2`, or
+// its alpha~ by `da`: a shift moves the hit point in the plane by up to
+// (1 + t) / |cos| of it, and u^2 + v^2 changes by 2 g per unit of that.
+double shift_for_r2(const Cand& c, double dr2) {
+  return std::fabs(dr2) * c.cosv / (2.0 * std::max(c.g, 1e-300) * (1.0 + std::fabs(c.t)));
+}
+double shift_for_alpha(const Cand& c, double da) {
+  return std::fabs(da) * c.cosv / (std::max(c.alpha * c.g, 1e-300) * (1.0 + std::fabs(c.t)));
 }
 
 // Margins of the acceptance decisions of the candidates with t <= t_limit.
@@ -504,9 +547,14 @@ void candidate_margins(const Params& P, const std::vector<Cand>& cands, const st
     const double Tb = T_before(prof, c.t);
     const double a_edge = op[c.id] * std::exp(-0.5 * P.support_r2);
     // Support edge: matters when the candidate would pass the opacity test there.
-    if (in_front && a_edge >= P.alpha_min && Tb * a_edge >= IMPACT)
+    if (in_front && a_edge >= P.alpha_min && Tb * a_edge >= IMPACT) {
       mg->put(M_SUPPORT, (c.r2 - P.support_r2) / P.support_r2);
-    if (in_front && in_support && Tb * P.alpha_min >= IMPACT) mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
+      mg->put(M_SUPPORT_SHIFT, shift_for_r2(c, c.r2 - P.support_r2));
+    }
+    if (in_front && in_support && Tb * P.alpha_min >= IMPACT) {
+      mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
+      mg->put(M_ALPHA_SHIFT, shift_for_alpha(c, c.alpha - P.alpha_min));
+    }
     if (in_support && dense && Tb * c.alpha >= IMPACT) mg->put(M_TMIN, (c.t - P.t_min) / P.t_min);
   }
 }
@@ -535,6 +583,7 @@ Record<S> composite(SP& surf, EP& env, const Params& P, const D3& o, const D3& d
   for (; j < acc.size(); ++j) {
     Surfel<S> s = surf.get(acc[j].id);
     HitS<S> h = intersect(s, o, d, P.alpha_max);
+    const double T_in = val(T);  // transmittance in front of hit j
     S w = T * h.alpha;
     W = W + w;
     Sx = Sx + scl(h.x, w);
@@ -554,8 +603,36 @@ Record<S> composite(SP& surf, EP& env, const Params& P, const D3& o, const D3& d
       mg->put(M_CAP, val(h.oG) - P.alpha_max);
       // Exactly equal depths (coplanar surfels) are ordered by id on both
       // sides; only distinct but nearly equal depths may swap in FP32.
-      if (j + 1 < acc.size() && acc[j + 1].t != acc[j].t)
-        mg->put(M_TIE, (acc[j + 1].t - acc[j].t) / std::max(1.0, std::fabs(acc[j].t)));
+      // Swapping hits j and j+1 leaves T behind them unchanged and moves the
+      // weighted sum of each composited attribute z by exactly
+      // T_in alpha_j alpha_j+1 (z_j - z_j+1) (position and depth by the tiny
+      // depth gap), the record z / W by that over W >= 1 - T behind both, so
+      // a near tie counts only when that change reaches IMPACT.
+      double swap = 0.0;
+      if (j + 1 < acc.size()) {
+        const SceneD& sd = *surf.sc;
+        const int i0 = acc[j].id, i1 = acc[j + 1].id;
+        const double f0 = dot(d, sd.nh[i0]) < 0.0 ? 1.0 : -1.0, f1 = dot(d, sd.nh[i1]) < 0.0 ? 1.0 : -1.0;
+        const D3 dn = scl(sd.nh[i0], f0) - scl(sd.nh[i1], f1), da = sd.a[i0] - sd.a[i1];
+        const double dz = std::max({std::fabs(dn.x), std::fabs(dn.y), std::fabs(dn.z), std::fabs(da.x),
+                                    std::fabs(da.y), std::fabs(da.z), std::fabs(sd.m[i0] - sd.m[i1]),
+                                    std::fabs(sd.r[i0] - sd.r[i1])});
+        const double a0 = val(h.alpha), a1 = acc[j + 1].alpha;
+        swap = T_in * a0 * a1 * dz / std::max(1e-300, 1.0 - T_in * (1.0 - a0) * (1.0 - a1));
+        // when the composite stops at hit j, a swap composites hit j+1 in its place
+        if (val(T) < P.T_min) swap = T_in;
+      }
+      if (j + 1 < acc.size() && acc[j + 1].t != acc[j].t && swap >= IMPACT) {
+        const double gap = acc[j + 1].t - acc[j].t;
+        mg->put(M_TIE, gap / std::max(1.0, std::fabs(acc[j].t)));
+        // t_k = (mu_k - o).n_k / (d.n_k): a shift of the origin moves the gap
+        // by the shift times n_j+1 / (d.n_j+1) - n_j / (d.n_j)
+        const D3& n0 = surf.sc->nh[acc[j].id];
+        const D3& n1 = surf.sc->nh[acc[j + 1].id];
+        const D3 dv = scl(n1, 1.0 / dot(d, n1)) - scl(n0, 1.0 / dot(d, n0));
+        const double sens = norm(dv) * (1.0 + std::fabs(acc[j].t));
+        if (sens > 0.0) mg->put(M_TIE_SHIFT, gap / sens);
+      }
     }
     if (val(T) < P.T_min) { ++j; break; }
   }
@@ -582,9 +659,14 @@ double shadow(const SceneD& sc, const Params& P, const D3& o, const D3& d, std::
     for (const Cand& c : cands) {
       bool in_front = c.t > P.t_min, in_support = c.r2 <= P.support_r2, dense = c.alpha >= P.alpha_min;
       const double a_edge = sc.op[c.id] * std::exp(-0.5 * P.support_r2);
-      if (in_front && a_edge >= P.alpha_min && V * a_edge >= IMPACT)
+      if (in_front && a_edge >= P.alpha_min && V * a_edge >= IMPACT) {
         mg->put(M_SUPPORT, (c.r2 - P.support_r2) / P.support_r2);
-      if (in_front && in_support && V * P.alpha_min >= IMPACT) mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
+        mg->put(M_SUPPORT_SHIFT, shift_for_r2(c, c.r2 - P.support_r2));
+      }
+      if (in_front && in_support && V * P.alpha_min >= IMPACT) {
+        mg->put(M_ALPHA, (c.alpha - P.alpha_min) / P.alpha_min);
+        mg->put(M_ALPHA_SHIFT, shift_for_alpha(c, c.alpha - P.alpha_min));
+      }
       if (in_support && dense && V * c.alpha >= IMPACT) mg->put(M_TMIN, (c.t - P.t_min) / P.t_min);
     }
   }
@@ -713,10 +795,15 @@ struct Work {  // per-thread scratch
   std::vector<std::pair<double, double>> prof;
 };
 
+// Sample data of one pixel.  Margins: `mg` (nullable) receives every shading
+// decision of the pixel; `smg` (nullable) receives one entry per sample with
+// that sample's own decisions plus the pixel-level ones (view cosine and
+// frame orientation at the primary record), which every sample depends on.
 void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Record<double>& rec,
                     const D3& d, uint32_t pixel, int spp, uint64_t seed, Work& wk,
-                    std::vector<SampleFz>& out, Margins* mg, int64_t* rays) {
+                    std::vector<SampleFz>& out, Margins* mg, int64_t* rays, std::vector<Margins>* smg = nullptr) {
   out.assign(spp, SampleFz());
+  if (smg) smg->assign(spp, Margins());
   if (rec.hits == 0) return;
   D3 wo = scl(d, -1.0), n = rec.n;
   D3 xs = rec.x + scl(n, P.ray_offset);
@@ -724,21 +811,27 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
   // View-side cosine (the Lambert term makes the estimator jump at 0) and the
   // sign of n_z that orients the sampling frame (an exact 0 is the same on
   // both sides).
-  if (mg) { mg->put(M_COS, co); if (n.z != 0.0) mg->put(M_FRAME, n.z); }
+  Margins pix;
+  pix.put(M_COS, co);
+  if (n.z != 0.0) pix.put(M_FRAME, n.z);
+  if (mg) mg->merge(pix);
+  if (smg) for (Margins& m : *smg) m.merge(pix);
   if (co <= 0.0) return;
   const double ps = P.brdf_mode == 1 ? 0.0 : P.p_spec;
   SurfelValues sv{&sc};
   EnvValues ev{&env0};
   for (int s = 0; s < spp; ++s) {
     SampleFz& fz = out[s];
+    Margins ms;
+    Margins* m = (mg || smg) ? &ms : nullptr;
     double u[9];
     sample_uniforms(pixel, (uint32_t)s, seed, P.sampler, u);
     if (P.sampling_mode != 1) {  // (i) environment NEE at the primary record
-      env_sample(env0, u[0], u[1], fz.we, fz.pe);
+      env_sample(env0, u[0], u[1], fz.we, fz.pe, m);
       double ce = dot(n, fz.we);
       if (ce > 0.0 && fz.pe > 0.0) {
         fz.e_ok = 1;
-        fz.Ve = shadow(sc, P, xs, fz.we, wk.cands, wk.acc, mg);
+        fz.Ve = shadow(sc, P, xs, fz.we, wk.cands, wk.acc, m);
         if (rays) ++*rays;
         double pb = pdf_bsdf(n, wo, fz.we, rec.r, ps);
         fz.wenv = P.sampling_mode == 2 ? 1.0 : fz.pe * fz.pe / (fz.pe * fz.pe + pb * pb);
@@ -748,48 +841,59 @@ void frozen_samples(const SceneD& sc, const Env& env0, const Params& P, const Re
     fz.wi = (u[2] < ps) ? sample_ggx(n, wo, rec.r, u[3], u[4]) : sample_cos(n, u[3], u[4]);
     double ci = dot(n, fz.wi);
     double pb = pdf_bsdf(n, wo, fz.wi, rec.r, ps);
-    if (!(ci > 0.0 && pb > 0.0)) continue;
-    fz.b_ok = 1;
-    fz.pb = pb;
-    double pe_i = env_pdf(env0, fz.wi);
-    fz.wbsdf = P.sampling_mode == 1 ? 1.0 : pb * pb / (pb * pb + pe_i * pe_i);
-    collect(sc, P, xs, fz.wi, wk.cands, wk.acc);
-    Record<double> r2 = composite<double>(sv, ev, P, xs, fz.wi, wk.acc, mg, &wk.prof);
-    candidate_margins(P, wk.cands, sc.op, r2.hits && val(r2.T) < P.T_min ? r2.t_stop : 1e300, mg, &wk.prof);
-    if (rays) ++*rays;
-    fz.T2 = r2.T;
-    if (r2.hits == 0) continue;
-    fz.sec_ok = 1;
-    D3 n2 = r2.n, wo2 = scl(fz.wi, -1.0);
-    D3 xs2 = r2.x + scl(n2, P.ray_offset);
-    double co2 = dot(n2, wo2);
-    if (mg) mg->put(M_COS, co2);
-    for (int q = 0; q < 2; ++q) {
-      env_sample(env0, u[5 + 2 * q], u[6 + 2 * q], fz.wq[q], fz.pq[q]);
-      double cq = dot(n2, fz.wq[q]);
-      if (!(cq > 0.0 && co2 > 0.0 && fz.pq[q] > 0.0)) continue;
-      fz.q_ok[q] = 1;
-      fz.Vq[q] = shadow(sc, P, xs2, fz.wq[q], wk.cands, wk.acc, mg);
+    if (ci > 0.0 && pb > 0.0) {
+      fz.b_ok = 1;
+      fz.pb = pb;
+      if (P.sampling_mode == 1) {
+        fz.wbsdf = 1.0;
+      } else {
+        double pe_i = env_pdf(env0, fz.wi, m);
+        fz.wbsdf = pb * pb / (pb * pb + pe_i * pe_i);
+      }
+      collect(sc, P, xs, fz.wi, wk.cands, wk.acc);
+      Record<double> r2 = composite<double>(sv, ev, P, xs, fz.wi, wk.acc, m, &wk.prof);
+      candidate_margins(P, wk.cands, sc.op, r2.hits && val(r2.T) < P.T_min ? r2.t_stop : 1e300, m, &wk.prof);
       if (rays) ++*rays;
-      D3 f2 = brdf<double>(n2, wo2, fz.wq[q], r2.a, r2.m, r2.r, P.brdf_mode);
-      fz.fcos_q[q] = scl(f2, cq);
+      fz.T2 = r2.T;
+      if (r2.hits > 0) {
+        fz.sec_ok = 1;
+        D3 n2 = r2.n, wo2 = scl(fz.wi, -1.0);
+        D3 xs2 = r2.x + scl(n2, P.ray_offset);
+        double co2 = dot(n2, wo2);
+        if (m) m->put(M_COS, co2);
+        for (int q = 0; q < 2; ++q) {
+          env_sample(env0, u[5 + 2 * q], u[6 + 2 * q], fz.wq[q], fz.pq[q], m);
+          double cq = dot(n2, fz.wq[q]);
+          if (!(cq > 0.0 && co2 > 0.0 && fz.pq[q] > 0.0)) continue;
+          fz.q_ok[q] = 1;
+          fz.Vq[q] = shadow(sc, P, xs2, fz.wq[q], wk.cands, wk.acc, m);
+          if (rays) ++*rays;
+          D3 f2 = brdf<double>(n2, wo2, fz.wq[q], r2.a, r2.m, r2.r, P.brdf_mode);
+          fz.fcos_q[q] = scl(f2, cq);
+        }
+      }
     }
+    if (mg) mg->merge(ms);
+    if (smg) (*smg)[s].merge(ms);
   }
 }
 
+// Pixel value L = T E(d) + (1 - T) / S * sum_s c_s, c_s = c_e + c_b of
+// Eq. 11.  `per_sample` (nullable, spp entries) receives each term c_s.
 template <class S, class EP>
 V3<S> eval_pixel(const Record<S>& rec, EP& env, const Params& P, const D3& d, const std::vector<SampleFz>& fzs,
-                 int spp) {
+                 int spp, V3<S>* per_sample = nullptr) {
   D3 wo = scl(d, -1.0);
   V3<S> Ld = env.lookup(d);
   V3<S> sum;
   for (int s = 0; s < spp && rec.hits > 0; ++s) {
     const SampleFz& fz = fzs[s];
+    V3<S> cs;
     if (fz.e_ok) {
       V3<S> f = brdf<S>(rec.n, wo, fz.we, rec.a, rec.m, rec.r, P.brdf_mode);
       S c = dot(rec.n, lift<S>(fz.we)) * (fz.Ve * fz.wenv / fz.pe);
       V3<S> E = env.lookup(fz.we);
-      sum = sum + scl(mul(f, E), c);
+      cs = cs + scl(mul(f, E), c);
     }
     if (fz.b_ok) {
       V3<S> f = brdf<S>(rec.n, wo, fz.wi, rec.a, rec.m, rec.r, P.brdf_mode);
@@ -805,8 +909,10 @@ V3<S> eval_pixel(const Record<S>& rec, EP& env, const Params& P, const D3& d, co
           inc = inc + V3<S>(E.x * (fz.fcos_q[q].x * k), E.y * (fz.fcos_q[q].y * k), E.z * (fz.fcos_q[q].z * k));
         }
       }
-      sum = sum + mul(beta, inc);
+      cs = cs + mul(beta, inc);
     }
+    sum = sum + cs;
+    if (per_sample) per_sample[s] = cs;
   }
   S A = 1.0 - rec.T;
   S kA = A / (double)spp;
@@ -988,12 +1094,6 @@ void or_shadow_rays(const or_scene* sc_in, const or_params* pp, const double* or
   }
 }
 
-// Render a set of camera pixels.  `sc0`/`env0` are the parameters the frozen
-// sample data come from (path replay); pass the same pointers as `sc`/`env`
-// for an ordinary render.  Outputs per pixel: NCH channels, RGB radiance
-// (when shade != 0), 2 x NMARGIN margins (nullable): those of the primary
-// ray, then those of the shading rays.  Returns the number of rays
-// traced (primary + shadow + continuation).
 // Pixel ray directions (the FP64 pinhole direction rounded once to FP32).
 void or_camera_dirs(const or_camera* cam_in, const int* pixels, int n, double* dirs) {
   Cam cam = make_cam(cam_in->eye, cam_in->target, cam_in->up, cam_in->fovy_deg, cam_in->width, cam_in->height);
@@ -1005,9 +1105,19 @@ void or_camera_dirs(const or_camera* cam_in, const int* pixels, int n, double* d
   }
 }
 
+// Render a set of camera pixels.  `sc0`/`env0` are the parameters the frozen
+// sample data come from (path replay); pass the same pointers as `sc`/`env`
+// for an ordinary render.  Outputs per pixel: NCH channels, RGB radiance
+// (when shade != 0), 2 x NMARGIN margins (nullable): those of the primary
+// ray, then those of every shading ray of the pixel.  Per sample (nullable,
+// pixel-major, spp entries per pixel): the term c_s of Eq. 11 (RGB) and
+// NMARGIN margins of that sample's decisions (with the pixel-level shading
+// decisions folded in).  Returns the number of rays traced (primary +
+// shadow + continuation).
 int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera* cam_in, const float* env_rgb,
                   const float* env0_rgb, int H, int W, const or_params* pp, const int* pixels, int n_pix, int spp,
-                  uint64_t seed, int shade, double* ch_out, double* rgb_out, double* margins, int n_threads) {
+                  uint64_t seed, int shade, double* ch_out, double* rgb_out, double* margins, int n_threads,
+                  double* samp_rgb, double* samp_margins) {
   SceneD sc = to_scene(sc_in);
   SceneD sc0 = (sc0_in && sc0_in != sc_in) ? to_scene(sc0_in) : SceneD();
   const SceneD& base = (sc0_in && sc0_in != sc_in) ? sc0 : sc;
@@ -1022,6 +1132,8 @@ int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera
   {
     Work wk;
     std::vector<SampleFz> fzs;
+    std::vector<Margins> smg;
+    std::vector<V3<double>> terms;
     SurfelValues sv{&sc}, sv0{&base};
     EnvValues ev{&e}, ev0{&e0};
 #pragma omp for schedule(dynamic, 1)
@@ -1043,9 +1155,16 @@ int64_t or_render(const or_scene* sc_in, const or_scene* sc0_in, const or_camera
           collect(base, P, cam.eye, d, wk.cands, wk.acc);
           r0 = composite<double>(sv0, ev0, P, cam.eye, d, wk.acc, nullptr);
         }
-        frozen_samples(base, e0, P, r0, d, (uint32_t)p, spp, seed, wk, fzs, &mgs, &rays);
-        V3<double> L = eval_pixel<double>(r, ev, P, d, fzs, spp);
+        frozen_samples(base, e0, P, r0, d, (uint32_t)p, spp, seed, wk, fzs, &mgs, &rays,
+                       samp_margins ? &smg : nullptr);
+        terms.assign(spp, V3<double>());
+        V3<double> L = eval_pixel<double>(r, ev, P, d, fzs, spp, terms.data());
         rgb_out[3 * i] = L.x; rgb_out[3 * i + 1] = L.y; rgb_out[3 * i + 2] = L.z;
+        for (int s = 0; s < spp; ++s) {
+          const size_t o = (size_t)i * spp + s;
+          if (samp_rgb) { samp_rgb[3 * o] = terms[s].x; samp_rgb[3 * o + 1] = terms[s].y; samp_rgb[3 * o + 2] = terms[s].z; }
+          if (samp_margins) for (int k = 0; k < NMARGIN; ++k) samp_margins[o * NMARGIN + k] = smg[s].m[k];
+        }
       }
       if (margins)
         for (int k = 0; k < NMARGIN; ++k) {
