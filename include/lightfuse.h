@@ -255,8 +255,12 @@ lf_status lf_shade_bounce(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_d
  *   - width * height * spp must be at most (LF_STATIC_SCRATCH_BYTES - 256) /
  *     128 = 524286 samples; larger requests return LF_ERR_INVALID with a
  *     message and enqueue nothing.
- *   - The first call on a device looks up the array's device address (with
+ *   - The calling thread's current device must be the context's device
+ *     (LF_ERR_INVALID otherwise).  The first call after a context was
+ *     created on a device looks up the array's device address there (with
  *     that device current); make that first call before any stream capture.
+ *     A cudaDeviceReset ends the contexts made before it; the next lf_create
+ *     on the device makes the following call look the address up again.
  *   - All calls share the array, which keeps the last call's contents; each
  *     call clears the counters that must start at zero.  Calls whose work
  *     overlaps on the GPU (other streams, contexts or threads) race on it.
@@ -265,6 +269,19 @@ lf_status lf_shade_bounce(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_d
 #define LF_STATIC_SCRATCH_BYTES (64u << 20)
 lf_status lf_shade_bounce_static(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
                                  uint64_t seed, float* rgb_dev, unsigned long long* ray_count_dev);
+
+/*
+ * The per-sample terms of Eq. 11 behind an lf_shade_bounce result (an
+ * inspection call): terms_dev[(p * spp + s) * 3 + c] = c_s, the NEE plus BSDF
+ * term of sample s of pixel p evaluated from the G-buffer and the sample
+ * buffer `samples_dev` of the lf_shade_bounce call with the same camera,
+ * G-buffer, environment and spp, so that
+ * rgb = T E(d) + (1 - T) / spp * sum_s c_s up to the order of the sum.
+ * Zero for pixels without a surface facing the camera.  terms_dev: device,
+ * width * height * spp * 3 floats.
+ */
+lf_status lf_shade_sample_terms(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_dev, int env_id, int spp,
+                                const void* samples_dev, size_t samples_bytes, float* terms_dev);
 
 /* Scratch bytes lf_trace_backward needs for a width x height image at spp
  * samples when it has to replay the shading (fwd_samples == NULL); with the
@@ -400,17 +417,30 @@ int lf_bvh_wide_node_bytes(void);
 
 /* ---------------------------------------------------------------- serving
  *
+ * The editing and relighting stage of the method (Sec. 3.4.2) served as a
+ * request loop.  The paper's edits are a target rigid transform of an
+ * object (Eq. 2: T = (R, t) on its surfel centres and orientations), a
+ * change of base colour, metallic or roughness, and a recovered or
+ * user-provided environment map; each edited state is then re-traced and
+ * shaded (Eq. 6-7, Eq. 11).  The loop itself (admission, batching, latency)
+ * has no counterpart in the paper.
+ *
  * A request is one edit plus one camera.  Edits are applied to the served
  * scene in submission order, each creating a new version of the edited
  * object (copy on write), so a request renders exactly the scene state
  * after its own edit, even while later requests are already editing.
  * Admission: a request is admitted when a slot is free and its frame and
  * object version fit under the memory budget; admitted requests are
- * batched into shared kernel launches (work items from several requests in
- * one launch) on a pool of streams, so their work overlaps on the device.
+ * batched into shared kernel launches (one primary-ray launch and one
+ * shading wavefront carry the work of every request of a launch group) on
+ * a pool of streams, so their work overlaps on the device.
  */
 typedef enum { LF_EDIT_NONE = 0, LF_EDIT_MOVE = 1, LF_EDIT_MATERIAL = 2, LF_EDIT_ENV = 3 } lf_edit_kind;
 
+/* One edit of Sec. 3.4.2.  MOVE is Eq. 2's rigid transform (as
+ * lf_bvh_refit), MATERIAL the base-colour / metallic / roughness edit (as
+ * lf_material_set), ENV the switch to another registered environment map
+ * (the recovered or user-provided lighting of the relit state). */
 typedef struct {
   int kind;          /* lf_edit_kind */
   int object_id;     /* MOVE / MATERIAL */
@@ -449,7 +479,11 @@ typedef struct lf_serve lf_serve;
  * 2 * max_slots finished ones stay unpolled ends in LF_ERR_TIMEOUT). */
 lf_status lf_serve_create(lf_ctx* ctx, size_t mem_budget_bytes, int max_slots, int n_streams, int batch_window_us,
                           lf_serve** out);
-/* Enqueue a request (host copy); returns its ticket.  Never blocks. */
+/* Enqueue a request (host copy); returns its ticket.  Never blocks.  The
+ * frame is the one-bounce render (Eq. 6-7, Eq. 11) of the scene state after
+ * the request's own edit: LF_ERR_INVALID (nothing enqueued) for an unknown
+ * object or environment, a MOVE that is not rigid, or a camera beyond
+ * 1024 x 1024. */
 lf_status lf_serve_submit(lf_serve* srv, const lf_request* req, uint64_t* ticket);
 /* done = 1 when finished; then frame_host (width*height*3 floats, may be
  * NULL) receives the image and timing (may be NULL) the timestamps. */

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("lf_shade_bounce", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P, _P,
                                   C.c_size_t]),
     ("lf_shade_bounce_static", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P]),
+    ("lf_shade_sample_terms", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, _P, C.c_size_t, _P]),
     ("lf_backward_scratch_bytes", C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     ("lf_trace_backward", C.c_int, [_P, C.POINTER(LfCamera), _P, C.c_int, C.c_int, C.c_uint64, _P, _P, _P, _P, _P,
                                     _P, C.c_size_t]),

@@ -202,6 +202,7 @@ lf_status lf_create(const lf_params* params, void* stream, lf_ctx** out) {
   c->stream = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) lf_static_scratch_forget(c->device);
   if (e == cudaSuccess) e = dev_alloc(&c->status_dev, 1);
   if (e == cudaSuccess) e = dev_alloc(&c->loss_dev, 1);
   if (e == cudaSuccess) e = cudaMemset(c->status_dev, 0, sizeof(int));
@@ -538,6 +539,20 @@ lf_status lf_shade_bounce(lf_ctx* c, const lf_camera* cam, const float* gbuf, in
                                     c->profile ? c->prof_ev + 2 : nullptr));
   LF_CUDA(c, launch_shade_combine(B, c->dp, S, c->stream));
   if (c->profile) LF_CUDA(c, cudaEventRecord(c->prof_ev[7], c->stream));
+  return LF_OK;
+}
+
+lf_status lf_shade_sample_terms(lf_ctx* c, const lf_camera* cam, const float* gbuf, int env_id, int spp,
+                                const void* samples, size_t samples_bytes, float* terms) {
+  lf_status st = check_render(c, cam, env_id);
+  if (st != LF_OK) return st;
+  if (!gbuf || !terms || spp <= 0 || spp > (1 << 20)) return fail(c, LF_ERR_INVALID, "bad arguments");
+  if ((long long)cam->width * cam->height * spp >= (1LL << 30)) return fail(c, LF_ERR_INVALID, "too many samples");
+  if (!samples || samples_bytes < lf_shade_scratch_bytes(cam->width, cam->height, spp))
+    return fail(c, LF_ERR_INVALID, "sample buffer too small");
+  const ShadeBatch B = one_job(c, cam, gbuf, env_id, spp, 0, nullptr);
+  const SampleBuf S = sample_buf(const_cast<void*>(samples), B.n_items);
+  LF_CUDA(c, launch_shade_terms(B, c->dp, S, terms, c->sms, c->stream));
   return LF_OK;
 }
 

@@ -367,6 +367,12 @@ __device__ __forceinline__ unsigned long long hit_key(float t, float tl, int id)
   return ((unsigned long long)tb << 32) | ((unsigned long long)q << 24) | (unsigned long long)(id & 0xffffff);
 }
 __device__ __forceinline__ float key_t(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
+// The low part of the depth that hit_key kept (to 1/256 of an ulp of key_t).
+__device__ __forceinline__ float key_tl(unsigned long long k) {
+  const unsigned tb = (unsigned)(k >> 32);
+  const float ulp = __uint_as_float(tb & 0x7f800000u) * 1.1920928955078125e-7f;
+  return (float)((int)((k >> 24) & 0xffu) - 128) * (ulp * (1.0f / 256.0f));
+}
 
 // Normal of a packed record facing the ray (two-sided surfels).
 __device__ __forceinline__ float3 record_normal(const Rec& r, const float3 d) {
@@ -457,6 +463,15 @@ __device__ __forceinline__ void env_sample(const EnvDev& e, float u1, float u2, 
 // Metallic-roughness: k_d/pi + F D G / (4 cos_i cos_o); GGX D (Walter et al.
 // 2007), separable Smith G, Schlick F; k_d = a (1-m), F0 = 0.04 (1-m) + a m,
 // alpha_g = r^2.  brdf_mode 1: a / pi.
+//
+// GGX denominator (n.h)^2 (alpha_g^2 - 1) + 1 = |n x h|^2 + alpha_g^2 (n.h)^2
+// for unit n and h: the right-hand form has no cancellation when h is close
+// to n (a glossy lobe), where 1 - (n.h)^2 computed from n.h loses most of its
+// digits in FP32.
+__device__ __forceinline__ float ggx_den(float3 n, float3 h, float nh, float a2) {
+  const float3 c = f3(n.y * h.z - n.z * h.y, n.z * h.x - n.x * h.z, n.x * h.y - n.y * h.x);
+  return fmaf(a2 * nh, nh, dot3(c, c));
+}
 __device__ __forceinline__ float3 brdf_eval(float3 n, float3 wo, float3 wi, float3 a, float m, float r, int mode) {
   float ci = dot3(n, wi), co = dot3(n, wo);
   if (!(ci > 0.0f) || !(co > 0.0f)) return f3(0.f, 0.f, 0.f);
@@ -466,7 +481,7 @@ __device__ __forceinline__ float3 brdf_eval(float3 n, float3 wo, float3 wi, floa
   float ag = r * r, a2 = ag * ag;
   float3 h = normalize3(wi + wo);
   float nh = dot3(n, h), oh = dot3(wo, h);
-  float den = nh * nh * (a2 - 1.0f) + 1.0f;
+  float den = ggx_den(n, h, nh, a2);
   float D = a2 / (PI_F * den * den);
   float Qi = 2.0f / (ci + sqrtf(a2 + (1.0f - a2) * ci * ci));
   float Qo = 2.0f / (co + sqrtf(a2 + (1.0f - a2) * co * co));
@@ -488,7 +503,7 @@ __device__ __forceinline__ void brdf_adjoint(float3 n, float3 wo, float3 wi, flo
   float ag = r * r, a2 = ag * ag;
   float3 h = normalize3(wi + wo);
   float nh = dot3(n, h), oh = dot3(wo, h);
-  float den = nh * nh * (a2 - 1.0f) + 1.0f;
+  float den = ggx_den(n, h, nh, a2);
   float D = a2 / (PI_F * den * den);
   float si = sqrtf(a2 + (1.0f - a2) * ci * ci), so = sqrtf(a2 + (1.0f - a2) * co * co);
   float Qi = 2.0f / (ci + si), Qo = 2.0f / (co + so);
@@ -529,16 +544,15 @@ __device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
   b2 = f3(b, sgn + n.y * n.y * a, -n.y);
 }
 
-__device__ __forceinline__ float ggx_D(float nh, float a2) {
-  float den = nh * nh * (a2 - 1.0f) + 1.0f;
-  return a2 / (PI_F * den * den);
-}
-
-// GGX half vector with density D(h)(n.h) (Walter et al. 2007), mirrored.
+// GGX half vector with density D(h)(n.h) (Walter et al. 2007), mirrored:
+// cos^2 theta_h = (1 - u1) / (1 + (a2 - 1) u1), evaluated as
+// (1 - u1) / ((1 - u1) + a2 u1) and sin^2 as a2 u1 / (same), which keeps the
+// digits of both for a glossy lobe (small a2) at either end of u1 (1 - u1 is
+// exact for the 24-bit uniforms).
 __device__ __forceinline__ float3 sample_ggx(float3 n, float3 wo, float r, float u1, float u2) {
   float ag = r * r, a2 = ag * ag;
-  float c2 = (1.0f - u1) / (1.0f + (a2 - 1.0f) * u1);
-  float ct = sqrtf(fmaxf(0.0f, c2)), st = sqrtf(fmaxf(0.0f, 1.0f - c2));
+  float om = 1.0f - u1, inv = 1.0f / fmaf(a2, u1, om);
+  float ct = sqrtf(om * inv), st = sqrtf(a2 * u1 * inv);
   float sp, cp;
   sincosf(2.0f * PI_F * u2, &sp, &cp);
   float3 b1, b2;
@@ -566,8 +580,8 @@ __device__ __forceinline__ float pdf_bsdf(float3 n, float3 wo, float3 wi, float 
       float3 h = hs * (1.0f / hl);
       float nh = dot3(n, h), oh = dot3(wo, h);
       if (nh > 0.0f && oh > 0.0f) {
-        float ag = r * r;
-        pg = ggx_D(nh, ag * ag) * nh / (4.0f * oh);
+        float ag = r * r, a2 = ag * ag, den = ggx_den(n, h, nh, a2);
+        pg = a2 / (PI_F * den * den) * nh / (4.0f * oh);
       }
     }
   }

@@ -431,8 +431,14 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   kb.mc = st.mc;
   kb.ma = st.ma;
   const Ray ray = make_ray(o, d);
-  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f;
-  float3 Sx = f3(0.f, 0.f, 0.f), Sn = Sx, Sa = Sx;
+  // The composited position sum w x_j / (W + eps) is kept as
+  // (o + t_ref d) W / (W + eps) + d sum w (t_j - t_ref) / (W + eps) around
+  // the depth t_ref + tl_ref of the first composited hit (its key keeps the
+  // low part): the hit points of a ray differ by little along it, so the
+  // offsets stay small and the position carries about one rounding of
+  // o + t_ref d instead of one per hit (shading rays start there).
+  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f, Sdt = 0.0f, t_ref = 0.0f, tl_ref = 0.0f;
+  float3 Sn = f3(0.f, 0.f, 0.f), Sa = Sn;
   int hits = 0;
   unsigned long long stop_key = 0ull, last = 0ull;
   bool done = false;
@@ -473,10 +479,12 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     const unsigned stopm = gballot(g, have && Ta < P.T_min);
     const int lastc = stopm ? __ffs(stopm) - 1 : n - 1;
     const float w = (have && g.c <= lastc) ? Tb * alpha : 0.0f;
+    if (round == 0) {
+      t_ref = gshfl(g, t, 0);
+      tl_ref = key_tl(gshfl(g, kb.bk, 0));
+    }
     W += gsum(g, w);
-    Sx.x += gsum(g, w * fmaf(d.x, t, o.x));
-    Sx.y += gsum(g, w * fmaf(d.y, t, o.y));
-    Sx.z += gsum(g, w * fmaf(d.z, t, o.z));
+    Sdt += gsum(g, w * (t - t_ref));
     St += gsum(g, w * t);
     Sn.x += gsum(g, w * nj.x);
     Sn.y += gsum(g, w * nj.y);
@@ -499,7 +507,11 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   const float inv = 1.0f / (W + P.eps_w);
   s.T = T;
   s.W = W;
-  s.x = Sx * inv;
+  {
+    const float wf = W * inv, lo = fmaf(Sdt, inv, tl_ref * wf);
+    s.x = f3(fmaf(wf, fmaf(d.x, t_ref, o.x), d.x * lo), fmaf(wf, fmaf(d.y, t_ref, o.y), d.y * lo),
+             fmaf(wf, fmaf(d.z, t_ref, o.z), d.z * lo));
+  }
   s.depth = St * inv;
   s.a = Sa * inv;
   s.Sa = Sa;

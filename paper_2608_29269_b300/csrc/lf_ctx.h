@@ -73,3 +73,6 @@ lf::TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id);
 // Wide-BVH arguments over the context's own storage (bases 0).
 lf::WideArgs lf_ctx_wide_args(lf_ctx* c);
 lf::CamDev lf_ctx_cam(const lf_camera& c);
+// Drop the cached device address of the allocation-free entry point's
+// scratch array for `device` (lf_static.cu); lf_create calls it.
+void lf_static_scratch_forget(int device);

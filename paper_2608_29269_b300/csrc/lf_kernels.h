@@ -96,6 +96,24 @@ struct TraceArgs {
 
 cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, cudaStream_t st);
 
+// Primary rays of up to MAX_PRIMARY_JOBS images in one launch, each with its
+// own scene snapshot, environment, camera and G-buffer (the launcher fills
+// tile0).
+constexpr int MAX_PRIMARY_JOBS = 32;
+struct PrimaryJob {
+  const Inst* insts;
+  int n_inst;
+  EnvDev env;
+  CamDev cam;
+  float* gbuf;
+  int tile0;
+};
+struct PrimaryBatch {
+  int n_jobs;
+  PrimaryJob jobs[MAX_PRIMARY_JOBS];
+};
+cudaError_t launch_trace_primary_batch(PrimaryBatch& B, const DevParams& P, int* status, cudaStream_t st);
+
 // Adjoint (lf_backward.cu)
 constexpr int SHADE_GRAD_CH = 9;  // per pixel: g_n (3), g_a (3), g_m, g_r, g_T
 cudaError_t launch_trace_backward(const TraceArgs& a, const SceneDev& s, const CamDev& cam, const float* gbuf,

@@ -11,7 +11,47 @@ constexpr int TILE_W = RGROUPS >= 4 ? 4 : RGROUPS;  // a block's pixels form a T
 constexpr int TILE_H = RGROUPS / TILE_W;
 
 // WIDE lanes per pixel: cooperative k-buffer composite of the primary ray
-// (lf_coop.cuh); lane 0 writes the G-buffer.
+// through pixel (x, y) (lf_coop.cuh); lane 0 writes the G-buffer.
+template <class Cnt>
+__device__ __forceinline__ void trace_pixel(const Grp& g, const CStack& st, const Inst* insts, int n_inst,
+                                            const DevParams& P, const EnvDev& env, int* status,
+                                            unsigned long long* counters, const CamDev& cam, float* __restrict__ gbuf,
+                                            int x, int y) {
+  const int p = y * cam.W + x;
+  const size_t NP = (size_t)cam.W * cam.H;
+  float3 d = f3(0.f, 0.f, 0.f);
+  if (g.c == 0) d = camera_dir(cam, p);  // FP64 once per pixel
+  d = f3(gshfl(g, d.x, 0), gshfl(g, d.y, 0), gshfl(g, d.z, 0));
+  Cnt cnt;
+  unsigned comp = 0;
+  Surface s;
+  coop_composite(g, insts, n_inst, cam.eye, d, P, st, status, cnt, s, comp);
+  if (g.c != 0) return;
+  const float3 rho = s.Sa + env_lookup(env, d) * s.T;
+  float* gp = gbuf + p;
+  gp[LF_CH_T * NP] = s.T;
+  gp[LF_CH_W * NP] = s.W;
+  gp[LF_CH_DEPTH * NP] = s.depth;
+  gp[(LF_CH_X + 0) * NP] = s.x.x; gp[(LF_CH_X + 1) * NP] = s.x.y; gp[(LF_CH_X + 2) * NP] = s.x.z;
+  gp[(LF_CH_N + 0) * NP] = s.n.x; gp[(LF_CH_N + 1) * NP] = s.n.y; gp[(LF_CH_N + 2) * NP] = s.n.z;
+  gp[(LF_CH_A + 0) * NP] = s.a.x; gp[(LF_CH_A + 1) * NP] = s.a.y; gp[(LF_CH_A + 2) * NP] = s.a.z;
+  gp[LF_CH_M * NP] = s.m;
+  gp[LF_CH_R * NP] = s.r;
+  gp[(LF_CH_RHO + 0) * NP] = rho.x; gp[(LF_CH_RHO + 1) * NP] = rho.y; gp[(LF_CH_RHO + 2) * NP] = rho.z;
+  gp[LF_CH_NLEN * NP] = s.nlen;
+  gp[LF_CH_HITS * NP] = (float)s.hits;
+  gp[LF_CH_TSTOP * NP] = key_t(s.stop_key);
+  gp[LF_CH_IDSTOP * NP] = s.hits ? (float)(int)(s.stop_key & 0xffffffull) : -1.0f;
+  gp[(LF_CH_DIR + 0) * NP] = d.x; gp[(LF_CH_DIR + 1) * NP] = d.y; gp[(LF_CH_DIR + 2) * NP] = d.z;
+  gp[LF_CH_STOPKEY_LO * NP] = __uint_as_float((unsigned)(s.stop_key & 0xffffffffull));
+  if (Cnt::on && counters) {  // slot 0 of the per-kernel counters: primary rays
+    atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
+    atomicAdd(counters + 1, (unsigned long long)cnt.tests);
+    atomicAdd(counters + 2, (unsigned long long)comp);
+    atomicAdd(counters + 3, 1ull);
+  }
+}
+
 template <class Cnt>
 __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
   extern __shared__ __align__(16) int s_cstack[];
@@ -20,39 +60,39 @@ __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam
   const CStack st = ray_smem(reinterpret_cast<unsigned char*>(s_cstack), RGROUPS, gid);
   const int x = blockIdx.x * TILE_W + gid % TILE_W, y = blockIdx.y * TILE_H + gid / TILE_W;
   if (x >= cam.W || y >= cam.H) return;  // uniform over the group
-  const int p = y * cam.W + x;
-  const size_t P = (size_t)cam.W * cam.H;
-  float3 d = f3(0.f, 0.f, 0.f);
-  if (g.c == 0) d = camera_dir(cam, p);  // FP64 once per pixel
-  d = f3(gshfl(g, d.x, 0), gshfl(g, d.y, 0), gshfl(g, d.z, 0));
-  Cnt cnt;
-  unsigned comp = 0;
-  Surface s;
-  coop_composite(g, a.insts, a.n_inst, cam.eye, d, a.P, st, a.status, cnt, s, comp);
-  if (g.c != 0) return;
-  const float3 rho = s.Sa + env_lookup(a.env, d) * s.T;
-  float* gp = gbuf + p;
-  gp[LF_CH_T * P] = s.T;
-  gp[LF_CH_W * P] = s.W;
-  gp[LF_CH_DEPTH * P] = s.depth;
-  gp[(LF_CH_X + 0) * P] = s.x.x; gp[(LF_CH_X + 1) * P] = s.x.y; gp[(LF_CH_X + 2) * P] = s.x.z;
-  gp[(LF_CH_N + 0) * P] = s.n.x; gp[(LF_CH_N + 1) * P] = s.n.y; gp[(LF_CH_N + 2) * P] = s.n.z;
-  gp[(LF_CH_A + 0) * P] = s.a.x; gp[(LF_CH_A + 1) * P] = s.a.y; gp[(LF_CH_A + 2) * P] = s.a.z;
-  gp[LF_CH_M * P] = s.m;
-  gp[LF_CH_R * P] = s.r;
-  gp[(LF_CH_RHO + 0) * P] = rho.x; gp[(LF_CH_RHO + 1) * P] = rho.y; gp[(LF_CH_RHO + 2) * P] = rho.z;
-  gp[LF_CH_NLEN * P] = s.nlen;
-  gp[LF_CH_HITS * P] = (float)s.hits;
-  gp[LF_CH_TSTOP * P] = key_t(s.stop_key);
-  gp[LF_CH_IDSTOP * P] = s.hits ? (float)(int)(s.stop_key & 0xffffffull) : -1.0f;
-  gp[(LF_CH_DIR + 0) * P] = d.x; gp[(LF_CH_DIR + 1) * P] = d.y; gp[(LF_CH_DIR + 2) * P] = d.z;
-  gp[LF_CH_STOPKEY_LO * P] = __uint_as_float((unsigned)(s.stop_key & 0xffffffffull));
-  if (Cnt::on && a.counters) {  // slot 0 of the per-kernel counters: primary rays
-    atomicAdd(a.counters + 0, (unsigned long long)cnt.nodes);
-    atomicAdd(a.counters + 1, (unsigned long long)cnt.tests);
-    atomicAdd(a.counters + 2, (unsigned long long)comp);
-    atomicAdd(a.counters + 3, 1ull);
+  trace_pixel<Cnt>(g, st, a.insts, a.n_inst, a.P, a.env, a.status, a.counters, cam, gbuf, x, y);
+}
+
+// Primary rays of several images in one launch (the served loop's launch
+// group): block b belongs to the job whose tile range holds it.
+__global__ void __launch_bounds__(TB, 8) k_trace_primary_batch(PrimaryBatch B, DevParams P, int* status) {
+  extern __shared__ __align__(16) int s_cstack[];
+  const Grp g = make_grp();
+  const int gid = threadIdx.x / WIDE;
+  const CStack st = ray_smem(reinterpret_cast<unsigned char*>(s_cstack), RGROUPS, gid);
+  int lo = 0, hi = B.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.jobs[mid].tile0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
+  const PrimaryJob& J = B.jobs[lo];
+  const int tile = (int)blockIdx.x - J.tile0;
+  const int tiles_x = (J.cam.W + TILE_W - 1) / TILE_W;
+  const int x = (tile % tiles_x) * TILE_W + gid % TILE_W, y = (tile / tiles_x) * TILE_H + gid / TILE_W;
+  if (x >= J.cam.W || y >= J.cam.H) return;  // uniform over the group
+  trace_pixel<NoCounters>(g, st, J.insts, J.n_inst, P, J.env, status, nullptr, J.cam, J.gbuf, x, y);
+}
+
+int primary_tiles(int W, int H) { return ((W + TILE_W - 1) / TILE_W) * ((H + TILE_H - 1) / TILE_H); }
+
+cudaError_t launch_trace_primary_batch(PrimaryBatch& B, const DevParams& P, int* status, cudaStream_t st) {
+  int tiles = 0;
+  for (int q = 0; q < B.n_jobs; ++q) {
+    B.jobs[q].tile0 = tiles;
+    tiles += primary_tiles(B.jobs[q].cam.W, B.jobs[q].cam.H);
+  }
+  if (tiles > 0) k_trace_primary_batch<<<tiles, TB, RSTACK_SMEM, st>>>(B, P, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trace_primary(const TraceArgs& a, const CamDev& cam, float* gbuf, cudaStream_t st) {

@@ -323,11 +323,25 @@ lf_status launch_group(lf_serve* s, Group* g) {
   B.n_jobs = (int)g->jobs.size();
   B.n_items = 0;
   B.n_pix_total = 0;
+  // the primary rays of every request of the group in one launch
+  PrimaryBatch PB;
+  PB.n_jobs = (int)g->jobs.size();
+  static_assert(MAX_PRIMARY_JOBS >= MAX_JOBS, "a launch group must fit one primary batch");
+  for (size_t q = 0; q < g->jobs.size(); ++q) {
+    Job* j = g->jobs[q];
+    const TraceArgs a = job_trace_args(s, j);
+    PrimaryJob& PJ = PB.jobs[q];
+    PJ.insts = a.insts;
+    PJ.n_inst = a.n_inst;
+    PJ.env = a.env;
+    PJ.cam = lf_ctx_cam(j->req.cam);
+    PJ.gbuf = j->gbuf;
+  }
+  if (launch_trace_primary_batch(PB, c->dp, c->status_dev, g->stream) != cudaSuccess) return LF_ERR_CUDA;
   for (size_t q = 0; q < g->jobs.size(); ++q) {
     Job* j = g->jobs[q];
     const lf_camera& cam = j->req.cam;
     const TraceArgs a = job_trace_args(s, j);
-    if (launch_trace_primary(a, lf_ctx_cam(cam), j->gbuf, g->stream) != cudaSuccess) return LF_ERR_CUDA;
     ShadeJob& J = B.jobs[q];
     J.insts = j->insts;
     J.n_inst = c->n_obj;

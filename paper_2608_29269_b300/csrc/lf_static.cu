@@ -23,12 +23,17 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_shade_scratch[LF_STATIC_SCRATCH_BYTES];
 
-// Device address of g_shade_scratch, looked up once per device (with that
-// device current) on the first call made there.
+// Device address of g_shade_scratch per device.  The host-side name of the
+// array is only a stand-in, so the address is looked up with
+// cudaGetSymbolAddress while the context's device is current, on the first
+// call after a context was created on that device (lf_create drops the
+// cached address: a cudaDeviceReset in between would leave it stale, and a
+// reset also ends every context made before it).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
+// `device` is the calling thread's current device.
 cudaError_t scratch_address(int device, void** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
@@ -54,6 +59,11 @@ size_t max_samples() {
 
 }  // namespace
 
+void lf_static_scratch_forget(int device) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (device >= 0 && device < kMaxDevices) g_addr[device] = nullptr;
+}
+
 extern "C" {
 
 lf_status lf_shade_bounce_static(lf_ctx* c, const lf_camera* cam, const float* gbuf, int env_id, int spp,
@@ -74,10 +84,19 @@ lf_status lf_shade_bounce_static(lf_ctx* c, const lf_camera* cam, const float* g
     c->err = msg;
     return LF_ERR_INVALID;
   }
+  // The array's address is per device: the kernels run on the context's
+  // device, so that device must be the current one (as for every call).
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
+  if (e == cudaSuccess && device != c->device) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "lf_shade_bounce_static: current device %d is not the context's device %d", device,
+             c->device);
+    c->err = msg;
+    return LF_ERR_INVALID;
+  }
   void* scratch = nullptr;
-  if (e == cudaSuccess) e = scratch_address(device, &scratch);
+  if (e == cudaSuccess) e = scratch_address(c->device, &scratch);
   if (e != cudaSuccess) {
     c->err = std::string("lf_shade_bounce_static: scratch address: ") + cudaGetErrorString(e);
     return LF_ERR_CUDA;

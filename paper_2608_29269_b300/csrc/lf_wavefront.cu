@@ -523,6 +523,26 @@ __global__ void __launch_bounds__(WB) k_wf_combine_adjoint(ShadeBatch B, DevPara
   sg[8 * NP + p] = gT;
 }
 
+// Per-sample terms c_s of the combine (one thread per work item), for
+// inspection: out[3 i + c] for item i; zero where the pixel has no surface
+// facing the camera.
+__global__ void __launch_bounds__(WB) k_wf_terms(ShadeBatch B, DevParams P, SampleBuf S, float* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < B.n_items;
+       i += (long long)gridDim.x * blockDim.x) {
+    const ShadeJob& J = B.jobs[job_of_item(B, i)];
+    const int p = (int)((i - J.item0) / J.spp);
+    const PixRec q = pix_record(J, p);
+    float3 c = f3(0.f, 0.f, 0.f);
+    if (q.hits > 0 && dot3(q.n, -q.d) > 0.0f) {
+      SampleTerms Et;
+      c = sample_value(S, i, q, J.env, P, Et);
+    }
+    out[3 * i + 0] = c.x;
+    out[3 * i + 1] = c.y;
+    out[3 * i + 2] = c.z;
+  }
+}
+
 __global__ void k_wf_count(const int* counts, unsigned long long* ray_count) {
   if (threadIdx.x == 0 && ray_count)
     atomicAdd(ray_count, (unsigned long long)counts[0] + (unsigned long long)counts[1] + (unsigned long long)counts[2]);
@@ -610,6 +630,12 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
 cudaError_t launch_shade_combine(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, cudaStream_t st) {
   const long long threads = (long long)B.n_pix_total * CG;
   if (B.n_pix_total > 0) k_wf_combine<<<(unsigned)((threads + WB - 1) / WB), WB, 0, st>>>(B, P, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade_terms(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, float* out, int sms,
+                               cudaStream_t st) {
+  if (B.n_items > 0) k_wf_terms<<<wf_grid(B.n_items, sms), WB, 0, st>>>(B, P, S, out);
   return cudaGetLastError();
 }
 

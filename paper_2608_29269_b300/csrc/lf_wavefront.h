@@ -59,6 +59,8 @@ cudaError_t launch_shade_wavefront(const ShadeBatch& B, const DevParams& P, cons
                                    unsigned long long* ray_count, unsigned long long* counters, int sms,
                                    cudaStream_t st, cudaEvent_t* ev = nullptr);
 cudaError_t launch_shade_combine(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, cudaStream_t st);
+cudaError_t launch_shade_terms(const ShadeBatch& B, const DevParams& P, const SampleBuf& S, float* out, int sms,
+                               cudaStream_t st);
 cudaError_t launch_shade_combine_adjoint(const ShadeBatch& B, const DevParams& P, const SampleBuf& S,
                                          const float* dL_drgb, float* sg, float* d_env, cudaStream_t st);
 

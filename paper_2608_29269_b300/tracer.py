@@ -224,6 +224,15 @@ class Tracer:
                                             samples.numel() * samples.element_size()))
         return out
 
+    def sample_terms(self, cam, gbuf: torch.Tensor, env_id: int, spp: int, samples: torch.Tensor) -> torch.Tensor:
+        """(width * height, spp, 3) per-sample terms c_s of the shade() call that filled `samples`."""
+        out = torch.empty((cam.width * cam.height, spp, 3), device="cuda", dtype=torch.float32)
+        c = camera_struct(cam)
+        self.check(self.lib.lf_shade_sample_terms(self.ctx, C.byref(c), _ptr(gbuf), int(env_id), int(spp),
+                                                  _ptr(samples), samples.numel() * samples.element_size(),
+                                                  _ptr(out)))
+        return out
+
     def scratch_bytes(self, cam, spp: int) -> int:
         return int(self.lib.lf_backward_scratch_bytes(cam.width, cam.height, int(spp)))
 
