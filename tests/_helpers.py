@@ -22,6 +22,19 @@ OCH = {n: i for i, n in enumerate(oracle.CHANNELS)}
 #  surfel scale.
 FLAG = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6)
 FLAG_SHADE = dict(support=4e-5, alpha=4e-5, tmin=1e-3, tie=1e-8, stop=2e-5, cos=2e-6, frame=2e-6)
+# Per shading sample: a shading ray starts from the FP32 G-buffer position
+# (within about one rounding of the FP64 composite, ~2.4e-7 in a room of
+# half-size 2) along an FP32 direction (~6e-8), so its support, opacity and
+# depth-order decisions are flagged when a ray shift of SHIFT (the oracle's
+# *_shift margins, a direction change counted as (1 + t) times an origin
+# shift) flips them, and by the relative margins of the primary ray for the
+# FP32 storage of the records.  Also: a uniform within FP32 rounding (2^-24)
+# of an environment CDF entry (FP32 tables may select the neighbouring
+# texel), a continuation direction within 1e-6 rad of a texel edge of the
+# piecewise-constant environment pdf (FP32 directions carry ~1e-7 rad).
+SHIFT = 2.5e-7
+FLAG_SAMPLE = dict(support=1e-6, alpha=1e-6, tmin=1e-3, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6, cdf=6e-8,
+                   ptex=1e-6, support_shift=SHIFT, alpha_shift=SHIFT, tie_shift=SHIFT)
 
 
 def flagged(margins, kinds=FLAG, margins_shade=None, kinds_shade=FLAG_SHADE):
@@ -68,3 +81,73 @@ def compare_gbuf(g_gpu, o_ch, ok, tol=1e-4):
         d = np.abs(g_gpu[ok, gi] - o_ch[ok, OCH[oname]])
         out[name] = float(d.max()) if d.size else 0.0
     return out
+
+
+def sample_flags(o, kinds=FLAG, kinds_sample=FLAG_SAMPLE):
+    """(n, spp) bool: shading sample s of pixel i is flagged when the pixel's
+    primary ray is flagged or one of the sample's own decisions (or the
+    pixel-level shading decisions folded into every sample) is."""
+    fp = flagged(o["margins"], kinds)
+    ms = o["margins_sample"]
+    f = np.zeros(ms.shape[:2], bool)
+    for k, thr in kinds_sample.items():
+        f |= ms[:, :, MG[k]] < thr
+    return f | fp[:, None]
+
+
+def compare_samples(o, terms_gpu, T_gpu, rgb_gpu, spp, tol=1e-4, kinds_sample=FLAG_SAMPLE):
+    """Per-sample comparison of the shading estimator (Eq. 11).
+
+    Each sample's share of its pixel, (1 - T) / spp * c_s, is compared with
+    the oracle's on every unflagged sample:
+        |d| <= tol * max(1, |share|)       (unclamped, HDR)
+    and each pixel with the flagged samples removed on both sides,
+        L' = L - (1 - T) / spp * sum_{s flagged} c_s,
+    on every pixel whose primary ray is not flagged:
+        |dL'| <= tol * max(1, |L'|)  and  |clip(L', 0, 1) - ...| <= tol.
+    terms_gpu: (n, spp, 3) GPU terms c_s; T_gpu: (n,) GPU transmittance;
+    rgb_gpu: (n, 3) GPU pixel values.  Returns a dict of the measured
+    fractions and worst errors (asserts nothing)."""
+    fs = sample_flags(o, kinds_sample=kinds_sample)
+    fp = flagged(o["margins"])
+    k = (1.0 - o["ch"][:, OCH["T"]]) / spp
+    kg = (1.0 - np.asarray(T_gpu, np.float64)) / spp
+    so = k[:, None, None] * o["samples"]
+    sg = kg[:, None, None] * np.asarray(terms_gpu, np.float64)
+    rel = np.abs(sg - so) / np.maximum(1.0, np.abs(so))
+    ok = ~fs
+    Lo = o["rgb"] - (so * fs[:, :, None]).sum(1)
+    Lg = np.asarray(rgb_gpu, np.float64) - (sg * fs[:, :, None]).sum(1)
+    pok = ~fp
+    prel = (np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo)))[pok]
+    pcl = np.abs(np.clip(Lg, 0, 1) - np.clip(Lo, 0, 1))[pok]
+    return dict(flagged_samples=float(fs.mean()), n_samples=int(fs.size), flagged_pixels=float(fp.mean()),
+                n_pixels=int(len(fp)),
+                sample_rel=float(rel[ok].max()) if ok.any() else 0.0,
+                failing_samples=int(((rel > tol) & ok[:, :, None]).any(2).sum()),
+                pixel_rel=float(prel.max()) if prel.size else 0.0,
+                pixel_clamped=float(pcl.max()) if pcl.size else 0.0)
+
+
+def gpu_shaded(tr, cam, env_id, spp, seed, pix):
+    """Trace and shade one frame on the GPU; returns (G-buffer tensor, sample
+    buffer, G-buffer (n, C), per-sample terms (n, spp, 3), rgb (n, 3)) with
+    the last three at the flat pixel indices `pix`."""
+    import torch
+    g = tr.trace_primary(cam, env_id)
+    samples = tr.alloc_samples(cam, spp)
+    rgb = tr.shade(cam, g, env_id, spp=spp, seed=seed, samples=samples)
+    terms = tr.sample_terms(cam, g, env_id, spp, samples)
+    tr.sync()
+    pt = torch.as_tensor(np.asarray(pix, np.int64), device="cuda")
+    return g, samples, gbuf_at(g, pix), terms[pt].cpu().numpy(), rgb.reshape(-1, 3)[pt].cpu().numpy()
+
+
+def assert_shading(r, tol=1e-4, max_flagged=0.01):
+    """The per-sample comparison's bounds: flagged fractions under
+    `max_flagged` (at least one sample or pixel may be flagged in a tiny
+    image), no unflagged sample or pixel beyond `tol`."""
+    assert r["flagged_pixels"] * r["n_pixels"] <= max(1.0, max_flagged * r["n_pixels"]), r
+    assert r["flagged_samples"] * r["n_samples"] <= max(1.0, max_flagged * r["n_samples"]), r
+    assert r["failing_samples"] == 0 and r["sample_rel"] <= tol, r
+    assert r["pixel_rel"] <= tol and r["pixel_clamped"] <= tol, r

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from synthetic import scenes as S
-from tests._helpers import flagged, gpu_tracer
+from tests._helpers import sample_flags, flagged, gpu_tracer
 
 pytestmark = pytest.mark.gpu
 
@@ -129,7 +129,7 @@ def test_cross_state_gradient_parity():
     for (R, t), seed in zip(states, seeds):
         ws = oracle.assemble_state(sc, R, t)
         o = oracle.render(ws, cam, env, pix, spp=spp, seed=seed)
-        ok = ~flagged(o["margins"], dict(FLAG_GRAD), margins_shade=o["margins_shade"])
+        ok = ~(flagged(o["margins"], FLAG_GRAD) | sample_flags(o).any(1))
         g_rgb = rng.normal(size=(cam.n_pixels, 3)) * ok[:, None]
         d_s, d_e = oracle.grad(ws, cam, env, pix, spp, seed, g_rgb, np.zeros((cam.n_pixels, 17)))
         d_ref += oracle.state_pullback(sc.object_offsets, R, d_s)

@@ -5,8 +5,10 @@ plugin that may not call cudaMalloc, a render loop that must not allocate
 after start-up) cannot hand lf_shade_bounce its per-sample scratch buffer;
 this entry point uses a fixed array inside the library instead.  The test
 calls it through the C ABI twice in a row and compares each image with the
-existing entry point's on the same inputs, and checks that a request larger
-than the array is refused.  This file is collected last on purpose.
+existing entry point's on the same inputs, checks that those two calls left
+the device's free memory and torch's allocation unchanged (nothing was
+allocated), and that a request larger than the array is refused.  This file
+is collected last on purpose.
 """
 import ctypes as C
 
@@ -36,12 +38,26 @@ def test_static_scratch_shading_matches_caller_scratch_twice():
     ref = tr.shade(cam, g, 0, spp=spp, seed=99)
     tr.sync()
     c = camera_struct(cam)
-    for _ in range(2):
-        out = torch.full_like(ref, float("nan"))
+
+    def call(out):
         st = lib.lf_shade_bounce_static(tr.ctx, C.byref(c), C.c_void_p(g.data_ptr()), 0, spp, C.c_uint64(99),
                                         C.c_void_p(out.data_ptr()), None)
         assert st == N.LF_OK, lib.lf_last_error(tr.ctx)
+
+    # outputs are allocated up front; a first call outside the measured span
+    outs = [torch.full_like(ref, float("nan")) for _ in range(2)]
+    call(torch.empty_like(ref))
+    tr.sync()
+    torch.cuda.synchronize()
+    free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for out in outs:
+        call(out)
         tr.sync()
+    torch.cuda.synchronize()
+    free1, torch1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    assert free1 == free0, (free0, free1)
+    assert torch1 == torch0, (torch0, torch1)
+    for out in outs:
         diff = (out - ref).abs().max().item()
         assert diff <= TOL, diff
     # a request beyond the array's capacity is refused before anything runs
