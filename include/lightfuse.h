@@ -209,8 +209,10 @@ lf_status lf_state_pullback(lf_ctx* ctx, const float* R, const float* d_world, f
  * texels, row 0 looking up (+y), column 0 at phi = 0 of the y-up
  * equirectangular mapping theta = acos(w_y), phi = atan2(w_x, -w_z) + pi.
  * Builds the importance-sampling tables (texel weight = (Rec.709 luminance
- * + 1e-6) * sin(theta at the row centre), FP64 sums, FP32 tables).  The
- * texels are read in place at render time.
+ * + 1e-6) * sin(theta at the row centre), FP64 sums, FP32 tables plus the
+ * FP32 residuals of the FP64 CDF values, so a sample's position inside its
+ * texel carries the FP64 table's accuracy).  The texels are read in place
+ * at render time.
  */
 lf_status lf_env_set(lf_ctx* ctx, int env_id, const float* rgb_dev, int H, int W);
 
@@ -253,8 +255,9 @@ lf_status lf_shade_bounce(lf_ctx* ctx, const lf_camera* cam, const float* gbuf_d
  * which every GPU that loads the library holds until the process exits.
  * Same arguments and results as lf_shade_bounce without the sample buffer.
  *   - width * height * spp must be at most (LF_STATIC_SCRATCH_BYTES - 256) /
- *     128 = 524286 samples; larger requests return LF_ERR_INVALID with a
- *     message and enqueue nothing.
+ *     140 = 479,347 samples (lf_shade_scratch_bytes gives the bytes a count
+ *     needs); larger requests return LF_ERR_INVALID with a message and
+ *     enqueue nothing.
  *   - The calling thread's current device must be the context's device
  *     (LF_ERR_INVALID otherwise).  The first call after a context was
  *     created on a device looks up the array's device address there (with

@@ -144,6 +144,8 @@ TraceArgs lf_ctx_trace_args(lf_ctx* c, int env_id) {
   a.env.cdf_row = e.tables + e.H;
   a.env.pmf_col = e.tables + 2 * e.H;
   a.env.cdf_col = e.tables + 2 * e.H + (size_t)e.H * e.W;
+  a.env.cdf_row_lo = e.tables + 2 * e.H + 2 * (size_t)e.H * e.W;
+  a.env.cdf_col_lo = e.tables + 3 * e.H + 2 * (size_t)e.H * e.W;
   a.env.H = e.H;
   a.env.W = e.W;
   a.status = c->status_dev;
@@ -435,7 +437,7 @@ lf_status lf_env_set(lf_ctx* c, int id, const float* rgb, int H, int W) {
   if (id < 0 || id >= LF_MAX_ENVS || !rgb || H <= 0 || W <= 0 || (long long)H * W > (1LL << 26))
     return fail(c, LF_ERR_INVALID, "bad environment map");
   EnvSlot& e = c->env[id];
-  const size_t need = 2 * (size_t)H + 2 * (size_t)H * W;
+  const size_t need = 3 * (size_t)H + 3 * (size_t)H * W;  // + the CDFs' low parts
   if (need > e.cap || H > e.cap_h) {
     dev_free(e.tables); dev_free(e.rowsum); dev_free(e.sin_row);
     cudaError_t err = dev_alloc(&e.tables, need);
@@ -457,7 +459,8 @@ lf_status lf_env_set(lf_ctx* c, int id, const float* rgb, int H, int W) {
   e.H = H;
   e.W = W;
   LF_CUDA(c, launch_env_tables(rgb, e.sin_row, H, W, e.rowsum, e.tables, e.tables + H, e.tables + 2 * H,
-                               e.tables + 2 * H + (size_t)H * W, c->stream));
+                               e.tables + 2 * H + (size_t)H * W, e.tables + 2 * H + 2 * (size_t)H * W,
+                               e.tables + 3 * H + 2 * (size_t)H * W, c->stream));
   // the host sin table must outlive the asynchronous copy
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   e.set = true;

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev 
       rc = load_rec(I.geo, I.n_leaves, l);
       mt = __ldg(I.mat + l);
       float tl;
-      hit_precise(rc, o, d, Pm, t, tl, alpha);
+      hit_precise(rc, o, f3(0.f, 0.f, 0.f), d, Pm, t, tl, alpha);
       nj = record_normal(rc, d);
       const float3 xj = o + d * t;
       gw = gW + dot3(gSx, xj) + gSt * t + dot3(gSn, nj) + gSa.x * mt.x + gSa.y * mt.y + gSa.z * mt.z +

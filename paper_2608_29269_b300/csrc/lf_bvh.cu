@@ -562,9 +562,19 @@ __device__ __forceinline__ double texel_weight(const float* t, double st) {
   return __dmul_rn(lum, st);
 }
 
+// The FP64 CDF value v goes out as the FP32 pair (hi, lo): hi = v rounded,
+// lo = v - hi rounded, so a sampler can place a uniform inside its texel to
+// FP64 accuracy while it searches the FP32 table.
+__device__ __forceinline__ void put_cdf(float* hi, float* lo, size_t i, double v) {
+  const float h = (float)v;
+  hi[i] = h;
+  lo[i] = (float)__dsub_rn(v, (double)h);
+}
+
 __global__ void __launch_bounds__(ENV_T) k_env_rows(const float* __restrict__ rgb, const double* __restrict__ sin_row,
                                                     int H, int W, double* __restrict__ rowsum,
-                                                    float* __restrict__ pmf_col, float* __restrict__ cdf_col) {
+                                                    float* __restrict__ pmf_col, float* __restrict__ cdf_col,
+                                                    float* __restrict__ cdf_col_lo) {
   __shared__ double s_w[ENV_CH], s_p[ENV_CH];
   __shared__ double s_acc;
   const int r = blockIdx.x;
@@ -602,13 +612,14 @@ __global__ void __launch_bounds__(ENV_T) k_env_rows(const float* __restrict__ rg
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += ENV_T) {
       pmf_col[(size_t)r * W + c0 + c] = (float)__ddiv_rn(s_w[c], acc);
-      cdf_col[(size_t)r * W + c0 + c] = (float)__ddiv_rn(s_p[c], acc);
+      put_cdf(cdf_col, cdf_col_lo, (size_t)r * W + c0 + c, __ddiv_rn(s_p[c], acc));
     }
   }
 }
 
 __global__ void __launch_bounds__(ENV_T) k_env_marginal(const double* __restrict__ rowsum, int H,
-                                                        float* __restrict__ pmf_row, float* __restrict__ cdf_row) {
+                                                        float* __restrict__ pmf_row, float* __restrict__ cdf_row,
+                                                        float* __restrict__ cdf_row_lo) {
   __shared__ double s_pre[ENV_CH];
   __shared__ double s_total;
   if (threadIdx.x == 0) {
@@ -629,7 +640,7 @@ __global__ void __launch_bounds__(ENV_T) k_env_marginal(const double* __restrict
     const double total = s_total;
     for (int r = threadIdx.x; r < n; r += ENV_T) {
       pmf_row[r0 + r] = (float)__ddiv_rn(rowsum[r0 + r], total);
-      cdf_row[r0 + r] = (float)__ddiv_rn(s_pre[r], total);
+      put_cdf(cdf_row, cdf_row_lo, r0 + r, __ddiv_rn(s_pre[r], total));
     }
   }
 }
@@ -722,9 +733,10 @@ cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int
 }
 
 cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, int W, double* rowsum, float* pmf_row,
-                              float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st) {
-  k_env_rows<<<H, ENV_T, 0, st>>>(rgb, sin_row, H, W, rowsum, pmf_col, cdf_col);
-  k_env_marginal<<<1, ENV_T, 0, st>>>(rowsum, H, pmf_row, cdf_row);
+                              float* cdf_row, float* pmf_col, float* cdf_col, float* cdf_row_lo, float* cdf_col_lo,
+                              cudaStream_t st) {
+  k_env_rows<<<H, ENV_T, 0, st>>>(rgb, sin_row, H, W, rowsum, pmf_col, cdf_col, cdf_col_lo);
+  k_env_marginal<<<1, ENV_T, 0, st>>>(rowsum, H, pmf_row, cdf_row, cdf_row_lo);
   return cudaGetLastError();
 }
 

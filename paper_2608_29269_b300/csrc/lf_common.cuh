@@ -82,6 +82,8 @@ struct EnvDev {
   const float* cdf_row;
   const float* pmf_col;
   const float* cdf_col;
+  const float* cdf_row_lo;  // FP64 CDF minus its FP32 rounding
+  const float* cdf_col_lo;
   int H, W;
 };
 
@@ -317,13 +319,14 @@ __device__ __forceinline__ bool hit_quick(const Rec& r, const float3 o, const fl
   return fmaf(u, u, v * v) <= 1.001f * P.support_r2;
 }
 
-__device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const float3 d, const DevParams& P,
-                                            float& t, float& tl, float& alpha) {
+__device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const float3 olo, const float3 d,
+                                            const DevParams& P, float& t, float& tl, float& alpha) {
   const float3 a = rec_a(r), b = rec_b(r), nh = rec_n(r);
   float3 ph, pl;
   two_sum(r.g0.x, -o.x, ph.x, pl.x);
   two_sum(r.g0.y, -o.y, ph.y, pl.y);
   two_sum(r.g0.z, -o.z, ph.z, pl.z);
+  pl = f3(__fsub_rn(pl.x, olo.x), __fsub_rn(pl.y, olo.y), __fsub_rn(pl.z, olo.z));
   float nhi, nlo, dhi, dlo;
   dot2(ph, pl, nh, nhi, nlo);
   dot2(d, f3(0.f, 0.f, 0.f), nh, dhi, dlo);
@@ -348,13 +351,13 @@ __device__ __forceinline__ bool hit_precise(const Rec& r, const float3 o, const 
 
 // Full test of record l: the quick test on its first three quads, then the
 // fourth quad and the precise test for a candidate that passes.
-__device__ __forceinline__ bool hit_surfel(const float4* geo, int n, int l, const float3 o, const float3 d,
-                                           const DevParams& P, Rec& r, float& t32, float& t, float& tl,
-                                           float& alpha) {
+__device__ __forceinline__ bool hit_surfel(const float4* geo, int n, int l, const float3 o, const float3 olo,
+                                           const float3 d, const DevParams& P, Rec& r, float& t32, float& t,
+                                           float& tl, float& alpha) {
   load_rec3(geo, n, l, r);
   if (!hit_quick(r, o, d, P, t32)) return false;
   load_rec_tail(geo, n, l, r);
-  return hit_precise(r, o, d, P, t, tl, alpha);
+  return hit_precise(r, o, olo, d, P, t, tl, alpha);
 }
 
 // 64-bit sort key of a hit: FP32 depth bits | low depth part quantised to
@@ -441,19 +444,32 @@ __device__ __forceinline__ float env_pdf(const EnvDev& e, float3 w) {
          (2.0f * PI_F * PI_F * st);
 }
 
+// Position of uniform u inside the texel [lo, hi) of a CDF given as
+// double-float pairs (h, l): u - lo and hi - lo are formed from the pairs,
+// so fr carries the FP64 table's accuracy, not its FP32 rounding (which is a
+// sizeable fraction of a narrow texel).
+__device__ __forceinline__ float in_texel(float u, float loh, float lol, float hih, float hil) {
+  const float num = __fsub_rn(__fsub_rn(u, loh), lol);
+  const float den = __fadd_rn(__fsub_rn(hih, loh), __fsub_rn(hil, lol));
+  return fminf(fmaxf(num / den, 0.0f), 1.0f);
+}
+
 __device__ __forceinline__ void env_sample(const EnvDev& e, float u1, float u2, float3& w, float& pdf) {
   int r = first_greater(e.cdf_row, e.H, u1);
   float lo = r > 0 ? __ldg(e.cdf_row + r - 1) : 0.0f, hi = __ldg(e.cdf_row + r);
-  float fr = fminf(fmaxf((u1 - lo) / (hi - lo), 0.0f), 1.0f);
+  float lol = r > 0 ? __ldg(e.cdf_row_lo + r - 1) : 0.0f, hil = __ldg(e.cdf_row_lo + r);
+  float fr = in_texel(u1, lo, lol, hi, hil);
   const float* row = e.cdf_col + r * e.W;
+  const float* rowl = e.cdf_col_lo + r * e.W;
   int c = first_greater(row, e.W, u2);
   float clo = c > 0 ? __ldg(row + c - 1) : 0.0f, chi = __ldg(row + c);
-  float fc = fminf(fmaxf((u2 - clo) / (chi - clo), 0.0f), 1.0f);
-  float th = PI_F * ((float)r + fr) / (float)e.H;
-  float ph = 2.0f * PI_F * ((float)c + fc) / (float)e.W - PI_F;
+  float clol = c > 0 ? __ldg(rowl + c - 1) : 0.0f, chil = __ldg(rowl + c);
+  float fc = in_texel(u2, clo, clol, chi, chil);
+  // theta = pi (r + fr) / H, phi - pi = pi (2 (c + fc) / W - 1): sincospif
+  // takes the angles in units of pi, so no FP32 multiple of pi is formed
   float st, ct, sp, cp;
-  sincosf(th, &st, &ct);
-  sincosf(ph, &sp, &cp);
+  sincospif(((float)r + fr) / (float)e.H, &st, &ct);
+  sincospif(2.0f * ((float)c + fc) / (float)e.W - 1.0f, &sp, &cp);
   w = f3(st * sp, ct, -st * cp);
   pdf = __ldg(e.pmf_row + r) * __ldg(e.pmf_col + r * e.W + c) * ((float)e.H * (float)e.W) /
         (2.0f * PI_F * PI_F * fmaxf(st, 1e-12f));
@@ -548,23 +564,35 @@ __device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
 // cos^2 theta_h = (1 - u1) / (1 + (a2 - 1) u1), evaluated as
 // (1 - u1) / ((1 - u1) + a2 u1) and sin^2 as a2 u1 / (same), which keeps the
 // digits of both for a glossy lobe (small a2) at either end of u1 (1 - u1 is
-// exact for the 24-bit uniforms).
+// exact for the 24-bit uniforms).  The frame, the half vector and the
+// reflection are assembled in FP64 from the FP32 inputs and rounded once:
+// in FP32 the reflection 2 (wo.h) h - wo doubles the rounding errors of h
+// (1e-7 rad at the median against 2.4e-8 for the cosine lobe), enough to
+// flip a support decision of a glossy metal's continuation ray.  Once per
+// sample, in the generation kernel (~1 % of a step).
 __device__ __forceinline__ float3 sample_ggx(float3 n, float3 wo, float r, float u1, float u2) {
-  float ag = r * r, a2 = ag * ag;
-  float om = 1.0f - u1, inv = 1.0f / fmaf(a2, u1, om);
-  float ct = sqrtf(om * inv), st = sqrtf(a2 * u1 * inv);
-  float sp, cp;
-  sincosf(2.0f * PI_F * u2, &sp, &cp);
-  float3 b1, b2;
-  onb(n, b1, b2);
-  float3 h = b1 * (st * cp) + b2 * (st * sp) + n * ct;
-  return h * (2.0f * dot3(wo, h)) - wo;
+  const double ag = (double)r * r, a2 = ag * ag;
+  const double om = 1.0 - (double)u1, inv = 1.0 / fma(a2, (double)u1, om);
+  const double ct = sqrt(om * inv), st = sqrt(a2 * (double)u1 * inv);
+  float spf, cpf;
+  sincospif(2.0f * u2, &spf, &cpf);  // angle 2 pi u2 without rounding 2 pi u2
+  const double sp = spf, cp = cpf;
+  const double nx = n.x, ny = n.y, nz = n.z;
+  const double sgn = copysign(1.0, nz);  // as in onb()
+  const double a = -1.0 / (sgn + nz), b = nx * ny * a;
+  const double b1x = 1.0 + sgn * nx * nx * a, b1y = sgn * b, b1z = -sgn * nx;
+  const double b2x = b, b2y = sgn + ny * ny * a, b2z = -ny;
+  const double hx = b1x * (st * cp) + b2x * (st * sp) + nx * ct;
+  const double hy = b1y * (st * cp) + b2y * (st * sp) + ny * ct;
+  const double hz = b1z * (st * cp) + b2z * (st * sp) + nz * ct;
+  const double oh2 = 2.0 * ((double)wo.x * hx + (double)wo.y * hy + (double)wo.z * hz);
+  return f3((float)(hx * oh2 - wo.x), (float)(hy * oh2 - wo.y), (float)(hz * oh2 - wo.z));
 }
 
 // Cosine-weighted hemisphere (Malley's method).
 __device__ __forceinline__ float3 sample_cos(float3 n, float u1, float u2) {
   float rr = sqrtf(u1), sp, cp;
-  sincosf(2.0f * PI_F * u2, &sp, &cp);
+  sincospif(2.0f * u2, &sp, &cp);  // angle 2 pi u2 without rounding 2 pi u2
   float3 b1, b2;
   onb(n, b1, b2);
   return b1 * (rr * cp) + b2 * (rr * sp) + n * sqrtf(fmaxf(0.0f, 1.0f - u1));
@@ -602,13 +630,17 @@ __device__ __forceinline__ float3 camera_dir(const CamDev& c, int p) {
 }
 
 // ------------------------------------------------------------------ traversal
+// The origin is o + olo: shading rays start at a G-buffer position plus an
+// offset along the normal, whose sum a double-float keeps exactly (the
+// precise hit test subtracts olo; the culling tests use o alone).
 struct Ray {
-  float3 o, d, inv, oinv;
+  float3 o, olo, d, inv, oinv;
 };
 
-__device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
+__device__ __forceinline__ Ray make_ray(float3 o, float3 d, float3 olo = f3(0.f, 0.f, 0.f)) {
   Ray r;
   r.o = o;
+  r.olo = olo;
   r.d = d;
   float ix = 1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x));
   float iy = 1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y));

@@ -10,7 +10,8 @@
 struct EnvSlot {
   const float* rgb = nullptr;  // caller-owned texels
   int H = 0, W = 0;
-  float* tables = nullptr;     // pmf_row (H) | cdf_row (H) | pmf_col (H*W) | cdf_col (H*W)
+  float* tables = nullptr;     // pmf_row (H) | cdf_row (H) | pmf_col (H*W) | cdf_col (H*W) |
+                               // cdf_row low parts (H) | cdf_col low parts (H*W)
   double* rowsum = nullptr;
   double* sin_row = nullptr;
   std::vector<double> sin_host;

@@ -80,7 +80,8 @@ cudaError_t launch_rigid(const SceneDev& s, int beg, int end, const Mat34& T, cu
 cudaError_t launch_material(const SceneDev& s, int beg, int end, float3 rgb, int set_rgb, float metal, float rough,
                             cudaStream_t st);
 cudaError_t launch_env_tables(const float* rgb, const double* sin_row, int H, int W, double* rowsum, float* pmf_row,
-                              float* cdf_row, float* pmf_col, float* cdf_col, cudaStream_t st);
+                              float* cdf_row, float* pmf_col, float* cdf_col, float* cdf_row_lo, float* cdf_col_lo,
+                              cudaStream_t st);
 cudaError_t launch_gather_insts(const InstPtrs& src, Inst* dst, int n, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st);
 

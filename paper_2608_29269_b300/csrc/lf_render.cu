@@ -25,7 +25,7 @@ __device__ __forceinline__ void trace_pixel(const Grp& g, const CStack& st, cons
   Cnt cnt;
   unsigned comp = 0;
   Surface s;
-  coop_composite(g, insts, n_inst, cam.eye, d, P, st, status, cnt, s, comp);
+  coop_composite(g, insts, n_inst, cam.eye, f3(0.f, 0.f, 0.f), d, P, st, status, cnt, s, comp);
   if (g.c != 0) return;
   const float3 rho = s.Sa + env_lookup(env, d) * s.T;
   float* gp = gbuf + p;

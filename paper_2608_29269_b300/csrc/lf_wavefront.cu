@@ -78,12 +78,23 @@ __device__ __forceinline__ PixRec pix_record(const ShadeJob& J, int p) {
   return q;
 }
 
-__device__ __forceinline__ float3 pix_origin(const ShadeJob& J, int p, float off) {
+// x + n off as a double-float hi + lo: the sum of two FP32 values is exact
+// as a pair (the product n off carries ~1e-11), so shading rays start
+// exactly at the stored position plus the offset.
+__device__ __forceinline__ float3 offset_origin(float3 x, float3 n, float off, float3& lo) {
+  float3 hi;
+  two_sum(x.x, n.x * off, hi.x, lo.x);
+  two_sum(x.y, n.y * off, hi.y, lo.y);
+  two_sum(x.z, n.z * off, hi.z, lo.z);
+  return hi;
+}
+
+__device__ __forceinline__ float3 pix_origin(const ShadeJob& J, int p, float off, float3& lo) {
   const size_t P = (size_t)J.n_pix;
   const float* g = J.gbuf + p;
   const float3 x = f3(__ldg(g + LF_CH_X * P), __ldg(g + (LF_CH_X + 1) * P), __ldg(g + (LF_CH_X + 2) * P));
   const float3 n = f3(__ldg(g + LF_CH_N * P), __ldg(g + (LF_CH_N + 1) * P), __ldg(g + (LF_CH_N + 2) * P));
-  return x + n * off;
+  return offset_origin(x, n, off, lo);
 }
 
 __device__ __forceinline__ float3 ld3(const float* const* pl, long long i) {
@@ -200,18 +211,22 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     ShadowCoop v;
     v.P = P;
-    float3 o, d;
+    v.insts = J.insts;
+    v.qc = st.qc;
+    v.qn = 0;
+    float3 o, olo, d;
     if (which == 0) {
       const long long loc = item - J.item0;
-      o = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+      o = pix_origin(J, (int)(loc / J.spp), P.ray_offset, olo);
       d = ld3(S.we, item);
     } else {
       o = ld3(S.xs2, item);
+      olo = ld3(S.xs2lo, item);
       d = (e & 1) ? ld3(S.wq1, item) : ld3(S.wq0, item);
     }
     v.V = 1.0f;
     v.stop = false;
-    const Ray ray = make_ray(o, d);
+    const Ray ray = make_ray(o, d, olo);
     coop_traverse(g, J.insts, J.n_inst, ray, v, st, status, cnt);
     if (g.c == 0) {
       if (which == 0) S.Ve[item] = v.V;
@@ -256,14 +271,17 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
     if (!LF_IN_BOUNDS(item, B.n_items, status, "continuation ray item")) continue;
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     const long long loc = item - J.item0;
-    const float3 xs = pix_origin(J, (int)(loc / J.spp), P.ray_offset);
+    float3 xslo;
+    const float3 xs = pix_origin(J, (int)(loc / J.spp), P.ray_offset, xslo);
     const float3 wi = ld3(S.wi, item);
     Surface s2;
-    coop_composite(g, J.insts, J.n_inst, xs, wi, P, st, status, cnt, s2, comp);
+    coop_composite(g, J.insts, J.n_inst, xs, xslo, wi, P, st, status, cnt, s2, comp);
     if (g.c == 0) {
       S.T2[item] = s2.T;
       if (s2.hits > 0) {
-        st3(S.xs2, item, s2.x + s2.n * P.ray_offset);
+        float3 lo;
+        st3(S.xs2, item, offset_origin(s2.x, s2.n, P.ray_offset, lo));
+        st3(S.xs2lo, item, lo);
         st3(rec_n2(S), item, s2.n);
         st3(rec_a2(S), item, s2.a);
         rec_m2(S)[item] = s2.m;
@@ -568,6 +586,7 @@ SampleBuf sample_buf(void* base, long long n_items) {
   S.wb = take(1);
   S.T2 = take(1);
   p = take(3); S.xs2[0] = p; S.xs2[1] = p + ns; S.xs2[2] = p + 2 * ns;
+  p = take(3); S.xs2lo[0] = p; S.xs2lo[1] = p + ns; S.xs2lo[2] = p + 2 * ns;
   p = take(3); S.wq0[0] = p; S.wq0[1] = p + ns; S.wq0[2] = p + 2 * ns;
   p = take(3); S.wq1[0] = p; S.wq1[1] = p + ns; S.wq1[2] = p + 2 * ns;
   p = take(3); S.fk0[0] = p; S.fk0[1] = p + ns; S.fk0[2] = p + 2 * ns;

@@ -5,7 +5,7 @@
 namespace lf {
 
 constexpr int MAX_JOBS = 32;
-constexpr int SAMPLE_PLANES = 28;
+constexpr int SAMPLE_PLANES = 31;
 
 // One image of a shading batch: its scene snapshot (instances), environment,
 // G-buffer (planes of n_pix floats), output and sampling parameters.  Its
@@ -40,7 +40,8 @@ struct SampleBuf {
   float* bc;   // 1 / pdf of the continuation; 0: no continuation ray
   float* wb;   // MIS weight of the escaped continuation
   float* T2;
-  float* xs2[3];
+  float* xs2[3];    // origin of the secondary NEE rays, high part
+  float* xs2lo[3];  // and its low part (double-float)
   float* wq0[3];
   float* wq1[3];
   float* fk0[3];  // f2 cos / pdf * (1 - T2) / 2 of secondary NEE #1; 0: none
