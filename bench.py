@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--ms-size", type=int, default=1024)
     ap.add_argument("--ms-spp", type=int, default=64)
     ap.add_argument("--ms-layouts", type=int, default=8)
+    ap.add_argument("--no-multistate", action="store_true",
+                    help="skip the bounded multi-state relighting object of the default line")
+    ap.add_argument("--ms-default-layouts", type=int, default=2,
+                    help="layouts of the bounded multi-state object (x 3 environments, 1024^2, 64 spp)")
     return ap.parse_args()
 
 
@@ -341,21 +345,27 @@ def run_serve_sweep(args):
 
 
 def run_multistate(args):
+    line = multistate(args.ms_size, args.ms_spp, args.ms_layouts)
+    print(json.dumps(line))
+
+
+def multistate(size, spp, n_layouts, stage_prefix="multi-state"):
     """Multi-state relighting (cross-state supervision, Sec. 3.2): the 1M-surfel
     scene (shell + 12 objects) as one canonical scene, 3 environment states x
-    `--ms-layouts` layouts, each layout moving 1-4 random objects (rotation
+    `n_layouts` layouts, each layout moving 1-4 random objects (rotation
     about +y through the object's centre, x/z shift U[-0.5, 0.5]).  Per
     (environment, layout): the state is assembled from the canonical scene
-    (Eq. 2, every BLAS refit), traced at ms-size^2, shaded at ms-spp,
+    (Eq. 2, every BLAS refit), traced at size^2, shaded at spp,
     differentiated, and its surfel gradient carried back to the canonical
-    parameters.  One warm-up state, then every state timed with CUDA events."""
+    parameters.  One warm-up state, then every state timed with CUDA events.
+    Returns the JSON object of the measurement."""
     import numpy as np
     import torch
     from synthetic import scenes as S
     from paper_2608_29269_b300 import SceneTensors, Tracer
-    stage("multi-state workload")
+    stage(f"{stage_prefix} workload")
     sc = S.scene_c4(0)
-    cam = S.camera_c4(args.ms_size, args.ms_size)
+    cam = S.camera_c4(size, size)
     envs = [S.env_sky_sun(i) for i in range(3)]
     tr = Tracer()
     can = SceneTensors.from_numpy(sc)
@@ -369,14 +379,14 @@ def run_multistate(args):
     rng = np.random.default_rng(7)
     M = sc.n_objects - 1
     layouts = []
-    for _ in range(args.ms_layouts):
+    for _ in range(n_layouts):
         R = np.stack([np.eye(3, dtype=np.float32)] * M)
         t = np.zeros((M, 3), np.float32)
         for o in rng.choice(np.arange(1, M + 1), size=int(rng.integers(1, 5)), replace=False):
             lo, hi = sc.object_offsets[o], sc.object_offsets[o + 1]
             R[o - 1], t[o - 1] = S.rigid_motion(rng, sc.mu[lo:hi].mean(0), max_shift=0.5)
         layouts.append((R, t))
-    spp, P = args.ms_spp, cam.width * cam.height
+    P = cam.width * cam.height
     gbuf = torch.empty((25, cam.height, cam.width), device="cuda")
     rgb = torch.empty((cam.height, cam.width, 3), device="cuda")
     samples = tr.alloc_samples(cam, spp)
@@ -406,10 +416,10 @@ def run_multistate(args):
         rec("backward", 1)
         rec("pullback", 0); tr.state_pullback(R, d_world, d_can); rec("pullback", 1)
 
-    stage("multi-state warm-up")
+    stage(f"{stage_prefix} warm-up")
     run_state(0, 0, None)
     tr.sync()
-    stage("multi-state timed")
+    stage(f"{stage_prefix} timed")
     evs = []
     for e, l in states:
         ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in names}
@@ -432,7 +442,8 @@ def run_multistate(args):
                        "surfels": sc.n, "width": cam.width, "height": cam.height, "spp": spp,
                        "states": len(states)},
             "canonical_grad_abs_sum": float(d_can.abs().sum().item())}
-    print(json.dumps(line))
+    tr.close()
+    return line
 
 
 def stage(msg):
@@ -538,20 +549,31 @@ def main():
     hbm, peak_kind = read_peaks()
     avg = {n: statistics.mean(v) for n, v in phase_ms.items()}
     kavg = {n: statistics.mean(v) for n, v in kern_ms.items()}
-    # algorithmic bytes per launch: node visits x node bytes (lf_bvh_wide_node_bytes), surfel tests x 48 B
-    # (the quick-test quads of the packed record), composited hits x 80 B (the record's fourth quad read
-    # by the precise test, two quads and the 16 B material read by the composite; in the adjoint 196 B:
-    # the 64 B record, 16 B material, 48 B of raw surfel parameters and 17 gradient atomics of 4 B),
-    # plus each kernel's per-ray input and output (adjoint: 25 G-buffer and 9 shading-gradient floats)
-    wnode = step.tr.lib.lf_bvh_wide_node_bytes()
-    per_ray_io = {"primary": 148, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32,
+    # Algorithmic bytes per launch with the unit costs of the hot-path scope
+    # (per ray: 64 B per node visit, 48 B per surfel test, 32 B per composited
+    # hit, plus the ray's own inputs and outputs; the adjoint adds 17 x 4 B of
+    # gradient atomics per hit it scatters).  Per-ray I/O: primary 88 B of
+    # G-buffer output (22 floats); NEE shadow 44 B (queue
+    # entry, origin from the G-buffer, direction, visibility), continuation
+    # 112 B (queue entry, origin, direction, secondary record, two NEE
+    # samples), secondary shadow 32 B, adjoint 136 B per pixel (25 G-buffer and
+    # 9 shading-gradient floats).  The wide-node layout actually reads all 32
+    # child slots of a node (lf_bvh_wide_node_bytes per visit) and 80 B per
+    # composited hit; that accounting is kept beside it.
+    unit = {"node": 64, "test": 48, "hit": 32, "grad_atomics": 68}
+    per_ray_io = {"primary": 88, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32,
                   "trace_backward": 136}
-    per_hit = {n: (196 if n == "trace_backward" else 80) for n in per_ray_io}
-    node_bytes = {n: wnode for n in per_ray_io}
-    kbytes = {n: node_bytes[n] * counters[n][0] + 48 * counters[n][1] + per_hit[n] * counters[n][2] +
+    hit_cost = {n: unit["hit"] + (unit["grad_atomics"] if n == "trace_backward" else 0) for n in per_ray_io}
+    kbytes = {n: unit["node"] * counters[n][0] + unit["test"] * counters[n][1] + hit_cost[n] * counters[n][2] +
               per_ray_io[n] * counters[n][3] for n in per_ray_io}
+    wnode = step.tr.lib.lf_bvh_wide_node_bytes()
+    wide_io = dict(per_ray_io, primary=148)
+    wide_hit = {n: (196 if n == "trace_backward" else 80) for n in per_ray_io}
+    kbytes_wide = {n: wnode * counters[n][0] + 48 * counters[n][1] + wide_hit[n] * counters[n][2] +
+                   wide_io[n] * counters[n][3] for n in per_ray_io}
     kernels = {n: {"ms": round(kavg[n], 3), "algorithmic_bytes": kbytes.get(n),
-                   "achieved_gbs": (kbytes[n] / (kavg[n] * 1e-3) / 1e9) if n in kbytes else None}
+                   "achieved_gbs": (kbytes[n] / (kavg[n] * 1e-3) / 1e9) if n in kbytes else None,
+                   "wide_node_bytes": kbytes_wide.get(n)}
                for n in kern_names}
     dom = max(per_ray_io, key=lambda n: kavg[n])
     achieved = kbytes[dom] / (kavg[dom] * 1e-3) / 1e9
@@ -560,9 +582,10 @@ def main():
     l2_peak = step.tr.measure_l2_read()
     l2_bytes = read_traffic(KERNEL_NAMES[dom], "l2_bytes_per_launch")
     l2 = {"peak": l2_peak, "unit": "GB/s", "peak_kind": "measured in this run (ld.global.cg read loop over 32 MB)",
-          "bytes_per_launch": l2_bytes,
+          "bytes_per_launch": l2_bytes, "bytes_kind": "ncu lts__t_sectors x 32 B of the same kernel",
           "achieved": l2_bytes / (kavg[dom] * 1e-3) / 1e9 if l2_bytes else None,
-          "frac": l2_bytes / (kavg[dom] * 1e-3) / 1e9 / l2_peak if l2_bytes else None}
+          "frac": l2_bytes / (kavg[dom] * 1e-3) / 1e9 / l2_peak if l2_bytes else None,
+          "algorithmic_frac": achieved / l2_peak}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -573,16 +596,24 @@ def main():
         "step_ms": {"median": statistics.median(per_step_ms), "min": min(per_step_ms), "max": max(per_step_ms)},
         "rays_per_step": rays_all / args.steps / world,
         "phase_ms": {n: round(v, 3) for n, v in avg.items()},
-        "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"bound": "l2", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy (burst)", "traffic": traffic,
-                     "algorithmic_bytes_per_launch": kbytes[dom], "launch_ms": kavg[dom], "l2": l2},
+                     "traffic_kind": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch",
+                     "algorithmic_bytes_per_launch": kbytes[dom], "unit_costs": dict(unit, io_per_ray=per_ray_io),
+                     "launch_ms": kavg[dom], "l2": l2,
+                     "wide_node_accounting": {"bytes_per_launch": kbytes_wide[dom], "node_bytes": wnode,
+                                              "achieved": kbytes_wide[dom] / (kavg[dom] * 1e-3) / 1e9}},
         "kernels": kernels,
-        "counters": dict(counters, fields=["node visits", "surfel tests", "composited hits", "rays"],
-                         node_bytes=node_bytes),
+        "counters": dict(counters, fields=["node visits", "surfel tests", "composited hits", "rays"]),
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": args.steps * sum(KERNELS_PER_STEP.values()),
     }
+    if not args.no_multistate:
+        try:
+            line["multistate"] = multistate(1024, 64, args.ms_default_layouts, stage_prefix="multi-state (bounded)")
+        except Exception as exc:
+            line["multistate"] = {"error": str(exc)}
     if not args.no_serving:
         stage("serving comparison")
         try:
