@@ -12,6 +12,9 @@
 namespace lf {
 
 constexpr int TB = 128;
+#ifndef BACKWARD_MIN_BLOCKS
+#define BACKWARD_MIN_BLOCKS 8  // resident blocks per SM asked of the compiler (10 and 12 measured slower)
+#endif
 constexpr int BGROUPS = TB / WIDE;  // pixels per block (one per lane group)
 constexpr int BSTACK_SMEM = BGROUPS * CRAY_SMEM;
 constexpr int BTILE_W = BGROUPS >= 4 ? 4 : BGROUPS;
@@ -80,7 +83,7 @@ __device__ __forceinline__ void surfel_adjoint(const SceneDev& sc, int id, float
 // T_c = T_in / P_c, and the running sum S of the later hits' gw w is an
 // exclusive prefix sum; each lane scatters its own hit's adjoint.
 template <class Cnt>
-__global__ void __launch_bounds__(TB, 8) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
+__global__ void __launch_bounds__(TB, BACKWARD_MIN_BLOCKS) k_trace_backward(TraceArgs a, SceneDev sc, CamDev cam,
                                                        const float* __restrict__ gbuf,
                                                        const float* __restrict__ sg,
                                                        const float* __restrict__ gg, float* __restrict__ d_surfel,

@@ -568,8 +568,9 @@ __device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
 // reflection are assembled in FP64 from the FP32 inputs and rounded once:
 // in FP32 the reflection 2 (wo.h) h - wo doubles the rounding errors of h
 // (1e-7 rad at the median against 2.4e-8 for the cosine lobe), enough to
-// flip a support decision of a glossy metal's continuation ray.  Once per
-// sample, in the generation kernel (~1 % of a step).
+// flip a support decision of a glossy metal's continuation ray (so did FP32
+// cos and sin of theta_h with the rest in FP64).  Once per sample, in the
+// generation kernel (~1 % of a step).
 __device__ __forceinline__ float3 sample_ggx(float3 n, float3 wo, float r, float u1, float u2) {
   const double ag = (double)r * r, a2 = ag * ag;
   const double om = 1.0 - (double)u1, inv = 1.0 / fma(a2, (double)u1, om);

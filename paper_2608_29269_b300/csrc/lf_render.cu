@@ -5,6 +5,9 @@
 namespace lf {
 
 constexpr int TB = 128;                      // threads per block
+#ifndef PRIMARY_MIN_BLOCKS
+#define PRIMARY_MIN_BLOCKS 12  // resident blocks per SM asked of the compiler (4 % faster than 8, measured)
+#endif
 constexpr int RGROUPS = TB / WIDE;           // pixels per block (one per lane group)
 constexpr int RSTACK_SMEM = RGROUPS * CRAY_SMEM;
 constexpr int TILE_W = RGROUPS >= 4 ? 4 : RGROUPS;  // a block's pixels form a TILE_W x TILE_H tile
@@ -53,7 +56,7 @@ __device__ __forceinline__ void trace_pixel(const Grp& g, const CStack& st, cons
 }
 
 template <class Cnt>
-__global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
+__global__ void __launch_bounds__(TB, PRIMARY_MIN_BLOCKS) k_trace_primary(TraceArgs a, CamDev cam, float* __restrict__ gbuf) {
   extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const int gid = threadIdx.x / WIDE;
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(TB, 8) k_trace_primary(TraceArgs a, CamDev cam
 
 // Primary rays of several images in one launch (the served loop's launch
 // group): block b belongs to the job whose tile range holds it.
-__global__ void __launch_bounds__(TB, 8) k_trace_primary_batch(PrimaryBatch B, DevParams P, int* status) {
+__global__ void __launch_bounds__(TB, PRIMARY_MIN_BLOCKS) k_trace_primary_batch(PrimaryBatch B, DevParams P, int* status) {
   extern __shared__ __align__(16) int s_cstack[];
   const Grp g = make_grp();
   const int gid = threadIdx.x / WIDE;
