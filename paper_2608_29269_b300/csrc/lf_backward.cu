@@ -15,6 +15,9 @@ constexpr int TB = 128;
 #ifndef BACKWARD_MIN_BLOCKS
 #define BACKWARD_MIN_BLOCKS 8  // resident blocks per SM asked of the compiler (10 and 12 measured slower)
 #endif
+#ifndef BACKWARD_RAY
+#define BACKWARD_RAY RayR  // the ray in registers (RayS measured slower here)
+#endif
 constexpr int BGROUPS = TB / WIDE;  // pixels per block (one per lane group)
 constexpr int BSTACK_SMEM = BGROUPS * CRAY_SMEM;
 constexpr int BTILE_W = BGROUPS >= 4 ? 4 : BGROUPS;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(TB, BACKWARD_MIN_BLOCKS) k_trace_backward(Trac
   bool inclusive = true;
   FarKCoop kb;
   kb.P = Pm;
-  const Ray ray = make_ray(o, d);
+  const auto ray = make_ray<BACKWARD_RAY>(st.ray, g.c, g.mask, o, d);
   Cnt cnt;
   unsigned adj = 0;  // hits whose gradient this ray scatters
   for (int round = 0; round < Pm.max_rounds && remaining > 0; ++round) {

@@ -634,29 +634,79 @@ __device__ __forceinline__ float3 camera_dir(const CamDev& c, int p) {
 // The origin is o + olo: shading rays start at a G-buffer position plus an
 // offset along the normal, whose sum a double-float keeps exactly (the
 // precise hit test subtracts olo; the culling tests use o alone).
-struct Ray {
-  float3 o, olo, d, inv, oinv;
+//
+// The lanes that trace a ray together all need the same 15 values (o, d,
+// 1/d, o/d, olo).  RayR keeps them in registers, in every lane; RayS keeps
+// them once per ray in shared memory (five 16-byte quads written by
+// make_ray) and each test reads the quads it needs when it runs (a
+// broadcast load), which frees those registers in every lane for the
+// traversal and hit-test state.  Each kernel takes the kind that measured
+// faster for it: RayS where the register cap forces spills (the shadow
+// rays at 32 registers), RayR elsewhere.
+constexpr int RAY_QUADS = 5;  // shared-memory quads per ray: o, d, inv, oinv, olo
+
+__device__ __forceinline__ float3 lds3(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return f3(v.x, v.y, v.z);
+}
+__device__ __forceinline__ void sts3(unsigned a, float3 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(0.0f)
+               : "memory");
+}
+
+struct RayS {
+  unsigned s;  // shared-memory address of the ray's quads
+  __device__ __forceinline__ float3 o() const { return lds3(s); }
+  __device__ __forceinline__ float3 d() const { return lds3(s + 16); }
+  __device__ __forceinline__ float3 inv() const { return lds3(s + 32); }
+  __device__ __forceinline__ float3 oinv() const { return lds3(s + 48); }
+  __device__ __forceinline__ float3 olo() const { return lds3(s + 64); }
+};
+struct RayR {
+  float3 o_, d_, inv_, oinv_, olo_;
+  __device__ __forceinline__ float3 o() const { return o_; }
+  __device__ __forceinline__ float3 d() const { return d_; }
+  __device__ __forceinline__ float3 inv() const { return inv_; }
+  __device__ __forceinline__ float3 oinv() const { return oinv_; }
+  __device__ __forceinline__ float3 olo() const { return olo_; }
 };
 
-__device__ __forceinline__ Ray make_ray(float3 o, float3 d, float3 olo = f3(0.f, 0.f, 0.f)) {
-  Ray r;
-  r.o = o;
-  r.olo = olo;
-  r.d = d;
-  float ix = 1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x));
-  float iy = 1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y));
-  float iz = 1.0f / (fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z));
-  r.inv = f3(ix, iy, iz);
-  r.oinv = f3(o.x * ix, o.y * iy, o.z * iz);
+// The ray from o + olo along d.  `slot` is the ray's RAY_QUADS quads of
+// shared memory (used by RayS); `lane` and `mask` are the calling lane's
+// index within the lanes of the ray and their warp mask (all of them call).
+template <class R>
+__device__ __forceinline__ R make_ray(float4* slot, int lane, unsigned mask, float3 o, float3 d,
+                                      float3 olo = f3(0.f, 0.f, 0.f)) {
+  const float ix = 1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x));
+  const float iy = 1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y));
+  const float iz = 1.0f / (fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z));
+  const float3 inv = f3(ix, iy, iz), oinv = f3(o.x * ix, o.y * iy, o.z * iz);
+  R r;
+  if constexpr (sizeof(R) == sizeof(RayS)) {
+    r.s = (unsigned)__cvta_generic_to_shared(slot);
+    __syncwarp(mask);  // the previous ray's readers are done with the slot
+    if (lane < RAY_QUADS)
+      sts3(r.s + 16 * lane, lane == 0 ? o : lane == 1 ? d : lane == 2 ? inv : lane == 3 ? oinv : olo);
+    __syncwarp(mask);
+  } else {
+    r.o_ = o;
+    r.d_ = d;
+    r.inv_ = inv;
+    r.oinv_ = oinv;
+    r.olo_ = olo;
+  }
   return r;
 }
 
 // Slab test of [lo, hi] against the ray clipped to [tlo, thi].
+template <class Ray>
 __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, float hy, float hz, const Ray& r,
                                      float tlo, float thi, float& tnear) {
-  float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
-  float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
-  float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
+  const float3 inv = r.inv(), oinv = r.oinv();
+  float tx0 = fmaf(lx, inv.x, -oinv.x), tx1 = fmaf(hx, inv.x, -oinv.x);
+  float ty0 = fmaf(ly, inv.y, -oinv.y), ty1 = fmaf(hy, inv.y, -oinv.y);
+  float tz0 = fmaf(lz, inv.z, -oinv.z), tz1 = fmaf(hz, inv.z, -oinv.z);
   tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
   float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
   return tnear <= tfar;
@@ -670,14 +720,15 @@ __device__ __forceinline__ float2 h2_bits(unsigned u) {  // low half -> .x
   return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(u & 0xffffu)),
                                        __ushort_as_half((unsigned short)(u >> 16))));
 }
+template <class Ray>
 __device__ __forceinline__ bool slab_rel(const uint4& S, const float4& H, const Ray& r, float tlo, float thi,
                                          float& tnear) {
-  const float cx = fmaf(H.x, r.inv.x, -r.oinv.x), cy = fmaf(H.y, r.inv.y, -r.oinv.y),
-              cz = fmaf(H.z, r.inv.z, -r.oinv.z);
+  const float3 inv = r.inv(), oinv = r.oinv();
+  const float cx = fmaf(H.x, inv.x, -oinv.x), cy = fmaf(H.y, inv.y, -oinv.y), cz = fmaf(H.z, inv.z, -oinv.z);
   const float2 lxy = h2_bits(S.x), lzhx = h2_bits(S.y), hyz = h2_bits(S.z);
-  const float tx0 = fmaf(lxy.x, r.inv.x, cx), tx1 = fmaf(lzhx.y, r.inv.x, cx);
-  const float ty0 = fmaf(lxy.y, r.inv.y, cy), ty1 = fmaf(hyz.x, r.inv.y, cy);
-  const float tz0 = fmaf(lzhx.x, r.inv.z, cz), tz1 = fmaf(hyz.y, r.inv.z, cz);
+  const float tx0 = fmaf(lxy.x, inv.x, cx), tx1 = fmaf(lzhx.y, inv.x, cx);
+  const float ty0 = fmaf(lxy.y, inv.y, cy), ty1 = fmaf(hyz.x, inv.y, cy);
+  const float tz0 = fmaf(lzhx.x, inv.z, cz), tz1 = fmaf(hyz.y, inv.z, cz);
   tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
   const float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
   return tnear <= tfar;

@@ -41,9 +41,10 @@ __device__ __forceinline__ T gshfl(const Grp& g, T v, int src) {
   return __shfl_sync(g.mask, v, src, WIDE);
 }
 
-// Per-ray shared memory: the traversal stack (three parallel arrays) and
+// Per-ray shared memory: the ray, the traversal stack (parallel arrays) and
 // the k-buffer's merge scratch (WIDE entries).
 struct CStack {
+  float4* ray;  // the ray (RAY_QUADS quads, make_ray)
   int* code;
   int* cnt;
   float* t;
@@ -66,14 +67,15 @@ struct CStack {
 static_assert(LF_DEFER >= 0 && LF_DEFER <= WIDE, "the queue holds at most WIDE candidates");
 
 // Bytes of shared memory per ray.
-constexpr int CRAY_SMEM = CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float)) +
+constexpr int CRAY_SMEM = RAY_QUADS * 16 + CSTACK * (2 * (int)sizeof(int) + (int)sizeof(float)) +
                           WIDE * ((int)sizeof(unsigned long long) + (int)sizeof(int) + (int)sizeof(float)) +
                           WIDE * (int)sizeof(int);
 
 // Carves ray `gid`'s arrays out of a block's shared memory holding n_rays rays.
 __device__ __forceinline__ CStack ray_smem(unsigned char* smem, int n_rays, int gid) {
   CStack st;
-  unsigned long long* mk = reinterpret_cast<unsigned long long*>(smem);
+  st.ray = reinterpret_cast<float4*>(smem) + gid * RAY_QUADS;
+  unsigned long long* mk = reinterpret_cast<unsigned long long*>(smem + n_rays * RAY_QUADS * 16);
   st.mk = mk + gid * WIDE;
   int* ints = reinterpret_cast<int*>(mk + n_rays * WIDE);
   st.code = ints + gid * CSTACK;
@@ -112,7 +114,7 @@ __device__ __forceinline__ int wentry(int ii, int code) {
 //              (shadow rays): the walk then descends into the first hit
 //              child slot instead of the nearest one, saving the min-reduce
 //              of every node visit
-template <class V, class Cnt>
+template <class V, class Ray, class Cnt>
 __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, int n_inst, const Ray& ray, V& vis,
                                               const CStack& st, int* status, Cnt& cnt) {
   int sp = 0;
@@ -254,6 +256,7 @@ struct ShadowCoop {
     }
   }
 #if LF_DEFER > 0
+  template <class Ray>
   __device__ __forceinline__ void flush(const Grp& g, const Ray& ray) {
     float f = 1.0f;
     if (g.c < qn) {
@@ -264,19 +267,20 @@ struct ShadowCoop {
       load_rec3(I.geo, I.n_leaves, l, r);
       load_rec_tail(I.geo, I.n_leaves, l, r);
       float t, tl, alpha;
-      if (hit_precise(r, ray.o, ray.olo, ray.d, P, t, tl, alpha)) f = 1.0f - alpha;
+      if (hit_precise(r, ray.o(), ray.olo(), ray.d(), P, t, tl, alpha)) f = 1.0f - alpha;
     }
     qn = 0;
     __syncwarp(g.mask);
     absorb(g, f);
   }
+  template <class Ray>
   __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
     bool cand = false;
     if (g.c < count) {
       Rec r;
       load_rec3(I.geo, I.n_leaves, first + g.c, r);
       float t32;
-      cand = hit_quick(r, ray.o, ray.d, P, t32);
+      cand = hit_quick(r, ray.o(), ray.d(), P, t32);
     }
     const int nm = __popc(gballot(g, cand));
     if (nm == 0) return;
@@ -287,19 +291,22 @@ struct ShadowCoop {
     queue_candidates(g, qc, qn, cand, (ii << 24) | (first + g.c));
     if (qn >= LF_DEFER) flush(g, ray);
   }
+  template <class Ray>
   __device__ __forceinline__ void finish(const Grp& g, const Ray& ray) {
     if (qn > 0) flush(g, ray);
   }
 #else
+  template <class Ray>
   __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int, int first, int count, const Inst& I) {
     float f = 1.0f;
     if (g.c < count) {
       Rec r;
       float t32, t, tl, alpha;
-      if (hit_surfel(I.geo, I.n_leaves, first + g.c, ray.o, ray.olo, ray.d, P, r, t32, t, tl, alpha)) f = 1.0f - alpha;
+      if (hit_surfel(I.geo, I.n_leaves, first + g.c, ray.o(), ray.olo(), ray.d(), P, r, t32, t, tl, alpha)) f = 1.0f - alpha;
     }
     absorb(g, f);
   }
+  template <class Ray>
   __device__ __forceinline__ void finish(const Grp&, const Ray&) {}
 #endif
 };
@@ -394,11 +401,12 @@ struct NearKCoop {
     else if (cnt >= WIDE) tcut = key_t(kmax);
   }
   // Precise test of record l of instance ii (its first three quads in r).
+  template <class Ray>
   __device__ __forceinline__ bool precise(const Ray& ray, const Inst& I, int ii, int l, Rec& r,
                                           unsigned long long& key, int& code, float& alpha) const {
     float t, tl;
     load_rec_tail(I.geo, I.n_leaves, l, r);
-    if (!hit_precise(r, ray.o, ray.olo, ray.d, P, t, tl, alpha)) return false;
+    if (!hit_precise(r, ray.o(), ray.olo(), ray.d(), P, t, tl, alpha)) return false;
     key = hit_key(t, tl, rec_id(r));
     code = (ii << 24) | l;
     return key > last && (cnt < WIDE || key < kmax);
@@ -407,6 +415,7 @@ struct NearKCoop {
   int* qc;  // candidate queue (LF_DEFER > 0)
   int qn;
 #if LF_DEFER > 0
+  template <class Ray>
   __device__ __forceinline__ void flush(const Grp& g, const Ray& ray) {
     bool valid = false;
     unsigned long long key = 0ull;
@@ -424,13 +433,14 @@ struct NearKCoop {
     __syncwarp(g.mask);
     merge(g, valid, key, code, alpha);
   }
+  template <class Ray>
   __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
     bool cand = false;
     if (g.c < count) {
       Rec r;
       load_rec3(I.geo, I.n_leaves, first + g.c, r);
       float t32;
-      cand = hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f);
+      cand = hit_quick(r, ray.o(), ray.d(), P, t32) && !(t32 > tcut * 1.0001f + 1e-6f);
     }
     const int nm = __popc(gballot(g, cand));
     if (nm == 0) return;
@@ -438,10 +448,12 @@ struct NearKCoop {
     queue_candidates(g, qc, qn, cand, (ii << 24) | (first + g.c));
     if (qn >= LF_DEFER) flush(g, ray);
   }
+  template <class Ray>
   __device__ __forceinline__ void finish(const Grp& g, const Ray& ray) {
     if (qn > 0) flush(g, ray);
   }
 #else
+  template <class Ray>
   __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
     bool valid = false;
     unsigned long long key = 0ull;
@@ -452,11 +464,12 @@ struct NearKCoop {
       Rec r;
       load_rec3(I.geo, I.n_leaves, l, r);
       float t32;
-      if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > tcut * 1.0001f + 1e-6f))
+      if (hit_quick(r, ray.o(), ray.d(), P, t32) && !(t32 > tcut * 1.0001f + 1e-6f))
         valid = precise(ray, I, ii, l, r, key, code, alpha);
     }
     merge(g, valid, key, code, alpha);
   }
+  template <class Ray>
   __device__ __forceinline__ void finish(const Grp&, const Ray&) {}
 #endif
 };
@@ -488,7 +501,9 @@ struct FarKCoop {
   __device__ __forceinline__ float thi() const { return key_t(bound); }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() { cnt = 0; }
+  template <class Ray>
   __device__ __forceinline__ void finish(const Grp&, const Ray&) {}
+  template <class Ray>
   __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
     bool valid = false;
     unsigned long long key = 0ull;
@@ -498,10 +513,10 @@ struct FarKCoop {
       Rec r;
       load_rec3(I.geo, I.n_leaves, l, r);
       float t32;
-      if (hit_quick(r, ray.o, ray.d, P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
+      if (hit_quick(r, ray.o(), ray.d(), P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
         float t, tl, alpha;
         load_rec_tail(I.geo, I.n_leaves, l, r);
-        if (hit_precise(r, ray.o, ray.olo, ray.d, P, t, tl, alpha)) {
+        if (hit_precise(r, ray.o(), ray.olo(), ray.d(), P, t, tl, alpha)) {
           key = hit_key(t, tl, rec_id(r));
           valid = (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
           code = (ii << 24) | l;
@@ -548,7 +563,7 @@ __device__ __forceinline__ float gsum(const Grp& g, float v) {
 // in front of each hit by a prefix product over the lanes, the stop at the
 // first hit whose transmittance behind it falls below T_min, weighted sums by
 // butterflies.  Every lane ends with the same Surface.
-template <class Cnt>
+template <class Ray, class Cnt>
 __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, int n_inst, float3 o, float3 olo,
                                                float3 d,
                                                const DevParams& P, const CStack& st, int* status, Cnt& cnt,
@@ -560,17 +575,31 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   kb.ma = st.ma;
   kb.insts = insts;
   kb.qc = st.qc;
-  const Ray ray = make_ray(o, d, olo);
+  const Ray ray = make_ray<Ray>(st.ray, g.c, g.mask, o, d, olo);
   // The composited position sum w x_j / (W + eps) is kept as
   // (o + t_ref d) W / (W + eps) + d sum w (t_j - t_ref) / (W + eps) around
   // the depth t_ref + tl_ref of the first composited hit (its key keeps the
   // low part): the hit points of a ray differ by little along it, so the
   // offsets stay small and the position carries about one rounding of
   // o + t_ref d instead of one per hit (shading rays start there).
-  float T = 1.0f, W = 0.0f, St = 0.0f, Sm = 0.0f, Sr = 0.0f, Sdt = 0.0f, t_ref = 0.0f, tl_ref = 0.0f;
-  float3 Sn = f3(0.f, 0.f, 0.f), Sa = Sn;
-  int hits = 0;
-  unsigned long long stop_key = 0ull, last = 0ull;
+  //
+  // The sums are the same for every lane; lane k % WIDE keeps sum k (slot
+  // k / WIDE of its acc), so across the traversal a lane holds one or two
+  // registers for them instead of fifteen.
+  enum { A_W, A_DT, A_T, A_NX, A_NY, A_NZ, A_AX, A_AY, A_AZ, A_M, A_R, A_TREF, A_TLREF, A_HITS, A_SKLO, A_SKHI, NACC };
+  constexpr int NSLOT = (NACC + WIDE - 1) / WIDE;
+  float acc[NSLOT];
+#pragma unroll
+  for (int k = 0; k < NSLOT; ++k) acc[k] = 0.0f;
+  auto add = [&](int k, float v) {
+    if (g.c == k % WIDE) acc[k / WIDE] += v;
+  };
+  auto put = [&](int k, float v) {
+    if (g.c == k % WIDE) acc[k / WIDE] = v;
+  };
+  auto get = [&](int k) { return gshfl(g, acc[k / WIDE], k % WIDE); };
+  float T = 1.0f, t_ref = 0.0f;
+  unsigned long long last = 0ull;
   bool done = false;
   for (int round = 0; round < P.max_rounds && !done; ++round) {
     kb.reset(last, T);
@@ -591,7 +620,7 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
       const float4 g0 = __ldg(I.geo + l), g1 = __ldg(I.geo + nl + l), g3 = __ldg(I.geo + 3 * nl + l);
       const float4 mt = __ldg(I.mat + l);
       const float3 nh = f3(g0.w, g1.x, g1.y);
-      nj = dot3(d, nh) < 0.0f ? nh : -nh;
+      nj = dot3(ray.d(), nh) < 0.0f ? nh : -nh;
       alb = f3(mt.x, mt.y, mt.z);
       mtl = mt.w;
       rgh = g3.z;
@@ -611,54 +640,63 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     const float w = (have && g.c <= lastc) ? Tb * alpha : 0.0f;
     if (round == 0) {
       t_ref = gshfl(g, t, 0);
-      tl_ref = key_tl(gshfl(g, kb.bk, 0));
+      put(A_TREF, t_ref);
+      put(A_TLREF, key_tl(gshfl(g, kb.bk, 0)));
     }
-    W += gsum(g, w);
-    Sdt += gsum(g, w * (t - t_ref));
-    St += gsum(g, w * t);
-    Sn.x += gsum(g, w * nj.x);
-    Sn.y += gsum(g, w * nj.y);
-    Sn.z += gsum(g, w * nj.z);
-    Sa.x += gsum(g, w * alb.x);
-    Sa.y += gsum(g, w * alb.y);
-    Sa.z += gsum(g, w * alb.z);
-    Sm += gsum(g, w * mtl);
-    Sr += gsum(g, w * rgh);
+    add(A_W, gsum(g, w));
+    add(A_DT, gsum(g, w * (t - t_ref)));
+    add(A_T, gsum(g, w * t));
+    add(A_NX, gsum(g, w * nj.x));
+    add(A_NY, gsum(g, w * nj.y));
+    add(A_NZ, gsum(g, w * nj.z));
+    add(A_AX, gsum(g, w * alb.x));
+    add(A_AY, gsum(g, w * alb.y));
+    add(A_AZ, gsum(g, w * alb.z));
+    add(A_M, gsum(g, w * mtl));
+    add(A_R, gsum(g, w * rgh));
     T = gshfl(g, Ta, lastc);
-    hits += lastc + 1;
-    stop_key = gshfl(g, kb.bk, lastc);
+    add(A_HITS, (float)(lastc + 1));
+    const unsigned long long sk = gshfl(g, kb.bk, lastc);
+    put(A_SKLO, __uint_as_float((unsigned)sk));
+    put(A_SKHI, __uint_as_float((unsigned)(sk >> 32)));
     done = stopm != 0u || n < WIDE;
     if (!done) {
       last = kb.kmax;
       if (round == P.max_rounds - 1 && g.c == 0) report(status, LF_ERR_ROUND_LIMIT);
+      t_ref = get(A_TREF);
     }
   }
+  const int hits = (int)get(A_HITS);
   if (g.c == 0) composited += (unsigned)hits;
+  const float W = get(A_W);
   const float inv = 1.0f / (W + P.eps_w);
   s.T = T;
   s.W = W;
   {
     // o + t_ref d as an exact pair (TwoProd, TwoSum), so the position is
     // rounded once, at the end
-    const float wf = W * inv, lo = fmaf(Sdt, inv, tl_ref * wf);
+    const float tr = get(A_TREF);
+    const float wf = W * inv, lo = fmaf(get(A_DT), inv, get(A_TLREF) * wf);
     auto axis = [&](float oc, float oloc, float dc) {
       float p, pe, h, he;
-      two_prod(dc, t_ref, p, pe);
+      two_prod(dc, tr, p, pe);
       two_sum(oc, p, h, he);
       return fmaf(wf, h, fmaf(wf, he + pe + oloc, dc * lo));
     };
+    const float3 o = ray.o(), olo = ray.olo(), d = ray.d();
     s.x = f3(axis(o.x, olo.x, d.x), axis(o.y, olo.y, d.y), axis(o.z, olo.z, d.z));
   }
-  s.depth = St * inv;
+  const float3 Sa = f3(get(A_AX), get(A_AY), get(A_AZ));
+  s.depth = get(A_T) * inv;
   s.a = Sa * inv;
   s.Sa = Sa;
-  s.m = Sm * inv;
-  s.r = Sr * inv;
-  const float3 mv = Sn * inv;
+  s.m = get(A_M) * inv;
+  s.r = get(A_R) * inv;
+  const float3 mv = f3(get(A_NX), get(A_NY), get(A_NZ)) * inv;
   s.nlen = sqrtf(dot3(mv, mv));
-  s.n = s.nlen < 1e-12f ? -d : mv * (1.0f / s.nlen);
+  s.n = s.nlen < 1e-12f ? -ray.d() : mv * (1.0f / s.nlen);
   s.hits = hits;
-  s.stop_key = stop_key;
+  s.stop_key = ((unsigned long long)__float_as_uint(get(A_SKHI)) << 32) | __float_as_uint(get(A_SKLO));
 }
 
 }  // namespace lf

@@ -8,6 +8,9 @@ constexpr int TB = 128;                      // threads per block
 #ifndef PRIMARY_MIN_BLOCKS
 #define PRIMARY_MIN_BLOCKS 12  // resident blocks per SM asked of the compiler (4 % faster than 8, measured)
 #endif
+#ifndef PRIMARY_RAY
+#define PRIMARY_RAY RayR  // the primary ray in registers (RayS measured slower here)
+#endif
 constexpr int RGROUPS = TB / WIDE;           // pixels per block (one per lane group)
 constexpr int RSTACK_SMEM = RGROUPS * CRAY_SMEM;
 constexpr int TILE_W = RGROUPS >= 4 ? 4 : RGROUPS;  // a block's pixels form a TILE_W x TILE_H tile
@@ -28,7 +31,7 @@ __device__ __forceinline__ void trace_pixel(const Grp& g, const CStack& st, cons
   Cnt cnt;
   unsigned comp = 0;
   Surface s;
-  coop_composite(g, insts, n_inst, cam.eye, f3(0.f, 0.f, 0.f), d, P, st, status, cnt, s, comp);
+  coop_composite<PRIMARY_RAY>(g, insts, n_inst, cam.eye, f3(0.f, 0.f, 0.f), d, P, st, status, cnt, s, comp);
   if (g.c != 0) return;
   const float3 rho = s.Sa + env_lookup(env, d) * s.T;
   float* gp = gbuf + p;

@@ -27,15 +27,23 @@
 namespace lf {
 
 constexpr int WB = 128;  // threads per block of the wavefront kernels
-// Minimum resident blocks per SM asked of the compiler (caps registers).
-// Measured with the deferred precise tests: shadow rays 16 blocks (full
-// occupancy, 32 registers) 4 % faster than 10; continuation rays 10 blocks
-// (48 registers) 2 % faster than 8 and 12.
+// Minimum resident blocks per SM asked of the compiler (caps registers) and
+// where the traced ray is held (RayS: shared memory, RayR: registers).
+// Measured on the 800x800x16 room step: shadow rays 16 blocks (full
+// occupancy, 32 registers) with RayS, 4 % faster than RayR; continuation
+// rays 8 blocks (64 registers) with RayS, 1 % faster than 10 blocks with
+// either kind and 5 % faster than 8 blocks with RayR.
 #ifndef WF_MIN_BLOCKS_SHADOW
 #define WF_MIN_BLOCKS_SHADOW 16
 #endif
 #ifndef WF_MIN_BLOCKS_CONTINUE
-#define WF_MIN_BLOCKS_CONTINUE 10
+#define WF_MIN_BLOCKS_CONTINUE 8
+#endif
+#ifndef WF_SHADOW_RAY
+#define WF_SHADOW_RAY RayS
+#endif
+#ifndef WF_CONTINUE_RAY
+#define WF_CONTINUE_RAY RayS
 #endif
 // Slots of SampleBuf::counts: queue lengths A, B, C (0-2); fetch cursors of
 // the three trace kernels (4-6).
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
     }
     v.V = 1.0f;
     v.stop = false;
-    const Ray ray = make_ray(o, d, olo);
+    const auto ray = make_ray<WF_SHADOW_RAY>(st.ray, g.c, g.mask, o, d, olo);
     coop_traverse(g, J.insts, J.n_inst, ray, v, st, status, cnt);
     if (g.c == 0) {
       if (which == 0) S.Ve[item] = v.V;
@@ -278,7 +286,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
     const float3 xs = pix_origin(J, (int)(loc / J.spp), P.ray_offset, xslo);
     const float3 wi = ld3(S.wi, item);
     Surface s2;
-    coop_composite(g, J.insts, J.n_inst, xs, xslo, wi, P, st, status, cnt, s2, comp);
+    coop_composite<WF_CONTINUE_RAY>(g, J.insts, J.n_inst, xs, xslo, wi, P, st, status, cnt, s2, comp);
     if (g.c == 0) {
       S.T2[item] = s2.T;
       if (s2.hits > 0) {
