@@ -118,14 +118,18 @@ template <class V, class Ray, class Cnt>
 __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, int n_inst, const Ray& ray, V& vis,
                                               const CStack& st, int* status, Cnt& cnt) {
   int sp = 0;
+  // a tree of n leaves has fewer than n wide nodes; the budget only guards
+  // against a malformed tree
+  int budget = 8;
   // instance boxes, WIDE at a time; instance 0 (background) ends up deepest
   for (int i0 = 0; i0 < n_inst; i0 += WIDE) {
     const int ii = i0 + g.c;
     bool hit = false;
     float tn = 0.0f;
-    int code = 0, count = 0;
+    int code = 0, count = 0, nl = 0;
     if (ii < n_inst) {
       const Inst& I = insts[ii];
+      nl = I.n_leaves;
       if (I.wroot != INT_MIN &&
           slab(I.lo[0], I.lo[1], I.lo[2], I.hi[0], I.hi[1], I.hi[2], ray, vis.tlo(), vis.thi(), tn)) {
         hit = true;
@@ -146,12 +150,9 @@ __device__ __forceinline__ void coop_traverse(const Grp& g, const Inst* insts, i
       st.t[pos] = tn;
     }
     sp += __popc(m);
+    budget += __reduce_add_sync(g.mask, nl);
   }
   __syncwarp(g.mask);
-  // a tree of n leaves has fewer than n wide nodes; the budget only guards
-  // against a malformed tree
-  int budget = 8;
-  for (int ii = 0; ii < n_inst; ++ii) budget += insts[ii].n_leaves;
   while (sp > 0) {
     --sp;
     const float t0 = st.t[sp];
