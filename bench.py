@@ -141,6 +141,7 @@ class Step:
         import numpy as np
         import torch
         from paper_2608_29269_b300 import SceneTensors, Tracer
+        from paper_2608_29269_b300._native import LF_GBUF_CHANNELS
         self.torch = torch
         self.cam, self.spp, self.seed = cam, spp, seed
         self.tr = Tracer()
@@ -149,7 +150,7 @@ class Step:
         self.tr.build(self.st)
         self.tr.set_env(0, self.env)
         P = cam.width * cam.height
-        self.gbuf = torch.empty((25, cam.height, cam.width), device="cuda")
+        self.gbuf = torch.empty((LF_GBUF_CHANNELS, cam.height, cam.width), device="cuda")
         self.rgb = torch.empty((cam.height, cam.width, 3), device="cuda")
         self.samples = self.tr.alloc_samples(cam, spp)
         self.scratch = torch.empty((9 * P * 4 + 256 + 3) // 4, device="cuda")
@@ -387,7 +388,8 @@ def multistate(size, spp, n_layouts, stage_prefix="multi-state"):
             R[o - 1], t[o - 1] = S.rigid_motion(rng, sc.mu[lo:hi].mean(0), max_shift=0.5)
         layouts.append((R, t))
     P = cam.width * cam.height
-    gbuf = torch.empty((25, cam.height, cam.width), device="cuda")
+    from paper_2608_29269_b300._native import LF_GBUF_CHANNELS
+    gbuf = torch.empty((LF_GBUF_CHANNELS, cam.height, cam.width), device="cuda")
     rgb = torch.empty((cam.height, cam.width, 3), device="cuda")
     samples = tr.alloc_samples(cam, spp)
     scratch = torch.empty((9 * P * 4 + 256 + 3) // 4, device="cuda")

@@ -121,7 +121,12 @@ enum {
   LF_CH_IDSTOP = 20, /* surfel id of the last composited hit (-1: none) */
   LF_CH_DIR = 21,    /* primary ray direction (3)                     */
   LF_CH_STOPKEY_LO = 24, /* raw bits: low word of the stop hit's sort key */
-  LF_GBUF_CHANNELS = 25,
+  LF_CH_X_LO = 25,   /* residual of the position below its FP32 value (3) */
+  LF_CH_N_LO = 28,   /* residual of the normal (3)                    */
+  LF_CH_R_LO = 31,   /* residual of the roughness                     */
+                     /* (x + x_lo etc.: the composite to ~1e-14; shading */
+                     /* rays start from and sample around these pairs) */
+  LF_GBUF_CHANNELS = 32,
   LF_GBUF_DIFF = 17  /* channels 0..16 accept an upstream gradient    */
 };
 

@@ -15,10 +15,10 @@ STATUS_NAMES = ["LF_OK", "LF_ERR_INVALID", "LF_ERR_OOM", "LF_ERR_CUDA", "LF_ERR_
 LF_MAX_OBJECTS = 64
 LF_MAX_ENVS = 16
 LF_KBUF = 32
-LF_GBUF_CHANNELS = 25
+LF_GBUF_CHANNELS = 32
 LF_GBUF_DIFF = 17
 CH = dict(T=0, W=1, depth=2, x=3, n=6, a=9, m=12, r=13, rho=14, nlen=17, hits=18, t_stop=19, id_stop=20, dir=21,
-          stopkey_lo=24)
+          stopkey_lo=24, x_lo=25, n_lo=28, r_lo=31)
 G_STRIDE = 17
 
 

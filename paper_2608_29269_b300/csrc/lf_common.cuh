@@ -277,6 +277,44 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   p = __fmul_rn(a, b);
   e = __fmaf_rn(a, b, -p);
 }
+// Double-float values hi + lo (|lo| <= ulp(hi) / 2) and the operations the
+// precise composite needs, after Dekker (1971): a sum by TwoSum, a product by
+// TwoProd, a quotient and a square root by one correction step of the FP32
+// result with its exactly formed residual; relative error ~1e-14.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_renorm(float s, float e) {  // |s| >= |e|
+  DF r;
+  r.hi = __fadd_rn(s, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+  return r;
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df_renorm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  return df_renorm(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q = __fdiv_rn(a.hi, b.hi);
+  float p, e;
+  two_prod(q, b.hi, p, e);  // q b.hi exactly
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), __fsub_rn(a.lo, __fmul_rn(q, b.lo)));
+  return df_renorm(q, __fdiv_rn(r, b.hi));
+}
+__device__ __forceinline__ DF df_sqrt(DF a) {  // a > 0
+  const float s = __fsqrt_rn(a.hi);
+  float p, e;
+  two_prod(s, s, p, e);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
+  return df_renorm(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
+
 // (ah + al) . b as a renormalised double-float (compensated dot product,
 // Ogita, Rump and Oishi 2005).
 __device__ __forceinline__ void dot2(float3 ah, float3 al, float3 b, float& hi, float& lo) {
@@ -551,52 +589,68 @@ __device__ __forceinline__ void brdf_adjoint(float3 n, float3 wo, float3 wi, flo
 }
 
 // ------------------------------------------------------------------ sampling
-// Orthonormal basis (b1, b2, n) after Duff et al. 2017.
-__device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
-  float sgn = copysignf(1.0f, n.z);
-  float a = -1.0f / (sgn + n.z);
-  float b = n.x * n.y * a;
-  b1 = f3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
-  b2 = f3(b, sgn + n.y * n.y * a, -n.y);
+// 1 / x and sqrt(x) in FP64 from FP32 seeds and one Newton step in the FMA
+// form (Markstein 1990): the seed's relative error e (~1e-7) leaves ~e^2,
+// without FP64 division or square root (slow on this part).
+__device__ __forceinline__ double rcp64(double x) {
+  const double r0 = (double)(1.0f / (float)x);
+  return fma(r0, fma(-x, r0, 1.0), r0);
+}
+__device__ __forceinline__ double sqrt64(double x) {  // x >= 0
+  const float xf = (float)x;
+  if (!(xf > 0.0f)) return 0.0;
+  const double s0 = (double)sqrtf(xf);
+  return fma(fma(-s0, s0, x), (double)(0.5f / (float)s0), s0);
 }
 
-// GGX half vector with density D(h)(n.h) (Walter et al. 2007), mirrored:
-// cos^2 theta_h = (1 - u1) / (1 + (a2 - 1) u1), evaluated as
+// BSDF sample direction: the cosine lobe (Malley's method) or, when `spec`,
+// the mirrored GGX half vector with density D(h)(n.h) (Walter et al. 2007).
+// The local direction, the frame (b1, b2, n) after Duff et al. 2017 of the
+// record's normal with its residual (n + nlo) and the reflection are
+// assembled in FP64 from the FP32 inputs (roughness r + rlo) and rounded
+// once, so the FP32 rounding of the result (~5e-8 rad) is about its only
+// error; in FP32 the frame and the reflection 2 (wo.h) h - wo (which doubles
+// the rounding errors of h and of the roughness) gave up to 6e-7 rad at
+// roughness 0.7, enough to flip a support decision of a glossy metal's
+// continuation ray.  The azimuth is sincospif's (one ulp, ~6e-8).  One code
+// path for both lobes, so a warp whose samples pick both pays for the FP64
+// assembly once.
+//
+// GGX: cos^2 theta_h = (1 - u1) / (1 + (a2 - 1) u1), evaluated as
 // (1 - u1) / ((1 - u1) + a2 u1) and sin^2 as a2 u1 / (same), which keeps the
 // digits of both for a glossy lobe (small a2) at either end of u1 (1 - u1 is
-// exact for the 24-bit uniforms).  The frame, the half vector and the
-// reflection are assembled in FP64 from the FP32 inputs and rounded once:
-// in FP32 the reflection 2 (wo.h) h - wo doubles the rounding errors of h
-// (1e-7 rad at the median against 2.4e-8 for the cosine lobe), enough to
-// flip a support decision of a glossy metal's continuation ray (so did FP32
-// cos and sin of theta_h with the rest in FP64).  Once per sample, in the
-// generation kernel (~1 % of a step).
-__device__ __forceinline__ float3 sample_ggx(float3 n, float3 wo, float r, float u1, float u2) {
-  const double ag = (double)r * r, a2 = ag * ag;
-  const double om = 1.0 - (double)u1, inv = 1.0 / fma(a2, (double)u1, om);
-  const double ct = sqrt(om * inv), st = sqrt(a2 * (double)u1 * inv);
+// exact for the 24-bit uniforms).
+__device__ __forceinline__ float3 sample_bsdf_dir(bool spec, float3 n, float3 nlo, float3 wo, float r, float rlo,
+                                                  float u1, float u2) {
+  double st, ct;
+  const double om = 1.0 - (double)u1;
+  if (spec) {
+    const double rd = (double)r + rlo, ag = rd * rd, a2 = ag * ag;
+    const double inv = rcp64(fma(a2, (double)u1, om));
+    ct = sqrt64(om * inv);
+    st = sqrt64(a2 * (double)u1 * inv);
+  } else {
+    st = sqrt64((double)u1);
+    ct = sqrt64(om);
+  }
   float spf, cpf;
   sincospif(2.0f * u2, &spf, &cpf);  // angle 2 pi u2 without rounding 2 pi u2
-  const double sp = spf, cp = cpf;
-  const double nx = n.x, ny = n.y, nz = n.z;
-  const double sgn = copysign(1.0, nz);  // as in onb()
-  const double a = -1.0 / (sgn + nz), b = nx * ny * a;
+  const double sp = (double)spf * st, cp = (double)cpf * st;
+  const double nx = (double)n.x + nlo.x, ny = (double)n.y + nlo.y, nz = (double)n.z + nlo.z;
+  const double sgn = copysign(1.0, nz);
+  const double a = -rcp64(sgn + nz), b = nx * ny * a;
   const double b1x = 1.0 + sgn * nx * nx * a, b1y = sgn * b, b1z = -sgn * nx;
   const double b2x = b, b2y = sgn + ny * ny * a, b2z = -ny;
-  const double hx = b1x * (st * cp) + b2x * (st * sp) + nx * ct;
-  const double hy = b1y * (st * cp) + b2y * (st * sp) + ny * ct;
-  const double hz = b1z * (st * cp) + b2z * (st * sp) + nz * ct;
-  const double oh2 = 2.0 * ((double)wo.x * hx + (double)wo.y * hy + (double)wo.z * hz);
-  return f3((float)(hx * oh2 - wo.x), (float)(hy * oh2 - wo.y), (float)(hz * oh2 - wo.z));
-}
-
-// Cosine-weighted hemisphere (Malley's method).
-__device__ __forceinline__ float3 sample_cos(float3 n, float u1, float u2) {
-  float rr = sqrtf(u1), sp, cp;
-  sincospif(2.0f * u2, &sp, &cp);  // angle 2 pi u2 without rounding 2 pi u2
-  float3 b1, b2;
-  onb(n, b1, b2);
-  return b1 * (rr * cp) + b2 * (rr * sp) + n * sqrtf(fmaxf(0.0f, 1.0f - u1));
+  double vx = b1x * cp + b2x * sp + nx * ct;
+  double vy = b1y * cp + b2y * sp + ny * ct;
+  double vz = b1z * cp + b2z * sp + nz * ct;
+  if (spec) {
+    const double oh2 = 2.0 * ((double)wo.x * vx + (double)wo.y * vy + (double)wo.z * vz);
+    vx = vx * oh2 - wo.x;
+    vy = vy * oh2 - wo.y;
+    vz = vz * oh2 - wo.z;
+  }
+  return f3((float)vx, (float)vy, (float)vz);
 }
 
 __device__ __forceinline__ float pdf_bsdf(float3 n, float3 wo, float3 wi, float r, float p_spec) {
@@ -758,6 +812,8 @@ constexpr int LEAF_BIT = 1 << 24;
 struct Surface {
   float T, W, depth, m, r, nlen;
   float3 x, n, a;
+  float3 x_lo, n_lo;  // residuals of x and n below their FP32 values (precise composite; else 0)
+  float r_lo;
   float3 Sa;  // sum w a (un-normalised)
   int hits;
   unsigned long long stop_key;  // key of the last composited hit (0: none)

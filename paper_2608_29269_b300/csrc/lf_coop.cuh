@@ -557,6 +557,21 @@ __device__ __forceinline__ float gsum(const Grp& g, float v) {
   for (int off = WIDE / 2; off > 0; off >>= 1) v += __shfl_xor_sync(g.mask, v, off, WIDE);
   return v;
 }
+// Group sum as a double-float: every butterfly step adds the partner's pair
+// by TwoSum, whose error term is the exact rounding error whatever the
+// operand order, so every lane again receives the same bits.
+__device__ __forceinline__ DF gsum_df(const Grp& g, float v) {
+  float h = v, l = 0.0f;
+#pragma unroll
+  for (int off = WIDE / 2; off > 0; off >>= 1) {
+    const float oh = __shfl_xor_sync(g.mask, h, off, WIDE), ol = __shfl_xor_sync(g.mask, l, off, WIDE);
+    float sh, e;
+    two_sum(h, oh, sh, e);
+    l = __fadd_rn(__fadd_rn(l, ol), e);
+    h = sh;
+  }
+  return df_renorm(h, l);
+}
 
 // Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop),
 // cooperative: each round collects the K nearest hits beyond the last
@@ -564,7 +579,16 @@ __device__ __forceinline__ float gsum(const Grp& g, float v) {
 // in front of each hit by a prefix product over the lanes, the stop at the
 // first hit whose transmittance behind it falls below T_min, weighted sums by
 // butterflies.  Every lane ends with the same Surface.
-template <class Ray, class Cnt>
+//
+// Precise (the primary record, from which shading rays start and BSDF
+// samples are drawn): the sums of w, w r and w n are double-floats, and x,
+// n and r are formed from them in double-float and returned as FP32 values
+// plus their residuals (x_lo, n_lo, r_lo), so the record carries about one
+// rounding of the FP64 composite instead of the FP32 butterflies' and
+// divisions' (up to ~3e-7 relative in r and n, and W / (W + eps) within an
+// ulp of 1 moved x by up to ~2e-7 in a room of half-size 2).  Otherwise the
+// residuals are 0.
+template <class Ray, bool Precise = false, class Cnt>
 __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, int n_inst, float3 o, float3 olo,
                                                float3 d,
                                                const DevParams& P, const CStack& st, int* status, Cnt& cnt,
@@ -586,8 +610,11 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   //
   // The sums are the same for every lane; lane k % WIDE keeps sum k (slot
   // k / WIDE of its acc), so across the traversal a lane holds one or two
-  // registers for them instead of fifteen.
-  enum { A_W, A_DT, A_T, A_NX, A_NY, A_NZ, A_AX, A_AY, A_AZ, A_M, A_R, A_TREF, A_TLREF, A_HITS, A_SKLO, A_SKHI, NACC };
+  // registers for them instead of fifteen or more.
+  enum {
+    A_W, A_DT, A_T, A_NX, A_NY, A_NZ, A_AX, A_AY, A_AZ, A_M, A_R, A_TREF, A_TLREF, A_HITS, A_SKLO, A_SKHI,
+    A_WL, A_NXL, A_NYL, A_NZL, A_RL, NACC  // the low words of the double-float sums (Precise)
+  };
   constexpr int NSLOT = (NACC + WIDE - 1) / WIDE;
   float acc[NSLOT];
 #pragma unroll
@@ -599,6 +626,11 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     if (g.c == k % WIDE) acc[k / WIDE] = v;
   };
   auto get = [&](int k) { return gshfl(g, acc[k / WIDE], k % WIDE); };
+  auto add_df = [&](int khi, int klo, DF v) {  // acc pair (khi, klo) += v
+    const DF sum = df_add(DF{get(khi), get(klo)}, v);
+    put(khi, sum.hi);
+    put(klo, sum.lo);
+  };
   float T = 1.0f, t_ref = 0.0f;
   unsigned long long last = 0ull;
   bool done = false;
@@ -644,17 +676,25 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
       put(A_TREF, t_ref);
       put(A_TLREF, key_tl(gshfl(g, kb.bk, 0)));
     }
-    add(A_W, gsum(g, w));
+    if constexpr (Precise) {
+      add_df(A_W, A_WL, gsum_df(g, w));
+      add_df(A_NX, A_NXL, gsum_df(g, w * nj.x));
+      add_df(A_NY, A_NYL, gsum_df(g, w * nj.y));
+      add_df(A_NZ, A_NZL, gsum_df(g, w * nj.z));
+      add_df(A_R, A_RL, gsum_df(g, w * rgh));
+    } else {
+      add(A_W, gsum(g, w));
+      add(A_NX, gsum(g, w * nj.x));
+      add(A_NY, gsum(g, w * nj.y));
+      add(A_NZ, gsum(g, w * nj.z));
+      add(A_R, gsum(g, w * rgh));
+    }
     add(A_DT, gsum(g, w * (t - t_ref)));
     add(A_T, gsum(g, w * t));
-    add(A_NX, gsum(g, w * nj.x));
-    add(A_NY, gsum(g, w * nj.y));
-    add(A_NZ, gsum(g, w * nj.z));
     add(A_AX, gsum(g, w * alb.x));
     add(A_AY, gsum(g, w * alb.y));
     add(A_AZ, gsum(g, w * alb.z));
     add(A_M, gsum(g, w * mtl));
-    add(A_R, gsum(g, w * rgh));
     T = gshfl(g, Ta, lastc);
     add(A_HITS, (float)(lastc + 1));
     const unsigned long long sk = gshfl(g, kb.bk, lastc);
@@ -673,10 +713,44 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   const float inv = 1.0f / (W + P.eps_w);
   s.T = T;
   s.W = W;
-  {
+  const float tr = get(A_TREF);
+  const float3 o3 = ray.o(), olo3 = ray.olo(), d3 = ray.d();
+  if constexpr (Precise) {
+    const DF den = df_add(DF{get(A_W), get(A_WL)}, DF{P.eps_w, 0.0f});
+    const DF idf = df_div(DF{1.0f, 0.0f}, den);
+    const DF wf = df_mul(DF{get(A_W), get(A_WL)}, idf);
+    const float lo = fmaf(get(A_DT), inv, get(A_TLREF) * wf.hi);
+    // o + olo + t_ref d as h + (he + pe + olo), exact to ~1e-15 relative,
+    // times W / (W + eps), plus the small offset along d
+    auto axis = [&](float oc, float oloc, float dc, float& xlo) {
+      float p, pe, h, he;
+      two_prod(dc, tr, p, pe);
+      two_sum(oc, p, h, he);
+      const DF x = df_add(df_mul(wf, df_renorm(h, __fadd_rn(__fadd_rn(he, pe), oloc))), DF{__fmul_rn(dc, lo), 0.0f});
+      xlo = x.lo;
+      return x.hi;
+    };
+    s.x = f3(axis(o3.x, olo3.x, d3.x, s.x_lo.x), axis(o3.y, olo3.y, d3.y, s.x_lo.y),
+             axis(o3.z, olo3.z, d3.z, s.x_lo.z));
+    const DF rr = df_mul(DF{get(A_R), get(A_RL)}, idf);
+    s.r = rr.hi;
+    s.r_lo = rr.lo;
+    const DF mx = df_mul(DF{get(A_NX), get(A_NXL)}, idf), my = df_mul(DF{get(A_NY), get(A_NYL)}, idf),
+             mz = df_mul(DF{get(A_NZ), get(A_NZL)}, idf);
+    const DF n2 = df_add(df_add(df_mul(mx, mx), df_mul(my, my)), df_mul(mz, mz));
+    s.nlen = sqrtf(n2.hi);
+    if (s.nlen < 1e-12f) {
+      s.n = -d3;
+      s.n_lo = f3(0.f, 0.f, 0.f);
+    } else {
+      const DF nl = df_sqrt(n2);
+      const DF nx = df_div(mx, nl), ny = df_div(my, nl), nz = df_div(mz, nl);
+      s.n = f3(nx.hi, ny.hi, nz.hi);
+      s.n_lo = f3(nx.lo, ny.lo, nz.lo);
+    }
+  } else {
     // o + t_ref d as an exact pair (TwoProd, TwoSum), so the position is
     // rounded once, at the end
-    const float tr = get(A_TREF);
     const float wf = W * inv, lo = fmaf(get(A_DT), inv, get(A_TLREF) * wf);
     auto axis = [&](float oc, float oloc, float dc) {
       float p, pe, h, he;
@@ -684,18 +758,20 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
       two_sum(oc, p, h, he);
       return fmaf(wf, h, fmaf(wf, he + pe + oloc, dc * lo));
     };
-    const float3 o = ray.o(), olo = ray.olo(), d = ray.d();
-    s.x = f3(axis(o.x, olo.x, d.x), axis(o.y, olo.y, d.y), axis(o.z, olo.z, d.z));
+    s.x = f3(axis(o3.x, olo3.x, d3.x), axis(o3.y, olo3.y, d3.y), axis(o3.z, olo3.z, d3.z));
+    s.x_lo = f3(0.f, 0.f, 0.f);
+    s.r = get(A_R) * inv;
+    s.r_lo = 0.0f;
+    const float3 mv = f3(get(A_NX), get(A_NY), get(A_NZ)) * inv;
+    s.nlen = sqrtf(dot3(mv, mv));
+    s.n = s.nlen < 1e-12f ? -d3 : mv * (1.0f / s.nlen);
+    s.n_lo = f3(0.f, 0.f, 0.f);
   }
   const float3 Sa = f3(get(A_AX), get(A_AY), get(A_AZ));
   s.depth = get(A_T) * inv;
   s.a = Sa * inv;
   s.Sa = Sa;
   s.m = get(A_M) * inv;
-  s.r = get(A_R) * inv;
-  const float3 mv = f3(get(A_NX), get(A_NY), get(A_NZ)) * inv;
-  s.nlen = sqrtf(dot3(mv, mv));
-  s.n = s.nlen < 1e-12f ? -ray.d() : mv * (1.0f / s.nlen);
   s.hits = hits;
   s.stop_key = ((unsigned long long)__float_as_uint(get(A_SKHI)) << 32) | __float_as_uint(get(A_SKLO));
 }

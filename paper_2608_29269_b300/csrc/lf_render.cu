@@ -31,7 +31,7 @@ __device__ __forceinline__ void trace_pixel(const Grp& g, const CStack& st, cons
   Cnt cnt;
   unsigned comp = 0;
   Surface s;
-  coop_composite<PRIMARY_RAY>(g, insts, n_inst, cam.eye, f3(0.f, 0.f, 0.f), d, P, st, status, cnt, s, comp);
+  coop_composite<PRIMARY_RAY, true>(g, insts, n_inst, cam.eye, f3(0.f, 0.f, 0.f), d, P, st, status, cnt, s, comp);
   if (g.c != 0) return;
   const float3 rho = s.Sa + env_lookup(env, d) * s.T;
   float* gp = gbuf + p;
@@ -50,6 +50,9 @@ __device__ __forceinline__ void trace_pixel(const Grp& g, const CStack& st, cons
   gp[LF_CH_IDSTOP * NP] = s.hits ? (float)(int)(s.stop_key & 0xffffffull) : -1.0f;
   gp[(LF_CH_DIR + 0) * NP] = d.x; gp[(LF_CH_DIR + 1) * NP] = d.y; gp[(LF_CH_DIR + 2) * NP] = d.z;
   gp[LF_CH_STOPKEY_LO * NP] = __uint_as_float((unsigned)(s.stop_key & 0xffffffffull));
+  gp[(LF_CH_X_LO + 0) * NP] = s.x_lo.x; gp[(LF_CH_X_LO + 1) * NP] = s.x_lo.y; gp[(LF_CH_X_LO + 2) * NP] = s.x_lo.z;
+  gp[(LF_CH_N_LO + 0) * NP] = s.n_lo.x; gp[(LF_CH_N_LO + 1) * NP] = s.n_lo.y; gp[(LF_CH_N_LO + 2) * NP] = s.n_lo.z;
+  gp[LF_CH_R_LO * NP] = s.r_lo;
   if (Cnt::on && counters) {  // slot 0 of the per-kernel counters: primary rays
     atomicAdd(counters + 0, (unsigned long long)cnt.nodes);
     atomicAdd(counters + 1, (unsigned long long)cnt.tests);

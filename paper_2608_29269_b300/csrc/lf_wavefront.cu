@@ -72,6 +72,8 @@ struct PixRec {
   int hits;
   float3 x, n, a, d;
   float m, r;
+  float3 n_lo;  // residuals of the normal and roughness (precise record)
+  float r_lo;
 };
 
 __device__ __forceinline__ PixRec pix_record(const ShadeJob& J, int p) {
@@ -86,17 +88,21 @@ __device__ __forceinline__ PixRec pix_record(const ShadeJob& J, int p) {
   q.m = __ldg(g + LF_CH_M * P);
   q.r = __ldg(g + LF_CH_R * P);
   q.d = f3(__ldg(g + LF_CH_DIR * P), __ldg(g + (LF_CH_DIR + 1) * P), __ldg(g + (LF_CH_DIR + 2) * P));
+  q.n_lo = f3(__ldg(g + LF_CH_N_LO * P), __ldg(g + (LF_CH_N_LO + 1) * P), __ldg(g + (LF_CH_N_LO + 2) * P));
+  q.r_lo = __ldg(g + LF_CH_R_LO * P);
   return q;
 }
 
-// x + n off as a double-float hi + lo: the sum of two FP32 values is exact
-// as a pair (the product n off carries ~1e-11), so shading rays start
-// exactly at the stored position plus the offset.
-__device__ __forceinline__ float3 offset_origin(float3 x, float3 n, float off, float3& lo) {
+// (x + xlo) + n off as a double-float hi + lo: the sum of the two FP32
+// values is exact as a pair (the product n off carries ~1e-11), so shading
+// rays start at the record's position (with its residual xlo) plus the
+// offset.
+__device__ __forceinline__ float3 offset_origin(float3 x, float3 xlo, float3 n, float off, float3& lo) {
   float3 hi;
   two_sum(x.x, n.x * off, hi.x, lo.x);
   two_sum(x.y, n.y * off, hi.y, lo.y);
   two_sum(x.z, n.z * off, hi.z, lo.z);
+  lo = lo + xlo;
   return hi;
 }
 
@@ -104,8 +110,9 @@ __device__ __forceinline__ float3 pix_origin(const ShadeJob& J, int p, float off
   const size_t P = (size_t)J.n_pix;
   const float* g = J.gbuf + p;
   const float3 x = f3(__ldg(g + LF_CH_X * P), __ldg(g + (LF_CH_X + 1) * P), __ldg(g + (LF_CH_X + 2) * P));
+  const float3 xlo = f3(__ldg(g + LF_CH_X_LO * P), __ldg(g + (LF_CH_X_LO + 1) * P), __ldg(g + (LF_CH_X_LO + 2) * P));
   const float3 n = f3(__ldg(g + LF_CH_N * P), __ldg(g + (LF_CH_N + 1) * P), __ldg(g + (LF_CH_N + 2) * P));
-  return offset_origin(x, n, off, lo);
+  return offset_origin(x, xlo, n, off, lo);
 }
 
 __device__ __forceinline__ float3 ld3(const float* const* pl, long long i) {
@@ -162,7 +169,7 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
           e_ok = true;
         }
       }
-      wi = (u[2] < ps) ? sample_ggx(n, wo, q.r, u[3], u[4]) : sample_cos(n, u[3], u[4]);
+      wi = sample_bsdf_dir(u[2] < ps, n, q.n_lo, wo, q.r, q.r_lo, u[3], u[4]);
       const float pb = pdf_bsdf(n, wo, wi, q.r, ps);
       if (dot3(n, wi) > 0.0f && pb > 0.0f) {
         const float pei = env_pdf(J.env, wi);
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
       S.T2[item] = s2.T;
       if (s2.hits > 0) {
         float3 lo;
-        st3(S.xs2, item, offset_origin(s2.x, s2.n, P.ray_offset, lo));
+        st3(S.xs2, item, offset_origin(s2.x, s2.x_lo, s2.n, P.ray_offset, lo));
         st3(S.xs2lo, item, lo);
         st3(rec_n2(S), item, s2.n);
         st3(rec_a2(S), item, s2.a);

@@ -22,17 +22,22 @@ OCH = {n: i for i, n in enumerate(oracle.CHANNELS)}
 #  surfel scale.
 FLAG = dict(support=1e-6, alpha=1e-6, tmin=1e-5, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6)
 FLAG_SHADE = dict(support=4e-5, alpha=4e-5, tmin=1e-3, tie=1e-8, stop=2e-5, cos=2e-6, frame=2e-6)
-# Per shading sample: a shading ray starts from the FP32 G-buffer position
-# (within about one rounding of the FP64 composite, ~2.4e-7 in a room of
-# half-size 2) along an FP32 direction (~6e-8), so its support, opacity and
-# depth-order decisions are flagged when a ray shift of SHIFT (the oracle's
-# *_shift margins, a direction change counted as (1 + t) times an origin
-# shift) flips them, and by the relative margins of the primary ray for the
-# FP32 storage of the records.  Also: a uniform within FP32 rounding (2^-24)
-# of an environment CDF entry (FP32 tables may select the neighbouring
-# texel), a continuation direction within 1e-6 rad of a texel edge of the
-# piecewise-constant environment pdf (FP32 directions carry ~1e-7 rad).
-SHIFT = 2.5e-7
+# Per shading sample: a shading ray starts from the record's position with
+# its residual (x + x_lo, within ~3e-10 of the FP64 composite at the median
+# pixel and ~1e-7 at the 99th percentile, where a pixel blends surfaces a
+# distance apart and the FP32 opacities of the weights count) along a
+# direction assembled in FP64 from the record's normal and roughness with
+# their residuals and rounded once to FP32 (measured against the oracle on
+# C2 and C4: 2e-8 rad at the median, 6e-8 at the 99th percentile).  Its
+# support, opacity and depth-order decisions are flagged when a ray shift of
+# SHIFT (the oracle's *_shift margins, a direction change counted as
+# (1 + t) times an origin shift) flips them; on those runs no unflagged
+# sample differed by more than 1e-4 with half this SHIFT either.  Also the
+# relative margins of the primary ray for the FP32 storage of the records; a
+# uniform within FP32 rounding (2^-24) of an environment CDF entry (FP32
+# tables may select the neighbouring texel), a continuation direction within
+# 1e-6 rad of a texel edge of the piecewise-constant environment pdf.
+SHIFT = 1e-7
 FLAG_SAMPLE = dict(support=1e-6, alpha=1e-6, tmin=1e-3, tie=1e-9, stop=2e-5, cos=2e-6, frame=2e-6, cdf=6e-8,
                    ptex=1e-6, support_shift=SHIFT, alpha_shift=SHIFT, tie_shift=SHIFT)
 

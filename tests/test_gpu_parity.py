@@ -98,6 +98,20 @@ def test_c2_one_bounce_parity_on_pixel_subset():
     np.testing.assert_array_equal(gg[~flag_p, 18], o["ch"][~flag_p, OCH["hits"]])
     assert max(errs.values()) <= TOL
     assert_shading(r)
+    # The record's residual planes carry the composite below FP32: x + x_lo,
+    # n + n_lo and r + r_lo stay within ~1e-9 of the oracle's FP64 values at
+    # the median pixel (the FP32 values alone: ~3e-8, one rounding).  The
+    # tail (~1e-7) is set by the FP32 opacities and transmittances of the
+    # weights where a pixel blends surfaces a distance apart.
+    ok = ~flag_p & (o["ch"][:, OCH["hits"]] > 0)
+    for ch, lo, oc, k in [(3, 25, OCH["x0"], 3), (6, 28, OCH["n0"], 3), (13, 31, OCH["r"], 1)]:
+        err_hi = np.abs(gg[ok, ch:ch + k] - o["ch"][ok, oc:oc + k]).max(1)
+        err = np.abs(gg[ok, ch:ch + k] + gg[ok, lo:lo + k] - o["ch"][ok, oc:oc + k]).max(1)
+        print("C2 record residual", ch, "median", np.median(err), "q99", np.quantile(err, 0.99),
+              "FP32 value alone median", np.median(err_hi))
+        assert np.median(err) <= 1e-8
+        assert np.quantile(err, 0.99) <= 2e-7
+        assert np.median(err) <= np.median(err_hi)
 
 
 def test_c4_layout_parity_on_pixel_subset():
@@ -132,14 +146,13 @@ def test_c4_layout_parity_on_pixel_subset():
     print("C4 gbuf errs", errs, "shading", r)
     assert max(errs.values()) <= TOL
     # The shell of this scene holds 4x the surfels per unit area of the
-    # 200k room's, so more shading rays pass within the FP32 error of a
-    # shading ray (about one rounding of a position of magnitude 2-4,
-    # 2.4e-7) of a support edge or a depth tie: about 1.4 % of samples.
-    assert_shading(r, max_flagged=0.015)
+    # 200k room's, so about twice C2's fraction of shading rays pass within
+    # the ray-shift allowance of a support edge or a depth tie (~0.8 %).
+    assert_shading(r)
     # adjoint of a loss on the sampled pixels none of whose decisions is flagged
     ok = ~(flag_p | sample_flags(o).any(1))
     print("C4 gradient pixels", int(ok.sum()), "of", len(pix))
-    assert ok.sum() >= 96  # about (1 - 1.4 %)^64 of the pixels have no flagged sample
+    assert ok.sum() >= 128  # flags cluster in pixels: well over half of them have none
     g_rgb = rng.normal(size=(len(pix), 3)) * ok[:, None]
     d_s, d_e = oracle.grad(ref, cam, envs[env_id], pix, spp, seed, g_rgb)
     full = torch.zeros((cam.height * cam.width, 3), device="cuda")
@@ -260,6 +273,7 @@ def test_wide_bvh_covers_every_leaf_once_and_nests():
 def test_c3_gradient_parity(params):
     """Adjoint vs the oracle's reverse-mode gradient (1e-3 relative), 512 surfels, 32x32, 4 spp."""
     import torch
+    from paper_2608_29269_b300 import _native as N
     full = S.scene_c2(0)
     cam = S.camera_c2(32, 32)
     sc = S.scene_c3_subset(full, cam, 512, seed=0)
@@ -275,7 +289,7 @@ def test_c3_gradient_parity(params):
     g = tr.trace_primary(cam, 0)
     samples = tr.alloc_samples(cam, 4)
     tr.shade(cam, g, 0, spp=4, seed=3, samples=samples)
-    gg = torch.zeros((25, cam.height * cam.width), device="cuda")
+    gg = torch.zeros((N.LF_GBUF_CHANNELS, cam.height * cam.width), device="cuda")
     gg[:17] = torch.as_tensor(g_ch.T, dtype=torch.float32, device="cuda")
     d_surf = torch.zeros((sc.n, 17), device="cuda")
     d_env = torch.zeros((env.height, env.width, 3), device="cuda")

@@ -64,7 +64,7 @@ def test_static_scratch_shading_matches_caller_scratch_twice():
     big = S.Camera((0.0, 0.0, 2.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 40.0, 512, 512)
     cb = camera_struct(big)
     out = torch.empty((512, 512, 3), device="cuda")
-    gb = torch.zeros((25, 512, 512), device="cuda")
+    gb = torch.zeros((N.LF_GBUF_CHANNELS, 512, 512), device="cuda")
     st = lib.lf_shade_bounce_static(tr.ctx, C.byref(cb), C.c_void_p(gb.data_ptr()), 0, 2, C.c_uint64(1),
                                     C.c_void_p(out.data_ptr()), None)
     assert st == N.LF_ERR_INVALID
