@@ -557,22 +557,6 @@ __device__ __forceinline__ float gsum(const Grp& g, float v) {
   for (int off = WIDE / 2; off > 0; off >>= 1) v += __shfl_xor_sync(g.mask, v, off, WIDE);
   return v;
 }
-// Group sum as a double-float: every butterfly step adds the partner's pair
-// by TwoSum, whose error term is the exact rounding error whatever the
-// operand order, so every lane again receives the same bits.
-__device__ __forceinline__ DF gsum_df(const Grp& g, float v) {
-  float h = v, l = 0.0f;
-#pragma unroll
-  for (int off = WIDE / 2; off > 0; off >>= 1) {
-    const float oh = __shfl_xor_sync(g.mask, h, off, WIDE), ol = __shfl_xor_sync(g.mask, l, off, WIDE);
-    float sh, e;
-    two_sum(h, oh, sh, e);
-    l = __fadd_rn(__fadd_rn(l, ol), e);
-    h = sh;
-  }
-  return df_renorm(h, l);
-}
-
 // Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop),
 // cooperative: each round collects the K nearest hits beyond the last
 // round's, then composites them front to back in parallel -- transmittance
@@ -580,14 +564,16 @@ __device__ __forceinline__ DF gsum_df(const Grp& g, float v) {
 // first hit whose transmittance behind it falls below T_min, weighted sums by
 // butterflies.  Every lane ends with the same Surface.
 //
+// Normal and roughness are summed, like the position, as offsets from the
+// first composited hit's (n_ref, r_ref): sum w n_j = W n_ref + sum w (n_j -
+// n_ref), so the FP32 sums carry small terms (exactly 0 on a flat wall)
+// and their rounding no longer scales with n and r themselves.
+//
 // Precise (the primary record, from which shading rays start and BSDF
-// samples are drawn): the sums of w, w r and w n are double-floats, and x,
-// n and r are formed from them in double-float and returned as FP32 values
-// plus their residuals (x_lo, n_lo, r_lo), so the record carries about one
-// rounding of the FP64 composite instead of the FP32 butterflies' and
-// divisions' (up to ~3e-7 relative in r and n, and W / (W + eps) within an
-// ulp of 1 moved x by up to ~2e-7 in a room of half-size 2).  Otherwise the
-// residuals are 0.
+// samples are drawn): x, n and r are assembled from the pairs and offsets
+// in double-float (W / (W + eps) too, which in FP32 can land an ulp below 1
+// and move x by up to ~2e-7) and returned as FP32 values plus their
+// residuals (x_lo, n_lo, r_lo).  Otherwise the residuals are 0.
 template <class Ray, bool Precise = false, class Cnt>
 __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, int n_inst, float3 o, float3 olo,
                                                float3 d,
@@ -613,7 +599,7 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   // registers for them instead of fifteen or more.
   enum {
     A_W, A_DT, A_T, A_NX, A_NY, A_NZ, A_AX, A_AY, A_AZ, A_M, A_R, A_TREF, A_TLREF, A_HITS, A_SKLO, A_SKHI,
-    A_WL, A_NXL, A_NYL, A_NZL, A_RL, NACC  // the low words of the double-float sums (Precise)
+    A_NXR, A_NYR, A_NZR, A_RR, NACC  // n_ref, r_ref
   };
   constexpr int NSLOT = (NACC + WIDE - 1) / WIDE;
   float acc[NSLOT];
@@ -626,12 +612,7 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     if (g.c == k % WIDE) acc[k / WIDE] = v;
   };
   auto get = [&](int k) { return gshfl(g, acc[k / WIDE], k % WIDE); };
-  auto add_df = [&](int khi, int klo, DF v) {  // acc pair (khi, klo) += v
-    const DF sum = df_add(DF{get(khi), get(klo)}, v);
-    put(khi, sum.hi);
-    put(klo, sum.lo);
-  };
-  float T = 1.0f, t_ref = 0.0f;
+  float T = 1.0f;
   unsigned long long last = 0ull;
   bool done = false;
   for (int round = 0; round < P.max_rounds && !done; ++round) {
@@ -671,24 +652,30 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     const unsigned stopm = gballot(g, have && Ta < P.T_min);
     const int lastc = stopm ? __ffs(stopm) - 1 : n - 1;
     const float w = (have && g.c <= lastc) ? Tb * alpha : 0.0f;
+    // the references: the first composited hit's (read back in later
+    // rounds rather than kept in registers across the walk)
+    float t_ref, r_ref;
+    float3 n_ref;
     if (round == 0) {
       t_ref = gshfl(g, t, 0);
+      n_ref = f3(gshfl(g, nj.x, 0), gshfl(g, nj.y, 0), gshfl(g, nj.z, 0));
+      r_ref = gshfl(g, rgh, 0);
       put(A_TREF, t_ref);
       put(A_TLREF, key_tl(gshfl(g, kb.bk, 0)));
-    }
-    if constexpr (Precise) {
-      add_df(A_W, A_WL, gsum_df(g, w));
-      add_df(A_NX, A_NXL, gsum_df(g, w * nj.x));
-      add_df(A_NY, A_NYL, gsum_df(g, w * nj.y));
-      add_df(A_NZ, A_NZL, gsum_df(g, w * nj.z));
-      add_df(A_R, A_RL, gsum_df(g, w * rgh));
+      put(A_NXR, n_ref.x);
+      put(A_NYR, n_ref.y);
+      put(A_NZR, n_ref.z);
+      put(A_RR, r_ref);
     } else {
-      add(A_W, gsum(g, w));
-      add(A_NX, gsum(g, w * nj.x));
-      add(A_NY, gsum(g, w * nj.y));
-      add(A_NZ, gsum(g, w * nj.z));
-      add(A_R, gsum(g, w * rgh));
+      t_ref = get(A_TREF);
+      n_ref = f3(get(A_NXR), get(A_NYR), get(A_NZR));
+      r_ref = get(A_RR);
     }
+    add(A_W, gsum(g, w));
+    add(A_NX, gsum(g, w * (nj.x - n_ref.x)));
+    add(A_NY, gsum(g, w * (nj.y - n_ref.y)));
+    add(A_NZ, gsum(g, w * (nj.z - n_ref.z)));
+    add(A_R, gsum(g, w * (rgh - r_ref)));
     add(A_DT, gsum(g, w * (t - t_ref)));
     add(A_T, gsum(g, w * t));
     add(A_AX, gsum(g, w * alb.x));
@@ -704,7 +691,6 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     if (!done) {
       last = kb.kmax;
       if (round == P.max_rounds - 1 && g.c == 0) report(status, LF_ERR_ROUND_LIMIT);
-      t_ref = get(A_TREF);
     }
   }
   const int hits = (int)get(A_HITS);
@@ -715,10 +701,15 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
   s.W = W;
   const float tr = get(A_TREF);
   const float3 o3 = ray.o(), olo3 = ray.olo(), d3 = ray.d();
+  const float3 nr = f3(get(A_NXR), get(A_NYR), get(A_NZR));
+  const float rref = get(A_RR);
+  const float3 Sn = f3(get(A_NX), get(A_NY), get(A_NZ));  // sum w (n_j - n_ref)
   if constexpr (Precise) {
-    const DF den = df_add(DF{get(A_W), get(A_WL)}, DF{P.eps_w, 0.0f});
-    const DF idf = df_div(DF{1.0f, 0.0f}, den);
-    const DF wf = df_mul(DF{get(A_W), get(A_WL)}, idf);
+    // W / (W + eps) = 1 - eps / (W + eps) as a pair (the FP32 error of W only
+    // moves the tiny second term)
+    const float ew = P.eps_w / (W + P.eps_w);
+    DF wf;
+    two_sum(1.0f, -ew, wf.hi, wf.lo);
     const float lo = fmaf(get(A_DT), inv, get(A_TLREF) * wf.hi);
     // o + olo + t_ref d as h + (he + pe + olo), exact to ~1e-15 relative,
     // times W / (W + eps), plus the small offset along d
@@ -732,21 +723,29 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     };
     s.x = f3(axis(o3.x, olo3.x, d3.x, s.x_lo.x), axis(o3.y, olo3.y, d3.y, s.x_lo.y),
              axis(o3.z, olo3.z, d3.z, s.x_lo.z));
-    const DF rr = df_mul(DF{get(A_R), get(A_RL)}, idf);
+    // r = r_ref W / (W + eps) + sum w (r_j - r_ref) / (W + eps)
+    const DF rr = df_add(df_mul(DF{rref, 0.0f}, wf), DF{get(A_R) * inv, 0.0f});
     s.r = rr.hi;
     s.r_lo = rr.lo;
-    const DF mx = df_mul(DF{get(A_NX), get(A_NXL)}, idf), my = df_mul(DF{get(A_NY), get(A_NYL)}, idf),
-             mz = df_mul(DF{get(A_NZ), get(A_NZL)}, idf);
-    const DF n2 = df_add(df_add(df_mul(mx, mx), df_mul(my, my)), df_mul(mz, mz));
-    s.nlen = sqrtf(n2.hi);
-    if (s.nlen < 1e-12f) {
-      s.n = -d3;
-      s.n_lo = f3(0.f, 0.f, 0.f);
-    } else {
-      const DF nl = df_sqrt(n2);
-      const DF nx = df_div(mx, nl), ny = df_div(my, nl), nz = df_div(mz, nl);
+    // n = v / |v| with v = n_ref + sum w (n_j - n_ref) / W
+    if (W > 0.0f) {
+      const float iw = 1.0f / W;
+      DF vx, vy, vz;
+      two_sum(nr.x, Sn.x * iw, vx.hi, vx.lo);
+      two_sum(nr.y, Sn.y * iw, vy.hi, vy.lo);
+      two_sum(nr.z, Sn.z * iw, vz.hi, vz.lo);
+      const DF v2 = df_add(df_add(df_mul(vx, vx), df_mul(vy, vy)), df_mul(vz, vz));
+      const DF vl = df_sqrt(v2);
+      s.nlen = vl.hi * wf.hi;
+      const DF nx = df_div(vx, vl), ny = df_div(vy, vl), nz = df_div(vz, vl);
       s.n = f3(nx.hi, ny.hi, nz.hi);
       s.n_lo = f3(nx.lo, ny.lo, nz.lo);
+    } else {
+      s.nlen = 0.0f;
+    }
+    if (!(s.nlen >= 1e-12f)) {
+      s.n = -d3;
+      s.n_lo = f3(0.f, 0.f, 0.f);
     }
   } else {
     // o + t_ref d as an exact pair (TwoProd, TwoSum), so the position is
@@ -760,9 +759,9 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
     };
     s.x = f3(axis(o3.x, olo3.x, d3.x), axis(o3.y, olo3.y, d3.y), axis(o3.z, olo3.z, d3.z));
     s.x_lo = f3(0.f, 0.f, 0.f);
-    s.r = get(A_R) * inv;
+    s.r = fmaf(rref, wf, get(A_R) * inv);
     s.r_lo = 0.0f;
-    const float3 mv = f3(get(A_NX), get(A_NY), get(A_NZ)) * inv;
+    const float3 mv = nr * wf + Sn * inv;
     s.nlen = sqrtf(dot3(mv, mv));
     s.n = s.nlen < 1e-12f ? -d3 : mv * (1.0f / s.nlen);
     s.n_lo = f3(0.f, 0.f, 0.f);
