@@ -561,7 +561,8 @@ def main():
     # samples), secondary shadow 32 B, adjoint 136 B per pixel (25 G-buffer and
     # 9 shading-gradient floats).  The wide-node layout actually reads all 32
     # child slots of a node (lf_bvh_wide_node_bytes per visit) and 80 B per
-    # composited hit; that accounting is kept beside it.
+    # composited hit, and a primary ray writes all 32 G-buffer planes (the
+    # residuals included); that accounting is kept beside it.
     unit = {"node": 64, "test": 48, "hit": 32, "grad_atomics": 68}
     per_ray_io = {"primary": 88, "nee_shadow": 44, "continuation": 112, "secondary_shadow": 32,
                   "trace_backward": 136}
@@ -569,7 +570,7 @@ def main():
     kbytes = {n: unit["node"] * counters[n][0] + unit["test"] * counters[n][1] + hit_cost[n] * counters[n][2] +
               per_ray_io[n] * counters[n][3] for n in per_ray_io}
     wnode = step.tr.lib.lf_bvh_wide_node_bytes()
-    wide_io = dict(per_ray_io, primary=148)
+    wide_io = dict(per_ray_io, primary=4 * 32)
     wide_hit = {n: (196 if n == "trace_backward" else 80) for n in per_ray_io}
     kbytes_wide = {n: wnode * counters[n][0] + 48 * counters[n][1] + wide_hit[n] * counters[n][2] +
                    wide_io[n] * counters[n][3] for n in per_ray_io}
