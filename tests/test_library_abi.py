@@ -76,3 +76,23 @@ def test_product_path_fails_loudly_without_extension(tmp_path):
             _native.load(str(tmp_path / "missing.so"))
     finally:
         _native._lib = saved
+
+
+def test_gbuffer_channels_agree_with_header():
+    """The binding's G-buffer plane indices and count are the header's enum."""
+    from paper_2608_29269_b300 import _native as N
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"\b(LF_CH_[A-Z_]+|LF_GBUF_[A-Z]+)\s*=\s*(\d+)", text)}
+    assert enum["LF_GBUF_CHANNELS"] == N.LF_GBUF_CHANNELS
+    assert enum["LF_GBUF_DIFF"] == N.LF_GBUF_DIFF
+    names = dict(T="LF_CH_T", W="LF_CH_W", depth="LF_CH_DEPTH", x="LF_CH_X", n="LF_CH_N", a="LF_CH_A",
+                 m="LF_CH_M", r="LF_CH_R", rho="LF_CH_RHO", nlen="LF_CH_NLEN", hits="LF_CH_HITS",
+                 t_stop="LF_CH_TSTOP", id_stop="LF_CH_IDSTOP", dir="LF_CH_DIR", stopkey_lo="LF_CH_STOPKEY_LO",
+                 x_lo="LF_CH_X_LO", n_lo="LF_CH_N_LO", r_lo="LF_CH_R_LO")
+    assert set(names) == set(N.CH)
+    for k, h in names.items():
+        assert N.CH[k] == enum[h], k
+    # planes are disjoint and fill the buffer
+    width = dict(x=3, n=3, a=3, rho=3, dir=3, x_lo=3, n_lo=3)
+    used = sorted(c for k, c0 in N.CH.items() for c in range(c0, c0 + width.get(k, 1)))
+    assert used == list(range(N.LF_GBUF_CHANNELS))
