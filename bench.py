@@ -589,6 +589,18 @@ def main():
           "achieved": l2_bytes / (kavg[dom] * 1e-3) / 1e9 if l2_bytes else None,
           "frac": l2_bytes / (kavg[dom] * 1e-3) / 1e9 / l2_peak if l2_bytes else None,
           "algorithmic_frac": achieved / l2_peak}
+    # the trace kernels are bound by instruction issue: warp instructions of
+    # the same kernel (ncu smsp__inst_executed, scaled per ray) against the
+    # issue rate of the SMs, one warp instruction per cycle per scheduler
+    # (148 SMs x 4 schedulers) at the SM clock sampled under load
+    insts = read_traffic(KERNEL_NAMES[dom], "warp_inst_per_launch")
+    sm_mhz = (clk or {}).get("sm_mhz") or 2032.0
+    issue_peak = 148 * 4 * sm_mhz * 1e6
+    issue = {"peak": issue_peak, "unit": "warp instructions/s",
+             "peak_kind": f"148 SMs x 4 schedulers x 1 warp instruction/cycle at {sm_mhz:.0f} MHz",
+             "inst_per_launch": insts, "inst_kind": "ncu smsp__inst_executed.sum of the same kernel, scaled per ray",
+             "achieved": insts / (kavg[dom] * 1e-3) if insts else None,
+             "frac": insts / (kavg[dom] * 1e-3) / issue_peak if insts else None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -603,7 +615,7 @@ def main():
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy (burst)", "traffic": traffic,
                      "traffic_kind": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch",
                      "algorithmic_bytes_per_launch": kbytes[dom], "unit_costs": dict(unit, io_per_ray=per_ray_io),
-                     "launch_ms": kavg[dom], "l2": l2,
+                     "launch_ms": kavg[dom], "l2": l2, "issue": issue,
                      "wide_node_accounting": {"bytes_per_launch": kbytes_wide[dom], "node_bytes": wnode,
                                               "achieved": kbytes_wide[dom] / (kavg[dom] * 1e-3) / 1e9}},
         "kernels": kernels,
