@@ -257,7 +257,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": dict(workload(args.size, args.spp), sample_pixels=len(pix)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": probe["threads"], "kind": "oracle",
-                             "sample": f"{len(pix)} seeded pixels of the 800x800 frame, 16 spp, fwd + gradient"},
+                             "sample": f"{len(pix)} seeded pixels of the {cam.width}x{cam.height} frame, "
+                                       f"{args.spp} spp, fwd + gradient per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
