@@ -567,6 +567,27 @@ __device__ __forceinline__ float gsum(const Grp& g, float v) {
   for (int off = WIDE / 2; off > 0; off >>= 1) v += __shfl_xor_sync(g.mask, v, off, WIDE);
   return v;
 }
+// Sixteen sums over the 32 lanes of a warp at once (a recursive-halving
+// reduce-scatter): at offsets 8, 4, 2, 1 each lane keeps the half of its
+// values whose index bit matches its own lane bit and adds its partner's
+// copy of that half, then one butterfly at offset 16 completes the sums, so
+// lanes k and k + 16 end with the sum of v[k]: 16 shuffles, 16 adds and 30
+// selects for sixteen sums instead of 80 shuffles and 80 adds.  Lanes k and
+// k + 16 add the same two partial sums, so they hold the same bits.
+__device__ __forceinline__ float gsum_transposed(const Grp& g, float (&v)[16]) {
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (g.c & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(g.mask, send, o, WIDE);
+    }
+  }
+  return v[0] + __shfl_xor_sync(g.mask, v[0], 16, WIDE);
+}
+
 // Multi-round k-buffer composite of one ray (Eq. 6-7 with the early stop),
 // cooperative: each round collects the K nearest hits beyond the last
 // round's, then composites them front to back in parallel -- transmittance
@@ -681,17 +702,28 @@ __device__ __forceinline__ void coop_composite(const Grp& g, const Inst* insts, 
       n_ref = f3(get(A_NXR), get(A_NYR), get(A_NZR));
       r_ref = get(A_RR);
     }
-    add(A_W, gsum(g, w));
-    add(A_NX, gsum(g, w * (nj.x - n_ref.x)));
-    add(A_NY, gsum(g, w * (nj.y - n_ref.y)));
-    add(A_NZ, gsum(g, w * (nj.z - n_ref.z)));
-    add(A_R, gsum(g, w * (rgh - r_ref)));
-    add(A_DT, gsum(g, w * (t - t_ref)));
-    add(A_T, gsum(g, w * t));
-    add(A_AX, gsum(g, w * alb.x));
-    add(A_AY, gsum(g, w * alb.y));
-    add(A_AZ, gsum(g, w * alb.z));
-    add(A_M, gsum(g, w * mtl));
+    if constexpr (WIDE == 32) {
+      // the eleven sums at once, ending in lane k = the sum's slot
+      float v[16] = {w, w * (t - t_ref), w * t, w * (nj.x - n_ref.x), w * (nj.y - n_ref.y), w * (nj.z - n_ref.z),
+                     w * alb.x, w * alb.y, w * alb.z, w * mtl, w * (rgh - r_ref), 0.f, 0.f, 0.f, 0.f, 0.f};
+      static_assert(A_W == 0 && A_DT == 1 && A_T == 2 && A_NX == 3 && A_NY == 4 && A_NZ == 5 && A_AX == 6 &&
+                        A_AY == 7 && A_AZ == 8 && A_M == 9 && A_R == 10,
+                    "the transposed sums land in slots 0..10");
+      const float sum = gsum_transposed(g, v);
+      if (g.c <= A_R) acc[0] += sum;
+    } else {
+      add(A_W, gsum(g, w));
+      add(A_NX, gsum(g, w * (nj.x - n_ref.x)));
+      add(A_NY, gsum(g, w * (nj.y - n_ref.y)));
+      add(A_NZ, gsum(g, w * (nj.z - n_ref.z)));
+      add(A_R, gsum(g, w * (rgh - r_ref)));
+      add(A_DT, gsum(g, w * (t - t_ref)));
+      add(A_T, gsum(g, w * t));
+      add(A_AX, gsum(g, w * alb.x));
+      add(A_AY, gsum(g, w * alb.y));
+      add(A_AZ, gsum(g, w * alb.z));
+      add(A_M, gsum(g, w * mtl));
+    }
     T = gshfl(g, Ta, lastc);
     add(A_HITS, (float)(lastc + 1));
     const unsigned long long sk = gshfl(g, kb.bk, lastc);
