@@ -150,6 +150,8 @@ __global__ void __launch_bounds__(TB, BACKWARD_MIN_BLOCKS) k_trace_backward(Trac
   bool inclusive = true;
   FarKCoop kb;
   kb.P = Pm;
+  kb.mk = st.mk;
+  kb.mc = st.mc;
   const auto ray = make_ray<BACKWARD_RAY>(st.ray, g.c, g.mask, o, d);
   Cnt cnt;
   unsigned adj = 0;  // hits whose gradient this ray scatters

@@ -498,6 +498,8 @@ struct FarKCoop {
   unsigned long long kmin;  // smallest held key once full
   float ktl;                // key_t(kmin) once full, else t_min
   DevParams P;
+  unsigned long long* mk;   // merge scratch in shared memory (WIDE entries per ray)
+  int* mc;
 
   __device__ __forceinline__ void reset(unsigned long long b, bool incl) {
     bk = 0ull;
@@ -534,29 +536,50 @@ struct FarKCoop {
         }
       }
     }
-    unsigned m = gballot(g, valid);
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1u;
-      const unsigned long long k = gshfl(g, key, src);
-      const int cd = gshfl(g, code, src);
-      if (cnt >= WIDE && k <= kmin) continue;
-      const unsigned long long pk = __shfl_up_sync(g.mask, bk, 1, WIDE);
-      const int pc = __shfl_up_sync(g.mask, bc, 1, WIDE);
-      if (bk < k) {
-        if (g.c == 0 || pk > k) {
-          bk = k;
-          bc = cd;
-        } else {
-          bk = pk;
-          bc = pc;
-        }
-      }
-      cnt = min(cnt + 1, WIDE);
-      if (cnt >= WIDE) {
-        kmin = gshfl(g, bk, WIDE - 1);
-        ktl = fmaxf(P.t_min, key_t(kmin));
-      }
+    merge(g, valid, key, code);
+  }
+  // The leaf's accepted hits merged into the descending buffer in one step,
+  // as NearKCoop::merge does it ascending: each element's place is its own
+  // index plus the number of larger elements of the other list (keys are
+  // distinct, so bk < kj is the complement of this lane's bit of the ballot
+  // bk > kj; two candidates per pass), scattered through shared memory;
+  // places beyond K fall off.  The buffer ends as the K largest keys of
+  // both, in order -- what inserting the candidates one by one gave.
+  __device__ __forceinline__ void merge(const Grp& g, bool valid, unsigned long long key, int code) {
+    const unsigned m = gballot(g, valid);
+    if (m == 0u) return;
+    int bshift = 0, cshift = 0, rb = 0;
+    unsigned mm = m;
+    while (mm) {
+      const int j0 = __ffs(mm) - 1;
+      mm &= mm - 1u;
+      const int j1 = mm ? __ffs(mm) - 1 : j0;
+      const bool two = mm != 0u;
+      mm &= mm - 1u;
+      const unsigned long long k0 = gshfl(g, key, j0), k1 = gshfl(g, key, j1);
+      const unsigned b0 = gballot(g, bk > k0), b1 = gballot(g, bk > k1);
+      if (g.c == j0) rb = __popc(b0);
+      if (two && g.c == j1) rb = __popc(b1);
+      bshift += (int)(((b0 >> g.c) & 1u) ^ 1u) + (two ? (int)(((b1 >> g.c) & 1u) ^ 1u) : 0);
+      cshift += ((valid && key < k0) ? 1 : 0) + ((two && valid && key < k1) ? 1 : 0);
+    }
+    const int db = g.c + bshift, dc = rb + cshift;
+    if (db < WIDE) {
+      mk[db] = bk;
+      mc[db] = bc;
+    }
+    if (valid && dc < WIDE) {
+      mk[dc] = key;
+      mc[dc] = code;
+    }
+    __syncwarp(g.mask);
+    bk = mk[g.c];
+    bc = mc[g.c];
+    __syncwarp(g.mask);
+    cnt = min(cnt + __popc(m), WIDE);
+    if (cnt >= WIDE) {
+      kmin = gshfl(g, bk, WIDE - 1);
+      ktl = fmaxf(P.t_min, key_t(kmin));
     }
   }
 };
