@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(TB, BACKWARD_MIN_BLOCKS) k_trace_backward(Trac
   kb.P = Pm;
   kb.mk = st.mk;
   kb.mc = st.mc;
+  kb.insts = a.insts;
+  kb.qc = st.qc;
   const auto ray = make_ray<BACKWARD_RAY>(st.ray, g.c, g.mask, o, d);
   Cnt cnt;
   unsigned adj = 0;  // hits whose gradient this ray scatters

@@ -353,6 +353,12 @@ struct NearKCoop {
   }
   __device__ __forceinline__ float tlo() const { return fmaxf(P.t_min, key_t(last)); }
   __device__ __forceinline__ float thi() const { return tcut; }
+  // quick-test window: beyond the far bound, or in front of the last round's
+  // largest key (later rounds re-walk the same leaves), with the margins of
+  // the quick test, no candidate can enter
+  __device__ __forceinline__ bool in_window(float t32) const {
+    return !(t32 > tcut * 1.0001f + 1e-6f) && !(t32 < key_t(last) * 0.9999f - 1e-6f);
+  }
   __device__ __forceinline__ bool done() const { return false; }
   __device__ __forceinline__ void abort() {
     cnt = 0;
@@ -451,7 +457,7 @@ struct NearKCoop {
       Rec r;
       load_rec3(I.geo, I.n_leaves, first + g.c, r);
       float t32;
-      cand = hit_quick(r, ray.o(), ray.d(), P, t32) && !(t32 > tcut * 1.0001f + 1e-6f);
+      cand = hit_quick(r, ray.o(), ray.d(), P, t32) && in_window(t32);
     }
     const int nm = __popc(gballot(g, cand));
     if (nm == 0) return;
@@ -475,7 +481,7 @@ struct NearKCoop {
       Rec r;
       load_rec3(I.geo, I.n_leaves, l, r);
       float t32;
-      if (hit_quick(r, ray.o(), ray.d(), P, t32) && !(t32 > tcut * 1.0001f + 1e-6f))
+      if (hit_quick(r, ray.o(), ray.d(), P, t32) && in_window(t32))
         valid = precise(ray, I, ii, l, r, key, code, alpha);
     }
     merge(g, valid, key, code, alpha);
@@ -509,11 +515,72 @@ struct FarKCoop {
     inclusive = incl;
     kmin = 0ull;
     ktl = P.t_min;
+    qn = 0;
   }
   __device__ __forceinline__ float tlo() const { return ktl; }
   __device__ __forceinline__ float thi() const { return key_t(bound); }
   __device__ __forceinline__ bool done() const { return false; }
-  __device__ __forceinline__ void abort() { cnt = 0; }
+  __device__ __forceinline__ void abort() {
+    cnt = 0;
+    qn = 0;
+  }
+  // Precise test of record l of instance ii (its first three quads in r).
+  template <class Ray>
+  __device__ __forceinline__ bool precise(const Ray& ray, const Inst& I, int ii, int l, Rec& r,
+                                          unsigned long long& key, int& code) const {
+    float t, tl, alpha;
+    load_rec_tail(I.geo, I.n_leaves, l, r);
+    if (!hit_precise(r, ray.o(), ray.olo(), ray.d(), P, t, tl, alpha)) return false;
+    key = hit_key(t, tl, rec_id(r));
+    code = (ii << 24) | l;
+    return (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
+  }
+  // quick-test window: beyond the bound or, once full, in front of kmin's
+  // depth (with the margins of the quick test) no candidate can enter
+  __device__ __forceinline__ bool in_window(float t32) const {
+    return !(t32 > thi() * 1.0001f + 1e-6f) && !(cnt >= WIDE && t32 < ktl * 0.9999f - 1e-6f);
+  }
+  const Inst* insts;
+  int* qc;  // candidate queue (LF_DEFER > 0)
+  int qn;
+#if LF_DEFER > 0
+  template <class Ray>
+  __device__ __forceinline__ void flush(const Grp& g, const Ray& ray) {
+    bool valid = false;
+    unsigned long long key = 0ull;
+    int code = 0;
+    if (g.c < qn) {
+      const int qcode = qc[g.c];
+      const int ii = qcode >> 24, l = qcode & 0xffffff;
+      const Inst& I = insts[ii];
+      Rec r;
+      load_rec3(I.geo, I.n_leaves, l, r);
+      valid = precise(ray, I, ii, l, r, key, code);
+    }
+    qn = 0;
+    __syncwarp(g.mask);
+    merge(g, valid, key, code);
+  }
+  template <class Ray>
+  __device__ __forceinline__ void leaf(const Grp& g, const Ray& ray, int ii, int first, int count, const Inst& I) {
+    bool cand = false;
+    if (g.c < count) {
+      Rec r;
+      load_rec3(I.geo, I.n_leaves, first + g.c, r);
+      float t32;
+      cand = hit_quick(r, ray.o(), ray.d(), P, t32) && in_window(t32);
+    }
+    const int nm = __popc(gballot(g, cand));
+    if (nm == 0) return;
+    if (qn + nm > WIDE) flush(g, ray);
+    queue_candidates(g, qc, qn, cand, (ii << 24) | (first + g.c));
+    if (qn >= LF_DEFER) flush(g, ray);
+  }
+  template <class Ray>
+  __device__ __forceinline__ void finish(const Grp& g, const Ray& ray) {
+    if (qn > 0) flush(g, ray);
+  }
+#else
   template <class Ray>
   __device__ __forceinline__ void finish(const Grp&, const Ray&) {}
   template <class Ray>
@@ -526,18 +593,11 @@ struct FarKCoop {
       Rec r;
       load_rec3(I.geo, I.n_leaves, l, r);
       float t32;
-      if (hit_quick(r, ray.o(), ray.d(), P, t32) && !(t32 > thi() * 1.0001f + 1e-6f)) {
-        float t, tl, alpha;
-        load_rec_tail(I.geo, I.n_leaves, l, r);
-        if (hit_precise(r, ray.o(), ray.olo(), ray.d(), P, t, tl, alpha)) {
-          key = hit_key(t, tl, rec_id(r));
-          valid = (key < bound || (key == bound && inclusive)) && (cnt < WIDE || key > kmin);
-          code = (ii << 24) | l;
-        }
-      }
+      if (hit_quick(r, ray.o(), ray.d(), P, t32) && in_window(t32)) valid = precise(ray, I, ii, l, r, key, code);
     }
     merge(g, valid, key, code);
   }
+#endif
   // The leaf's accepted hits merged into the descending buffer in one step,
   // as NearKCoop::merge does it ascending: each element's place is its own
   // index plus the number of larger elements of the other list (keys are
