@@ -49,6 +49,12 @@ constexpr int WB = 128;  // threads per block of the wavefront kernels
 // the three trace kernels (4-6).
 constexpr int CURSOR_A = 4, CURSOR_B = 5, CURSOR_C = 6, N_COUNTS = 8;
 
+// A sample's pixel and index within its job from its offset in the job
+// (under 2^30: the entry points refuse larger sample counts), by a 32-bit
+// division instead of a 64-bit one.
+__device__ __forceinline__ int pixel_of(long long loc, int spp) { return (int)((unsigned)loc / (unsigned)spp); }
+__device__ __forceinline__ int sample_of(long long loc, int spp) { return (int)((unsigned)loc % (unsigned)spp); }
+
 __device__ __forceinline__ int job_of_item(const ShadeBatch& B, long long item) {
   int lo = 0, hi = B.n_jobs - 1;
   while (lo < hi) {
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(WB) k_wf_gen(ShadeBatch B, DevParams P, Sample
     if (i < B.n_items) {
     const ShadeJob& J = B.jobs[job_of_item(B, i)];
     const long long loc = i - J.item0;
-    const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+    const int p = pixel_of(loc, J.spp), s = sample_of(loc, J.spp);
     const PixRec q = pix_record(J, p);
     const float3 wo = -q.d, n = q.n;
     const float ps = P.brdf_mode == 1 ? 0.0f : P.p_spec;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_SHADOW) k_wf_shadow(ShadeBat
     float3 o, olo, d;
     if (which == 0) {
       const long long loc = item - J.item0;
-      o = pix_origin(J, (int)(loc / J.spp), P.ray_offset, olo);
+      o = pix_origin(J, pixel_of(loc, J.spp), P.ray_offset, olo);
       d = ld3(S.we, item);
     } else {
       o = ld3(S.xs2, item);
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(WB, WF_MIN_BLOCKS_CONTINUE) k_wf_continue(Shad
     const ShadeJob& J = B.jobs[job_of_item(B, item)];
     const long long loc = item - J.item0;
     float3 xslo;
-    const float3 xs = pix_origin(J, (int)(loc / J.spp), P.ray_offset, xslo);
+    const float3 xs = pix_origin(J, pixel_of(loc, J.spp), P.ray_offset, xslo);
     const float3 wi = ld3(S.wi, item);
     Surface s2;
     coop_composite<WF_CONTINUE_RAY>(g, J.insts, J.n_inst, xs, xslo, wi, P, st, status, cnt, s2, comp);
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(WB) k_wf_secondary(ShadeBatch B, DevParams P, 
       if (T2 < 1.0f) {
         const ShadeJob& J = B.jobs[job_of_item(B, item)];
         const long long loc = item - J.item0;
-        const int p = (int)(loc / J.spp), s = (int)(loc % J.spp);
+        const int p = pixel_of(loc, J.spp), s = sample_of(loc, J.spp);
         const float3 n2 = ld3(rec_n2(S), item), a2 = ld3(rec_a2(S), item);
         const float m2 = rec_m2(S)[item], r2 = rec_r2(S)[item];
         const float3 wo2 = -ld3(S.wi, item);
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(WB) k_wf_terms(ShadeBatch B, DevParams P, Samp
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < B.n_items;
        i += (long long)gridDim.x * blockDim.x) {
     const ShadeJob& J = B.jobs[job_of_item(B, i)];
-    const int p = (int)((i - J.item0) / J.spp);
+    const int p = pixel_of(i - J.item0, J.spp);
     const PixRec q = pix_record(J, p);
     float3 c = f3(0.f, 0.f, 0.f);
     if (q.hits > 0 && dot3(q.n, -q.d) > 0.0f) {
