@@ -589,68 +589,64 @@ __device__ __forceinline__ void brdf_adjoint(float3 n, float3 wo, float3 wi, flo
 }
 
 // ------------------------------------------------------------------ sampling
-// 1 / x and sqrt(x) in FP64 from FP32 seeds and one Newton step in the FMA
-// form (Markstein 1990): the seed's relative error e (~1e-7) leaves ~e^2,
-// without FP64 division or square root (slow on this part).
-__device__ __forceinline__ double rcp64(double x) {
-  const double r0 = (double)(1.0f / (float)x);
-  return fma(r0, fma(-x, r0, 1.0), r0);
-}
-__device__ __forceinline__ double sqrt64(double x) {  // x >= 0
-  const float xf = (float)x;
-  if (!(xf > 0.0f)) return 0.0;
-  const double s0 = (double)sqrtf(xf);
-  return fma(fma(-s0, s0, x), (double)(0.5f / (float)s0), s0);
-}
-
 // BSDF sample direction: the cosine lobe (Malley's method) or, when `spec`,
 // the mirrored GGX half vector with density D(h)(n.h) (Walter et al. 2007).
 // The local direction, the frame (b1, b2, n) after Duff et al. 2017 of the
 // record's normal with its residual (n + nlo) and the reflection are
-// assembled in FP64 from the FP32 inputs (roughness r + rlo) and rounded
-// once, so the FP32 rounding of the result (~5e-8 rad) is about its only
-// error; in FP32 the frame and the reflection 2 (wo.h) h - wo (which doubles
-// the rounding errors of h and of the roughness) gave up to 6e-7 rad at
-// roughness 0.7, enough to flip a support decision of a glossy metal's
-// continuation ray.  The azimuth is sincospif's (one ulp, ~6e-8).  One code
-// path for both lobes, so a warp whose samples pick both pays for the FP64
-// assembly once.
+// assembled in double-float arithmetic (the DF operations above, ~1e-14)
+// from the FP32 inputs (roughness r + rlo) and rounded once, so the FP32
+// rounding of the result (~5e-8 rad) is about its only error; in FP32 the
+// frame and the reflection 2 (wo.h) h - wo (which doubles the rounding
+// errors of h and of the roughness) gave up to 6e-7 rad at roughness 0.7,
+// enough to flip a support decision of a glossy metal's continuation ray.
+// Double-float rather than FP64 because FP64 runs at a small fraction of
+// the FP32 rate on this part: sample generation 1.70 -> 0.68 ms at the same
+// accuracy.  The azimuth is sincospif's (one ulp, ~6e-8).  One code path for
+// both lobes, so a warp whose samples pick both pays for the assembly once.
 //
 // GGX: cos^2 theta_h = (1 - u1) / (1 + (a2 - 1) u1), evaluated as
 // (1 - u1) / ((1 - u1) + a2 u1) and sin^2 as a2 u1 / (same), which keeps the
 // digits of both for a glossy lobe (small a2) at either end of u1 (1 - u1 is
 // exact for the 24-bit uniforms).
+__device__ __forceinline__ DF dff(float x) { return DF{x, 0.0f}; }
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sqrt0(DF a) { return a.hi > 0.0f ? df_sqrt(a) : DF{0.0f, 0.0f}; }
+__device__ __forceinline__ DF df_fma(DF a, DF b, DF c) { return df_add(df_mul(a, b), c); }
 __device__ __forceinline__ float3 sample_bsdf_dir(bool spec, float3 n, float3 nlo, float3 wo, float r, float rlo,
                                                   float u1, float u2) {
-  double st, ct;
-  const double om = 1.0 - (double)u1;
+  DF st, ct;
+  const float om = 1.0f - u1;  // exact for the 24-bit uniforms
   if (spec) {
-    const double rd = (double)r + rlo, ag = rd * rd, a2 = ag * ag;
-    const double inv = rcp64(fma(a2, (double)u1, om));
-    ct = sqrt64(om * inv);
-    st = sqrt64(a2 * (double)u1 * inv);
+    const DF rd{r, rlo};
+    const DF ag = df_mul(rd, rd), a2 = df_mul(ag, ag), a2u = df_mul(a2, dff(u1));
+    const DF inv = df_div(dff(1.0f), df_add(a2u, dff(om)));
+    ct = df_sqrt0(df_mul(dff(om), inv));
+    st = df_sqrt0(df_mul(a2u, inv));
   } else {
-    st = sqrt64((double)u1);
-    ct = sqrt64(om);
+    st = df_sqrt0(dff(u1));
+    ct = df_sqrt0(dff(om));
   }
   float spf, cpf;
   sincospif(2.0f * u2, &spf, &cpf);  // angle 2 pi u2 without rounding 2 pi u2
-  const double sp = (double)spf * st, cp = (double)cpf * st;
-  const double nx = (double)n.x + nlo.x, ny = (double)n.y + nlo.y, nz = (double)n.z + nlo.z;
-  const double sgn = copysign(1.0, nz);
-  const double a = -rcp64(sgn + nz), b = nx * ny * a;
-  const double b1x = 1.0 + sgn * nx * nx * a, b1y = sgn * b, b1z = -sgn * nx;
-  const double b2x = b, b2y = sgn + ny * ny * a, b2z = -ny;
-  double vx = b1x * cp + b2x * sp + nx * ct;
-  double vy = b1y * cp + b2y * sp + ny * ct;
-  double vz = b1z * cp + b2z * sp + nz * ct;
+  const DF sp = df_mul(dff(spf), st), cp = df_mul(dff(cpf), st);
+  const DF nx{n.x, nlo.x}, ny{n.y, nlo.y}, nz{n.z, nlo.z};
+  const bool pos = nz.hi > 0.0f || (nz.hi == 0.0f && !signbit(nz.lo != 0.0f ? nz.lo : nz.hi));
+  const float sgn = pos ? 1.0f : -1.0f;
+  const DF a = df_div(dff(-1.0f), df_add(dff(sgn), nz));
+  const DF b = df_mul(df_mul(nx, ny), a), nx2a = df_mul(df_mul(nx, nx), a);
+  const DF b1x = df_add(dff(1.0f), pos ? nx2a : df_neg(nx2a)), b1y = pos ? b : df_neg(b), b1z = pos ? df_neg(nx) : nx;
+  const DF b2x = b, b2y = df_add(dff(sgn), df_mul(df_mul(ny, ny), a)), b2z = df_neg(ny);
+  DF vx = df_fma(b1x, cp, df_fma(b2x, sp, df_mul(nx, ct)));
+  DF vy = df_fma(b1y, cp, df_fma(b2y, sp, df_mul(ny, ct)));
+  DF vz = df_fma(b1z, cp, df_fma(b2z, sp, df_mul(nz, ct)));
   if (spec) {
-    const double oh2 = 2.0 * ((double)wo.x * vx + (double)wo.y * vy + (double)wo.z * vz);
-    vx = vx * oh2 - wo.x;
-    vy = vy * oh2 - wo.y;
-    vz = vz * oh2 - wo.z;
+    const DF oh = df_fma(dff(wo.x), vx, df_fma(dff(wo.y), vy, df_mul(dff(wo.z), vz)));
+    const DF oh2{2.0f * oh.hi, 2.0f * oh.lo};
+    vx = df_fma(vx, oh2, dff(-wo.x));
+    vy = df_fma(vy, oh2, dff(-wo.y));
+    vz = df_fma(vz, oh2, dff(-wo.z));
   }
-  return f3((float)vx, (float)vy, (float)vz);
+  return f3(vx.hi, vy.hi, vz.hi);
 }
 
 __device__ __forceinline__ float pdf_bsdf(float3 n, float3 wo, float3 wi, float r, float p_spec) {

@@ -26,7 +26,7 @@ FLAG_SHADE = dict(support=4e-5, alpha=4e-5, tmin=1e-3, tie=1e-8, stop=2e-5, cos=
 # its residual (x + x_lo, within ~3e-10 of the FP64 composite at the median
 # pixel and ~1e-7 at the 99th percentile, where a pixel blends surfaces a
 # distance apart and the FP32 opacities of the weights count) along a
-# direction assembled in FP64 from the record's normal and roughness with
+# direction assembled in double-float from the record's normal and roughness with
 # their residuals and rounded once to FP32 (measured against the oracle on
 # C2 and C4: 2e-8 rad at the median, 6e-8 at the 99th percentile).  Its
 # support, opacity and depth-order decisions are flagged when a ray shift of
