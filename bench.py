@@ -690,13 +690,18 @@ def read_traffic(kernel, field="dram_bytes_per_launch"):
 
 
 def sources_sha():
+    """Hash of the kernel sources with comments and blank lines removed, so
+    a committed ncu summary stays attached to the code it measured."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2608_29269_b300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(csrc, name)) as f:
+                text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+            lines = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
+            h.update("\n".join(line for line in lines if line).encode())
     return h.hexdigest()[:16]
 
 

@@ -41,8 +41,8 @@ __device__ __forceinline__ T gshfl(const Grp& g, T v, int src) {
   return __shfl_sync(g.mask, v, src, WIDE);
 }
 
-// Per-ray shared memory: the ray, the traversal stack (parallel arrays) and
-// the k-buffer's merge scratch (WIDE entries).
+// Per-ray shared memory: the ray, the traversal stack (parallel arrays), the
+// k-buffers' merge scratch and the candidate queue (WIDE entries each).
 struct CStack {
   float4* ray;  // the ray (RAY_QUADS quads, make_ray)
   int* code;
@@ -315,11 +315,11 @@ struct ShadowCoop {
 
 // Cooperative k-buffer (K = WIDE): the K smallest hit keys strictly greater
 // than the last round's, sorted over the lanes (lane c holds entry c with its
-// opacity alpha~).  A leaf's accepted candidates are merged in one step: every
-// element's place in the merged order is its own index plus the number of
-// smaller elements of the other list (counted with one ballot per
-// candidate), elements are scattered to those places in shared memory and
-// read back; places beyond K fall off.
+// opacity alpha~).  The accepted candidates of a queue flush are merged in
+// one step: every element's place in the merged order is its own index plus
+// the number of smaller elements of the other list (counted with ballots,
+// two candidates per pass), elements are scattered to those places in
+// shared memory and read back; places beyond K fall off.
 //
 // Transmittance cut: with T the transmittance in front of the round, the
 // composite of the sorted buffer stops at the first entry s with
@@ -676,8 +676,9 @@ __device__ __forceinline__ float gsum_transposed(const Grp& g, float (&v)[16]) {
 // cooperative: each round collects the K nearest hits beyond the last
 // round's, then composites them front to back in parallel -- transmittance
 // in front of each hit by a prefix product over the lanes, the stop at the
-// first hit whose transmittance behind it falls below T_min, weighted sums by
-// butterflies.  Every lane ends with the same Surface.
+// first hit whose transmittance behind it falls below T_min, the weighted
+// sums by one reduce-scatter over the lanes.  Every lane ends with the same
+// Surface.
 //
 // Normal and roughness are summed, like the position, as offsets from the
 // first composited hit's (n_ref, r_ref): sum w n_j = W n_ref + sum w (n_j -
